@@ -1,0 +1,207 @@
+/*
+ * mcubes.h -- C ABI of the GB300 (sm_103a) m-Cubes integrator library (libmcubes.so).
+ *
+ * m-Cubes (Sakiotis et al.; the integrator of arXiv 2302.05730, Sec. 3.2) is a VEGAS-style
+ * Monte Carlo integrator over the unit cube [0,1]^d. Each iteration:
+ *   - splits [0,1]^d into m = g^d sub-cubes and draws p samples in each;
+ *   - maps every draw through the separable VEGAS importance grid (500 bins per axis);
+ *   - evaluates the integrand and forms each sub-cube's mean and variance;
+ *   - accumulates per-bin contributions (Algorithm 2, the "V-Sample" kernel).
+ * The grid is then refined from the bin contributions (Rebin). The iteration estimates are
+ * combined by inverse-variance weighting.
+ *
+ * Conventions for every call:
+ *   - Return value: a status code (MCUBES_OK = 0 on success). Nothing is thrown across the ABI.
+ *     Output buffers are written only on MCUBES_OK (a result struct's status field is set
+ *     either way).
+ *   - Host pointers are owned by the caller. The library copies what it needs and keeps no
+ *     pointer after the call returns.
+ *   - Device pointers ("d_" prefix) must be device memory of the current CUDA device. They
+ *     must not be used by other work while the call's stream runs.
+ *   - `stream` is a cudaStream_t, or NULL for a stream the library owns per host thread.
+ *     "_dev" calls are asynchronous on that stream; every other call synchronises before it
+ *     returns.
+ *   - Grids are row-major d x (MCUBES_NBINS + 1) doubles: B[i][0] = 0 < B[i][1] < ... <
+ *     B[i][500] = 1. Bin contributions are d x MCUBES_NBINS doubles.
+ *   - Integrand parameters are 2d doubles: a[0..d-1] then u[0..d-1] (constant: a[0] = c).
+ *   - Calls from different host threads are safe. Each thread has its own cached workspace,
+ *     released by mcubes_shutdown() on that thread.
+ */
+#ifndef MCUBES_H
+#define MCUBES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* VEGAS bins per axis: Algorithm 2's inputs B[500 d] and C[500 d] (Sec. 3.2). */
+#define MCUBES_NBINS 500
+/* Largest supported dimension. */
+#define MCUBES_DMAX 16
+
+/* Status codes. */
+#define MCUBES_OK 0
+#define MCUBES_ERR_INVALID_ARG 1      /* a size, count, pointer or flag is out of range */
+#define MCUBES_ERR_UNSUPPORTED_DIM 2  /* d < 1 or d > MCUBES_DMAX */
+#define MCUBES_ERR_UNKNOWN_INTEGRAND 3
+#define MCUBES_ERR_CUDA 4             /* a CUDA runtime call failed; see mcubes_last_cuda_error() */
+#define MCUBES_ERR_ALLOC 5            /* device or pinned-host allocation failed */
+#define MCUBES_ERR_NONFINITE 6        /* the integrand produced a NaN or infinity */
+#define MCUBES_ERR_TIMEOUT 7          /* a bounded device-side wait gave up */
+#define MCUBES_ERR_WORKSPACE 8        /* caller-provided workspace too small or misaligned */
+
+/* Integrands: Genz families behind the paper's benchmark integrands (Sec. 5, Eq. 1-6) plus
+ * the addition integrand of Sec. 5.3 and a constant. */
+#define MCUBES_OSCILLATORY 0    /* cos(2 pi u_0 + sum a_i x_i)          Eq. 1: a_i = i, u_0 = 0 */
+#define MCUBES_PRODUCT_PEAK 1   /* prod (a_i^-2 + (x_i - u_i)^2)^-1     Eq. 2: a_i = 50, u_i = 1/2 */
+#define MCUBES_CORNER_PEAK 2    /* (1 + sum a_i x_i)^-(d+1)             Eq. 3: a_i = i */
+#define MCUBES_GAUSSIAN 3       /* exp(-sum a_i^2 (x_i - u_i)^2)        Eq. 4: a_i = 25, u_i = 1/2 */
+#define MCUBES_C0 4             /* exp(-sum a_i |x_i - u_i|)            Eq. 5: a_i = 10, u_i = 1/2 */
+#define MCUBES_DISCONTINUOUS 5  /* exp(sum a_i x_i) if x_i < u_i on every axis, else 0
+                                                                         Eq. 6: a_i = i+4, u_i = (3+i)/10 */
+#define MCUBES_ADDITION 6       /* sum x_i                               Sec. 5.3 */
+#define MCUBES_CONSTANT 7       /* a_0 */
+#define MCUBES_N_INTEGRANDS 8
+
+/* Arithmetic of the sampling path.
+ *   MCUBES_FP64: the paper's setting. Draws, map, integrand and statistics are all FP64.
+ *   MCUBES_FP32_EVAL: the point is formed, and the integrand evaluated, in FP32 with fast
+ *     SFU math. The integrand is scaled by a host-computed FP64 factor so that it stays in
+ *     range. Per-cube combination, the global sums and Rebin stay FP64. */
+#define MCUBES_FP64 0
+#define MCUBES_FP32_EVAL 1
+
+typedef struct mcubes_result {
+    double estimate;          /* combined integral estimate */
+    double error;             /* its standard deviation */
+    double chi2_dof;          /* chi^2 per degree of freedom of the iteration estimates */
+    int32_t iters_done;
+    int32_t status;           /* mirrors the return value */
+    int64_t samples_per_iter; /* m * p, the samples actually drawn per iteration */
+} mcubes_result;
+
+/* Launch tuning. Zero fields take the defaults. */
+typedef struct mcubes_tuning {
+    int32_t block_threads;    /* threads per V-Sample block (64..1024, multiple of 32); default 256 */
+    int32_t blocks_per_sm;    /* resident blocks per SM to launch (persistent grid); default: occupancy */
+    int32_t reserved[6];
+} mcubes_tuning;
+
+/* Stratification (Sec. 3.2: m sub-cubes so that a 2-point MC estimate runs in each while about
+ * ncall samples are drawn). g is the largest integer with 2 g^d <= ncall, m = g^d,
+ * p = max(2, floor(ncall / m)). Host only.
+ * Errors: UNSUPPORTED_DIM; INVALID_ARG if ncall < 2, m >= 2^32, or an output pointer is NULL. */
+int mcubes_stratify(int d, int64_t ncall, int64_t *g, int64_t *m, int64_t *p);
+
+/* Whole integration (the paper's problem statement; V-Sample = Algorithm 2, then Rebin).
+ * itmax iterations (1..65535). The first iter_adjust (0..itmax) iterations accumulate bin
+ * contributions and refine the grid; the rest sample a frozen grid. All iterations are
+ * combined by inverse-variance weighting (an iteration with zero variance makes the estimate
+ * the mean of such iterations, with error 0). Philox4x32-10 is keyed by seed. FP64 precision,
+ * default tuning, library stream.
+ * Errors: UNSUPPORTED_DIM, UNKNOWN_INTEGRAND, INVALID_ARG (NULL params/out, ncall < 2,
+ * itmax out of range, m >= 2^32), ALLOC, CUDA, NONFINITE. */
+int mcubes_integrate(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
+                     int iter_adjust, uint64_t seed, mcubes_result *out);
+
+/* mcubes_integrate with every option.
+ *   precision: MCUBES_FP64 or MCUBES_FP32_EVAL.
+ *   tune: NULL for defaults.
+ *   stream: cudaStream_t or NULL.
+ *   iter_out: NULL, or 2 * itmax doubles that receive (I_it, Var_it) for each iteration.
+ *   grid_in: NULL for the uniform grid, else d x 501 starting grid (host).
+ *   grid_out: NULL, or d x 501 doubles that receive the final grid (host).
+ * FP32_EVAL additionally requires g <= 2^24 (INVALID_ARG otherwise). */
+int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
+                        int iter_adjust, uint64_t seed, int precision, const mcubes_tuning *tune,
+                        void *stream, double *iter_out, const double *grid_in, double *grid_out,
+                        mcubes_result *out);
+
+/* One V-Sample pass (Algorithm 2) on a caller-supplied grid, with host buffers. This is the
+ * per-iteration parity hook.
+ *   iteration (0..65535) and job select the Philox counters (ctr = (t, q, iteration<<16 | j, job)).
+ *   adjust != 0: bin contributions are accumulated. Then C_out (d x 500, may be NULL) receives
+ *     them, and grid_out (d x 501, may be NULL) receives the Rebin of grid_in by them.
+ *   adjust == 0: grid_out and C_out are ignored.
+ *   grid_in: NULL for the uniform grid.
+ *   I_out, var_out: the iteration's estimate (1/m) sum I_t and variance (1/m^2) sum V_t.
+ * Errors: as mcubes_integrate_ex. */
+int mcubes_vsample_once(int integrand_id, const double *params, int d, int64_t ncall,
+                        uint64_t seed, int iteration, uint32_t job, int adjust, int precision,
+                        const double *grid_in, double *grid_out, double *C_out,
+                        double *I_out, double *var_out);
+
+/* ---------------------------------------------------------------------------------------
+ * Device-level calls: all pointers are device memory, work is queued on `stream` and the call
+ * returns without synchronising. Host-side argument errors are reported at once; kernel
+ * errors surface at the caller's next synchronisation.
+ * --------------------------------------------------------------------------------------- */
+
+/* The V-Sample kernel alone (Algorithm 2). Accumulates into d_sums[0] += sum_t I_t and
+ * d_sums[1] += sum_t V_t (not yet divided by m, m^2), and, when adjust != 0, into
+ * d_C[i][k] += sum of w^2 (d x 500). The caller zeroes d_sums and d_C first.
+ *   d_grid: d x 501.
+ *   d_prev: NULL, or the previous iteration's (I, Var) on the device. In FP32_EVAL it sets the
+ *     scale of the single-precision histogram; it never changes the result beyond rounding.
+ *   d_probe: NULL, or (m >> probe_shift) + 1 pairs of doubles. Sub-cube t with
+ *     t mod 2^probe_shift == 0 writes (I_t, V_t) to pair t >> probe_shift.
+ * Errors: as mcubes_integrate_ex. INVALID_ARG if d_grid or d_sums is NULL, if adjust is set
+ * with d_C NULL, or if probe_shift is outside 0..31. */
+int mcubes_vsample_dev(int integrand_id, const double *params, int d, int64_t ncall,
+                       uint64_t seed, int iteration, uint32_t job, int adjust, int precision,
+                       const double *d_grid, double *d_C, double *d_sums, const double *d_prev,
+                       double *d_probe, int probe_shift, const mcubes_tuning *tune, void *stream);
+
+/* Grid refinement (VEGAS, Lepage 1978; m-Cubes delegates to it). Per axis, on the device:
+ *   1. 3-point smoothing of C;
+ *   2. normalisation;
+ *   3. damping r = ((1 - rho)/ln(1/rho))^alpha with alpha = 1.5;
+ *   4. new boundaries at equal damped mass, linear inside each old bin.
+ * An axis with no contribution keeps its grid. d_grid_out and d_grid_in must be distinct.
+ * Errors: UNSUPPORTED_DIM, INVALID_ARG (NULL or aliased pointers), CUDA. */
+int mcubes_rebin_dev(int d, const double *d_grid_in, const double *d_C, double *d_grid_out,
+                     void *stream);
+
+/* Bytes of device workspace one mcubes_iteration_dev call needs for dimension d (the bin
+ * contribution accumulator and the sums; 256-byte aligned). */
+size_t mcubes_workspace_bytes(int d);
+
+/* One whole iteration on the device: zero the workspace, V-Sample, and Rebin (when adjust),
+ * then write d_result[0] = I = sum I_t / m and d_result[1] = Var = sum V_t / m^2.
+ *   d_grid_out: receives the refined grid when adjust != 0, else a copy of d_grid_in; it must
+ *     not alias d_grid_in.
+ *   d_prev: optional previous (I, Var), as in mcubes_vsample_dev.
+ *   d_workspace: at least mcubes_workspace_bytes(d) bytes of scratch, 256-byte aligned. Its
+ *     contents are overwritten.
+ * Errors: as mcubes_vsample_dev; WORKSPACE if d_workspace is NULL, misaligned or too small. */
+int mcubes_iteration_dev(int integrand_id, const double *params, int d, int64_t ncall,
+                         uint64_t seed, int iteration, uint32_t job, int adjust, int precision,
+                         const double *d_grid_in, double *d_grid_out, double *d_result,
+                         const double *d_prev, void *d_workspace, size_t workspace_bytes,
+                         const mcubes_tuning *tune, void *stream);
+
+/* Philox4x32-10 on the device, for checking the generator. out[4j..4j+3] = Philox(ctr[4j..4j+3],
+ * key = (seed mod 2^32, seed >> 32)) for j < n.
+ *   impl 0: the library's own generator (the one the sampler uses).
+ *   impl 1: the CUDA toolkit's cuRAND device function curand_Philox4x32_10.
+ * Errors: INVALID_ARG (NULL pointers, impl not 0/1), CUDA. */
+int mcubes_philox_dev(const uint32_t *d_ctr, uint64_t n, uint64_t seed, int impl,
+                      uint32_t *d_out, void *stream);
+
+/* Static description of a status code (never NULL). */
+const char *mcubes_status_string(int status);
+
+/* The last cudaError_t the calling thread saw inside the library (0 if none). */
+int mcubes_last_cuda_error(void);
+
+/* Release the calling thread's cached device workspace and stream. */
+void mcubes_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCUBES_H */

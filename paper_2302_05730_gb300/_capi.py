@@ -1,0 +1,242 @@
+"""ctypes binding of libmcubes.so (include/mcubes.h). Argument marshalling only.
+
+Every call forwards to the C ABI of the same name without the ``mcubes_`` prefix. Every step of
+the integration runs in the library's CUDA kernels. There is no CPU fallback: if the library
+has not been built, or cannot be loaded, importing this module raises.
+
+Device buffers may be given as torch CUDA tensors (their data_ptr is passed) or as raw
+integer addresses. Streams may be a torch.cuda.Stream, a raw cudaStream_t integer, or None.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmcubes.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "mcubes.h")
+
+NBINS = 500
+DMAX = 16
+FP64, FP32_EVAL = 0, 1
+
+OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_DIM", 3: "UNKNOWN_INTEGRAND", 4: "CUDA",
+          5: "ALLOC", 6: "NONFINITE", 7: "TIMEOUT", 8: "WORKSPACE"}
+
+
+class McubesError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.mcubes_status_string(status).decode() if _lib is not None else STATUS.get(status, "?")
+        extra = ""
+        if status == 4 and _lib is not None:
+            extra = f" (cudaError {_lib.mcubes_last_cuda_error()})"
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}{extra}")
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("error", ctypes.c_double),
+                ("chi2_dof", ctypes.c_double), ("iters_done", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("samples_per_iter", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmcubes.so is not built ({LIB_PATH}); run "
+                          "`python -m paper_2302_05730_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, u32, u64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "mcubes_stratify": (i32, [i32, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "mcubes_integrate": (i32, [i32, dp, i32, i64, i32, i32, u64, ctypes.POINTER(Result)]),
+        "mcubes_integrate_ex": (i32, [i32, dp, i32, i64, i32, i32, u64, i32, ctypes.POINTER(Tuning), vp,
+                                      dp, dp, dp, ctypes.POINTER(Result)]),
+        "mcubes_vsample_once": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, dp, dp, dp, dp, dp]),
+        "mcubes_vsample_dev": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, vp, vp, vp, vp, vp, i32,
+                                     ctypes.POINTER(Tuning), vp]),
+        "mcubes_rebin_dev": (i32, [i32, vp, vp, vp, vp]),
+        "mcubes_workspace_bytes": (ctypes.c_size_t, [i32]),
+        "mcubes_iteration_dev": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, vp, vp, vp, vp, vp,
+                                       ctypes.c_size_t, ctypes.POINTER(Tuning), vp]),
+        "mcubes_philox_dev": (i32, [vp, u64, u64, i32, vp, vp]),
+        "mcubes_status_string": (ctypes.c_char_p, [i32]),
+        "mcubes_last_cuda_error": (i32, []),
+        "mcubes_shutdown": (None, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+_lib = None
+_lib = _load()
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/mcubes.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcubes_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    return _lib
+
+
+# ------------------------------------------------------------------------------ marshalling
+def _dptr(x):
+    """Address of a device buffer: torch tensor, int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_cuda") and not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError(type(s))
+
+
+def _hd(a):
+    """Contiguous float64 host array and its pointer."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _tune(tune):
+    if tune is None:
+        return None
+    if isinstance(tune, Tuning):
+        return ctypes.byref(tune)
+    t = Tuning()
+    t.block_threads = int(tune.get("block_threads", 0))
+    t.blocks_per_sm = int(tune.get("blocks_per_sm", 0))
+    return ctypes.byref(t)
+
+
+def _check(st, where):
+    if st != OK:
+        raise McubesError(st, where)
+
+
+# ------------------------------------------------------------------------------ calls
+def stratify(d: int, ncall: int):
+    g, m, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.mcubes_stratify(d, ncall, ctypes.byref(g), ctypes.byref(m), ctypes.byref(p)), "stratify")
+    return g.value, m.value, p.value
+
+
+def integrate(fid, params, d, ncall, itmax, iter_adjust, seed, precision=FP64, tune=None, stream=None,
+              grid_in=None, return_iters=False, return_grid=False):
+    """Whole m-Cubes integration. Returns dict(estimate, error, chi2_dof, iters_done,
+    samples_per_iter[, iters (itmax x 2: I, Var)][, grid (d x 501)])."""
+    par, pp = _hd(params)
+    res = Result()
+    iters = np.zeros((itmax, 2)) if return_iters else None
+    grid = np.zeros((d, NBINS + 1)) if return_grid else None
+    gin = None
+    if grid_in is not None:
+        gin, gp = _hd(grid_in)
+    st = _lib.mcubes_integrate_ex(int(fid), pp, d, int(ncall), itmax, iter_adjust, int(seed) & (2 ** 64 - 1),
+                                  precision, _tune(tune), _stream(stream), _hptr(iters),
+                                  None if gin is None else gp, _hptr(grid), ctypes.byref(res))
+    _check(st, "integrate")
+    out = dict(estimate=res.estimate, error=res.error, chi2_dof=res.chi2_dof, iters_done=res.iters_done,
+               samples_per_iter=res.samples_per_iter)
+    if iters is not None:
+        out["iters"] = iters
+    if grid is not None:
+        out["grid"] = grid
+    return out
+
+
+def vsample_once(fid, params, d, ncall, seed, iteration=0, job=0, adjust=1, precision=FP64,
+                 grid_in=None, want_grid=True, want_C=True):
+    """One V-Sample pass (+ Rebin when adjust) with host buffers. Returns dict(I, Var[, C][, grid])."""
+    par, pp = _hd(params)
+    gin = gp = None
+    if grid_in is not None:
+        gin, gp = _hd(grid_in)
+    grid = np.zeros((d, NBINS + 1)) if (adjust and want_grid) else None
+    C = np.zeros((d, NBINS)) if (adjust and want_C) else None
+    I = ctypes.c_double()
+    V = ctypes.c_double()
+    st = _lib.mcubes_vsample_once(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
+                                  int(adjust), precision, gp, _hptr(grid), _hptr(C), ctypes.byref(I), ctypes.byref(V))
+    _check(st, "vsample_once")
+    out = dict(I=I.value, Var=V.value)
+    if grid is not None:
+        out["grid"] = grid
+    if C is not None:
+        out["C"] = C
+    return out
+
+
+def vsample_dev(fid, params, d, ncall, seed, iteration, job, adjust, precision, d_grid, d_C, d_sums,
+                d_prev=None, d_probe=None, probe_shift=0, tune=None, stream=None):
+    par, pp = _hd(params)
+    st = _lib.mcubes_vsample_dev(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
+                                 int(adjust), precision, _dptr(d_grid), _dptr(d_C), _dptr(d_sums), _dptr(d_prev),
+                                 _dptr(d_probe), probe_shift, _tune(tune), _stream(stream))
+    _check(st, "vsample_dev")
+
+
+def rebin_dev(d, d_grid_in, d_C, d_grid_out, stream=None):
+    _check(_lib.mcubes_rebin_dev(d, _dptr(d_grid_in), _dptr(d_C), _dptr(d_grid_out), _stream(stream)), "rebin_dev")
+
+
+def workspace_bytes(d: int) -> int:
+    return int(_lib.mcubes_workspace_bytes(d))
+
+
+def iteration_dev(fid, params, d, ncall, seed, iteration, job, adjust, precision, d_grid_in, d_grid_out,
+                  d_result, d_prev=None, d_workspace=None, workspace_bytes=0, tune=None, stream=None):
+    par, pp = _hd(params)
+    st = _lib.mcubes_iteration_dev(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
+                                   int(adjust), precision, _dptr(d_grid_in), _dptr(d_grid_out), _dptr(d_result),
+                                   _dptr(d_prev), _dptr(d_workspace), int(workspace_bytes), _tune(tune),
+                                   _stream(stream))
+    _check(st, "iteration_dev")
+
+
+def philox_dev(d_ctr, n, seed, impl, d_out, stream=None):
+    _check(_lib.mcubes_philox_dev(_dptr(d_ctr), int(n), int(seed) & (2 ** 64 - 1), impl, _dptr(d_out),
+                                  _stream(stream)), "philox_dev")
+
+
+def status_string(status: int) -> str:
+    return _lib.mcubes_status_string(status).decode()
+
+
+def last_cuda_error() -> int:
+    return int(_lib.mcubes_last_cuda_error())
+
+
+def shutdown() -> None:
+    _lib.mcubes_shutdown()

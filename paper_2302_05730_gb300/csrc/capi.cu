@@ -1,0 +1,612 @@
+// C ABI of libmcubes.so (declared in include/mcubes.h): argument checks, stratification,
+// per-thread device workspace, the iteration loop of m-Cubes (paper Sec. 3.2) and the
+// inverse-variance combination of the iteration estimates.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mcubes.h"
+#include "internal.h"
+
+using namespace mcubes;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return MCUBES_OK;
+    g_last_cuda_error = (int)e;
+    (void)cudaGetLastError();   // clear the runtime's last-error slot
+    return (e == cudaErrorMemoryAllocation) ? MCUBES_ERR_ALLOC : MCUBES_ERR_CUDA;
+}
+
+#define MC_TRY(expr)                                   \
+    do {                                               \
+        const int _st = cuda_status((cudaError_t)(expr)); \
+        if (_st != MCUBES_OK) return _st;              \
+    } while (0)
+
+constexpr int kGridStride = kNB + 1;
+
+// ---------------------------------------------------------------------------- stratification
+// g: the largest integer with 2 g^d <= n (integer arithmetic only); m = g^d; p = max(2, n / m).
+bool pow_at_most(int64_t g, int d, int64_t limit)
+{
+    int64_t v = 1;
+    for (int i = 0; i < d; ++i) {
+        if (v > limit / g) return false;
+        v *= g;
+    }
+    return v <= limit;
+}
+
+int stratify(int d, int64_t n, int64_t *g, int64_t *m, int64_t *p)
+{
+    if (d < 1 || d > MCUBES_DMAX) return MCUBES_ERR_UNSUPPORTED_DIM;
+    if (n < 2) return MCUBES_ERR_INVALID_ARG;
+    const int64_t half = n / 2;
+    int64_t lo = 1, hi = half;
+    // start the search near the root to keep it short
+    const double guess = std::floor(std::pow((double)half, 1.0 / d));
+    if (guess >= 1.0 && guess < 9.0e15) {
+        int64_t gg = (int64_t)guess;
+        while (gg > 1 && !pow_at_most(gg, d, half)) --gg;
+        while (pow_at_most(gg + 1, d, half)) ++gg;
+        lo = hi = gg;
+    }
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (pow_at_most(mid, d, half)) lo = mid; else hi = mid - 1;
+    }
+    int64_t mm = 1;
+    for (int i = 0; i < d; ++i) mm *= lo;
+    if (mm > (int64_t)0xFFFFFFFFll) return MCUBES_ERR_INVALID_ARG;
+    int64_t pp = n / mm;
+    if (pp < 2) pp = 2;
+    *g = lo;
+    *m = mm;
+    *p = pp;
+    return MCUBES_OK;
+}
+
+// ---------------------------------------------------------------------------- parameters
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kSqrtLog2e = 1.2011224087864498;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+struct Problem {
+    int fid, d, prec;
+    int64_t g, m, p;
+    VsampleParams P;
+};
+
+int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, int iteration,
+            uint32_t job, int adjust, int prec, Problem &pb)
+{
+    if (d < 1 || d > MCUBES_DMAX) return MCUBES_ERR_UNSUPPORTED_DIM;
+    if (fid < 0 || fid >= MCUBES_N_INTEGRANDS) return MCUBES_ERR_UNKNOWN_INTEGRAND;
+    if (params == nullptr) return MCUBES_ERR_INVALID_ARG;
+    if (prec != MCUBES_FP64 && prec != MCUBES_FP32_EVAL) return MCUBES_ERR_INVALID_ARG;
+    if (iteration < 0 || iteration > 0xFFFF) return MCUBES_ERR_INVALID_ARG;
+    int st = stratify(d, ncall, &pb.g, &pb.m, &pb.p);
+    if (st) return st;
+    if (pb.p > 0xFFFFFFFFll) return MCUBES_ERR_INVALID_ARG;
+    if (prec == MCUBES_FP32_EVAL && pb.g > (1 << 24)) return MCUBES_ERR_INVALID_ARG;
+    for (int i = 0; i < 2 * d; ++i)
+        if (!std::isfinite(params[i])) return MCUBES_ERR_INVALID_ARG;
+
+    pb.fid = fid;
+    pb.d = d;
+    pb.prec = prec;
+    VsampleParams &P = pb.P;
+    std::memset(&P, 0, sizeof(P));
+    P.m = (uint32_t)pb.m;
+    P.p = (uint32_t)pb.p;
+    P.g = (uint32_t)pb.g;
+    P.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    P.key1 = (uint32_t)(seed >> 32);
+    P.ctr2_hi = (uint32_t)iteration << 16;
+    P.job = job;
+    P.adjust = adjust ? 1 : 0;
+    P.R = (double)kNB / (double)pb.g;
+    P.R32 = (float)P.R;
+    P.ycap = std::nextafter((double)kNB, 0.0);
+    P.ycap32 = std::nextafterf((float)kNB, 0.0f);
+    P.inv_p = 1.0 / (double)pb.p;
+    P.inv_pp1 = 1.0 / ((double)pb.p * (double)(pb.p - 1));
+    P.probe_mask = 0xFFFFFFFFu;
+
+    IntegrandParams &ip = P.ip;
+    ip.d = d;
+    const double *a = params, *u = params + d;
+    for (int i = 0; i < d; ++i) {
+        ip.a[i] = a[i];
+        ip.u[i] = u[i];
+    }
+    if (prec == MCUBES_FP64) {
+        double s = 1.0;
+        for (int i = 0; i < d; ++i) s *= (double)kNB;
+        P.fscale = s;   // the Jacobian's nd^d, applied per block
+        if (fid == MCUBES_PRODUCT_PEAK)
+            for (int i = 0; i < d; ++i) ip.b[i] = 1.0 / (a[i] * a[i]);
+    } else {
+        double F = 1.0;
+        switch (fid) {
+        case MCUBES_OSCILLATORY:
+            for (int i = 0; i < d; ++i) ip.fa[i] = (float)(a[i] / kTwoPi);
+            ip.fc = (float)(u[0] - std::floor(u[0]));
+            break;
+        case MCUBES_PRODUCT_PEAK:
+            for (int i = 0; i < d; ++i) {
+                ip.fa[i] = (float)a[i];
+                ip.fu[i] = (float)u[i];
+                F *= a[i] * a[i];
+            }
+            break;
+        case MCUBES_CORNER_PEAK:
+            for (int i = 0; i < d; ++i) ip.fa[i] = (float)a[i];
+            break;
+        case MCUBES_GAUSSIAN:
+            for (int i = 0; i < d; ++i) {
+                ip.fa[i] = (float)(a[i] * kSqrtLog2e);
+                ip.fu[i] = (float)u[i];
+            }
+            break;
+        case MCUBES_C0:
+            for (int i = 0; i < d; ++i) {
+                ip.fa[i] = (float)(a[i] * kLog2e);
+                ip.fu[i] = (float)u[i];
+            }
+            break;
+        case MCUBES_DISCONTINUOUS: {
+            double e = 0.0;
+            for (int i = 0; i < d; ++i) {
+                const double uc = u[i] < 1.0 ? u[i] : 1.0;
+                ip.fa[i] = (float)(a[i] * kLog2e);
+                ip.fu[i] = (float)u[i];
+                ip.fb[i] = (float)uc;
+                e += a[i] * uc;
+            }
+            F = std::exp(e);
+            break;
+        }
+        case MCUBES_ADDITION:
+            break;
+        case MCUBES_CONSTANT:
+            F = a[0];
+            break;
+        }
+        if (!std::isfinite(F)) return MCUBES_ERR_INVALID_ARG;
+        P.fscale = F;
+    }
+    return MCUBES_OK;
+}
+
+using Launcher = int (*)(int, const VsampleParams &, const LaunchReq &, cudaStream_t);
+
+Launcher launcher_for(int prec, int fid)
+{
+    static const Launcher f64[8] = {launch_vsample_f64_0, launch_vsample_f64_1, launch_vsample_f64_2,
+                                    launch_vsample_f64_3, launch_vsample_f64_4, launch_vsample_f64_5,
+                                    launch_vsample_f64_6, launch_vsample_f64_7};
+    static const Launcher f32[8] = {launch_vsample_f32_0, launch_vsample_f32_1, launch_vsample_f32_2,
+                                    launch_vsample_f32_3, launch_vsample_f32_4, launch_vsample_f32_5,
+                                    launch_vsample_f32_6, launch_vsample_f32_7};
+    return prec == MCUBES_FP32_EVAL ? f32[fid] : f64[fid];
+}
+
+int make_req(const mcubes_tuning *tune, LaunchReq &req)
+{
+    int dev = 0;
+    MC_TRY(cudaGetDevice(&dev));
+    int sms = 0;
+    MC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    req.num_sms = sms;
+    req.threads = kMaxBlockThreads;
+    req.blocks_per_sm = 0;
+    if (tune) {
+        if (tune->block_threads) {
+            if (tune->block_threads < 64 || tune->block_threads > kMaxBlockThreads || tune->block_threads % 32)
+                return MCUBES_ERR_INVALID_ARG;
+            req.threads = tune->block_threads;
+        }
+        if (tune->blocks_per_sm < 0 || tune->blocks_per_sm > 64) return MCUBES_ERR_INVALID_ARG;
+        req.blocks_per_sm = tune->blocks_per_sm;
+    }
+    return MCUBES_OK;
+}
+
+int launch_vsample(const Problem &pb, const mcubes_tuning *tune, cudaStream_t s)
+{
+    LaunchReq req;
+    int st = make_req(tune, req);
+    if (st) return st;
+    return cuda_status((cudaError_t)launcher_for(pb.prec, pb.fid)(pb.d, pb.P, req, s));
+}
+
+// ---------------------------------------------------------------------------- small kernels
+__global__ void uniform_grid_kernel(double *grid, int d)
+{
+    const int n = d * kGridStride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int k = e % kGridStride;
+        grid[e] = (double)k / (double)kNB;
+    }
+}
+
+// result = (sums[0] / m, sums[1] / m^2)
+__global__ void finalize_kernel(const double *sums, double *result, double inv_m)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        result[0] = sums[0] * inv_m;
+        result[1] = sums[1] * inv_m * inv_m;
+    }
+}
+
+// ---------------------------------------------------------------------------- workspace
+struct Workspace {
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    double *d_grid[2] = {nullptr, nullptr};   // ping-pong grids, DMAX x 501
+    double *d_C = nullptr;                    // DMAX x 500
+    double *d_iter = nullptr;                 // 2 x iter_cap sums
+    int iter_cap = 0;
+    double *h_pin = nullptr;                  // pinned staging
+    size_t h_pin_bytes = 0;
+
+    void release()
+    {
+        if (device >= 0) {
+            int cur = 0;
+            cudaGetDevice(&cur);
+            cudaSetDevice(device);
+            if (stream) cudaStreamDestroy(stream);
+            cudaFree(d_grid[0]);
+            cudaFree(d_grid[1]);
+            cudaFree(d_C);
+            cudaFree(d_iter);
+            if (h_pin) cudaFreeHost(h_pin);
+            cudaSetDevice(cur);
+        }
+        *this = Workspace();
+    }
+};
+
+thread_local Workspace g_ws;
+
+int workspace(int iters, size_t host_bytes, Workspace *&out)
+{
+    int dev = 0;
+    MC_TRY(cudaGetDevice(&dev));
+    Workspace &w = g_ws;
+    if (w.device != dev) {
+        w.release();
+        w.device = dev;
+        MC_TRY(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+        const size_t gb = sizeof(double) * MCUBES_DMAX * kGridStride;
+        MC_TRY(cudaMalloc(&w.d_grid[0], gb));
+        MC_TRY(cudaMalloc(&w.d_grid[1], gb));
+        MC_TRY(cudaMalloc(&w.d_C, sizeof(double) * MCUBES_DMAX * kNB));
+    }
+    if (iters > w.iter_cap) {
+        if (w.d_iter) MC_TRY(cudaFree(w.d_iter));
+        w.d_iter = nullptr;
+        w.iter_cap = 0;
+        MC_TRY(cudaMalloc(&w.d_iter, sizeof(double) * 2 * (size_t)iters));
+        w.iter_cap = iters;
+    }
+    if (host_bytes > w.h_pin_bytes) {
+        if (w.h_pin) MC_TRY(cudaFreeHost(w.h_pin));
+        w.h_pin = nullptr;
+        w.h_pin_bytes = 0;
+        MC_TRY(cudaMallocHost(&w.h_pin, host_bytes));
+        w.h_pin_bytes = host_bytes;
+    }
+    out = &w;
+    return MCUBES_OK;
+}
+
+int upload_grid(const double *grid_in, int d, double *d_grid, double *h_stage, cudaStream_t s)
+{
+    if (grid_in) {
+        std::memcpy(h_stage, grid_in, sizeof(double) * d * kGridStride);
+        MC_TRY(cudaMemcpyAsync(d_grid, h_stage, sizeof(double) * d * kGridStride, cudaMemcpyHostToDevice, s));
+    } else {
+        uniform_grid_kernel<<<(d * kGridStride + 255) / 256, 256, 0, s>>>(d_grid, d);
+        MC_TRY(cudaGetLastError());
+    }
+    return MCUBES_OK;
+}
+
+bool grid_ok(const double *grid, int d)
+{
+    for (int i = 0; i < d; ++i) {
+        const double *b = grid + (size_t)i * kGridStride;
+        if (!(b[0] == 0.0 && b[kNB] == 1.0)) return false;
+        for (int k = 0; k < kNB; ++k)
+            if (!(b[k + 1] > b[k])) return false;
+    }
+    return true;
+}
+
+// Inverse-variance combination of the iteration estimates.
+void combine(const std::vector<double> &I, const std::vector<double> &V, mcubes_result *out)
+{
+    const int n = (int)I.size();
+    int nzero = 0;
+    double zsum = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (V[i] == 0.0) {
+            ++nzero;
+            zsum += I[i];
+        }
+    if (nzero > 0) {
+        out->estimate = zsum / nzero;
+        out->error = 0.0;
+        out->chi2_dof = 0.0;
+        return;
+    }
+    double sw = 0.0, swI = 0.0;
+    for (int i = 0; i < n; ++i) {
+        sw += 1.0 / V[i];
+        swI += I[i] / V[i];
+    }
+    const double Ibar = swI / sw;
+    double chi = 0.0;
+    for (int i = 0; i < n; ++i) chi += (I[i] - Ibar) * (I[i] - Ibar) / V[i];
+    out->estimate = Ibar;
+    out->error = 1.0 / std::sqrt(sw);
+    out->chi2_dof = n > 1 ? chi / (double)(n - 1) : 0.0;
+}
+
+}  // namespace
+
+// ============================================================================ exported calls
+extern "C" {
+
+const char *mcubes_status_string(int status)
+{
+    switch (status) {
+    case MCUBES_OK: return "ok";
+    case MCUBES_ERR_INVALID_ARG: return "invalid argument";
+    case MCUBES_ERR_UNSUPPORTED_DIM: return "unsupported dimension (1..16)";
+    case MCUBES_ERR_UNKNOWN_INTEGRAND: return "unknown integrand id";
+    case MCUBES_ERR_CUDA: return "CUDA runtime error";
+    case MCUBES_ERR_ALLOC: return "allocation failed";
+    case MCUBES_ERR_NONFINITE: return "integrand produced a non-finite value";
+    case MCUBES_ERR_TIMEOUT: return "device-side wait timed out";
+    case MCUBES_ERR_WORKSPACE: return "workspace too small or misaligned";
+    default: return "unknown status";
+    }
+}
+
+int mcubes_last_cuda_error(void) { return g_last_cuda_error; }
+
+void mcubes_shutdown(void) { g_ws.release(); }
+
+int mcubes_stratify(int d, int64_t ncall, int64_t *g, int64_t *m, int64_t *p)
+{
+    if (!g || !m || !p) return MCUBES_ERR_INVALID_ARG;
+    return stratify(d, ncall, g, m, p);
+}
+
+int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
+                        int iter_adjust, uint64_t seed, int precision, const mcubes_tuning *tune,
+                        void *stream, double *iter_out, const double *grid_in, double *grid_out,
+                        mcubes_result *out)
+{
+    if (out) std::memset(out, 0, sizeof(*out));
+    int st = MCUBES_OK;
+    Problem pb;
+    if (!out) st = MCUBES_ERR_INVALID_ARG;
+    else if (itmax < 1 || itmax > 0xFFFF || iter_adjust < 0 || iter_adjust > itmax) st = MCUBES_ERR_INVALID_ARG;
+    if (!st) st = prepare(integrand_id, params, d, ncall, seed, 0, 0, iter_adjust > 0, precision, pb);
+    if (!st && grid_in && !grid_ok(grid_in, d)) st = MCUBES_ERR_INVALID_ARG;
+    if (st) {
+        if (out) out->status = st;
+        return st;
+    }
+    auto fail = [&](int s) {
+        out->status = s;
+        return s;
+    };
+
+    Workspace *w = nullptr;
+    const size_t host_bytes = sizeof(double) * (2 * (size_t)itmax + (size_t)d * kGridStride);
+    if ((st = workspace(itmax, host_bytes, w))) return fail(st);
+    cudaStream_t s = stream ? (cudaStream_t)stream : w->stream;
+
+    int cur = 0;
+    if ((st = upload_grid(grid_in, d, w->d_grid[0], w->h_pin, s))) return fail(st);
+    if ((st = cuda_status(cudaMemsetAsync(w->d_iter, 0, sizeof(double) * 2 * itmax, s)))) return fail(st);
+    for (int it = 0; it < itmax; ++it) {
+        const int adjust = it < iter_adjust;
+        VsampleParams &P = pb.P;
+        P.grid = w->d_grid[cur];
+        P.C = w->d_C;
+        P.sums = w->d_iter + 2 * it;
+        P.prev = it > 0 ? w->d_iter + 2 * (it - 1) : nullptr;   // raw sums: I = sum / m
+        P.prev_scale = 1.0 / (double)pb.m;
+        P.adjust = adjust;
+        P.ctr2_hi = (uint32_t)it << 16;
+        if (adjust) {
+            if ((st = cuda_status(cudaMemsetAsync(w->d_C, 0, sizeof(double) * d * kNB, s)))) return fail(st);
+        }
+        if ((st = launch_vsample(pb, tune, s))) return fail(st);
+        if (adjust && it + 1 < itmax) {
+            if ((st = cuda_status((cudaError_t)launch_rebin(d, w->d_grid[cur], w->d_C, w->d_grid[1 - cur], 1.5, s))))
+                return fail(st);
+            cur = 1 - cur;
+        }
+    }
+    double *h_iter = w->h_pin;
+    double *h_grid = w->h_pin + 2 * itmax;
+    if ((st = cuda_status(cudaMemcpyAsync(h_iter, w->d_iter, sizeof(double) * 2 * itmax, cudaMemcpyDeviceToHost, s))))
+        return fail(st);
+    if (grid_out) {
+        if ((st = cuda_status(cudaMemcpyAsync(h_grid, w->d_grid[cur], sizeof(double) * d * kGridStride,
+                                              cudaMemcpyDeviceToHost, s))))
+            return fail(st);
+    }
+    if ((st = cuda_status(cudaStreamSynchronize(s)))) return fail(st);
+
+    std::vector<double> I(itmax), V(itmax);
+    const double m = (double)pb.m;
+    for (int it = 0; it < itmax; ++it) {
+        I[it] = h_iter[2 * it] / m;
+        V[it] = h_iter[2 * it + 1] / (m * m);
+        if (!std::isfinite(I[it]) || !std::isfinite(V[it])) return fail(MCUBES_ERR_NONFINITE);
+    }
+    if (iter_out)
+        for (int it = 0; it < itmax; ++it) {
+            iter_out[2 * it] = I[it];
+            iter_out[2 * it + 1] = V[it];
+        }
+    if (grid_out) std::memcpy(grid_out, h_grid, sizeof(double) * d * kGridStride);
+    combine(I, V, out);
+    out->iters_done = itmax;
+    out->samples_per_iter = pb.m * pb.p;
+    out->status = MCUBES_OK;
+    return MCUBES_OK;
+}
+
+int mcubes_integrate(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
+                     int iter_adjust, uint64_t seed, mcubes_result *out)
+{
+    return mcubes_integrate_ex(integrand_id, params, d, ncall, itmax, iter_adjust, seed, MCUBES_FP64,
+                               nullptr, nullptr, nullptr, nullptr, nullptr, out);
+}
+
+int mcubes_vsample_once(int integrand_id, const double *params, int d, int64_t ncall, uint64_t seed,
+                        int iteration, uint32_t job, int adjust, int precision, const double *grid_in,
+                        double *grid_out, double *C_out, double *I_out, double *var_out)
+{
+    Problem pb;
+    int st = prepare(integrand_id, params, d, ncall, seed, iteration, job, adjust, precision, pb);
+    if (st) return st;
+    if (!I_out || !var_out) return MCUBES_ERR_INVALID_ARG;
+    if (grid_in && !grid_ok(grid_in, d)) return MCUBES_ERR_INVALID_ARG;
+    Workspace *w = nullptr;
+    const size_t nb = (size_t)d * kGridStride, nc = (size_t)d * kNB;
+    if ((st = workspace(1, sizeof(double) * (nb + nc + 2 + nb), w))) return st;
+    cudaStream_t s = w->stream;
+    if ((st = upload_grid(grid_in, d, w->d_grid[0], w->h_pin, s))) return st;
+    MC_TRY(cudaMemsetAsync(w->d_iter, 0, sizeof(double) * 2, s));
+    if (adjust) MC_TRY(cudaMemsetAsync(w->d_C, 0, sizeof(double) * nc, s));
+    VsampleParams &P = pb.P;
+    P.grid = w->d_grid[0];
+    P.C = w->d_C;
+    P.sums = w->d_iter;
+    if ((st = launch_vsample(pb, nullptr, s))) return st;
+    if (adjust && grid_out) {
+        MC_TRY(launch_rebin(d, w->d_grid[0], w->d_C, w->d_grid[1], 1.5, s));
+    }
+    double *h_sums = w->h_pin + nb;
+    double *h_C = h_sums + 2;
+    double *h_grid = h_C + nc;
+    MC_TRY(cudaMemcpyAsync(h_sums, w->d_iter, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    if (adjust && C_out) MC_TRY(cudaMemcpyAsync(h_C, w->d_C, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    if (adjust && grid_out)
+        MC_TRY(cudaMemcpyAsync(h_grid, w->d_grid[1], sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    MC_TRY(cudaStreamSynchronize(s));
+    const double m = (double)pb.m;
+    const double I = h_sums[0] / m, V = h_sums[1] / (m * m);
+    if (!std::isfinite(I) || !std::isfinite(V)) return MCUBES_ERR_NONFINITE;
+    *I_out = I;
+    *var_out = V;
+    if (adjust && C_out) std::memcpy(C_out, h_C, sizeof(double) * nc);
+    if (adjust && grid_out) std::memcpy(grid_out, h_grid, sizeof(double) * nb);
+    return MCUBES_OK;
+}
+
+int mcubes_vsample_dev(int integrand_id, const double *params, int d, int64_t ncall, uint64_t seed,
+                       int iteration, uint32_t job, int adjust, int precision, const double *d_grid,
+                       double *d_C, double *d_sums, const double *d_prev, double *d_probe,
+                       int probe_shift, const mcubes_tuning *tune, void *stream)
+{
+    Problem pb;
+    int st = prepare(integrand_id, params, d, ncall, seed, iteration, job, adjust, precision, pb);
+    if (st) return st;
+    if (!d_grid || !d_sums || (adjust && !d_C)) return MCUBES_ERR_INVALID_ARG;
+    if (probe_shift < 0 || probe_shift > 31) return MCUBES_ERR_INVALID_ARG;
+    VsampleParams &P = pb.P;
+    P.grid = d_grid;
+    P.C = d_C;
+    P.sums = d_sums;
+    P.prev = d_prev;
+    P.prev_scale = 1.0;
+    P.probe = d_probe;
+    P.probe_shift = (uint32_t)probe_shift;
+    P.probe_mask = d_probe ? ((probe_shift == 0) ? 0u : ((1u << probe_shift) - 1u)) : 0xFFFFFFFFu;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) {
+        Workspace *w = nullptr;
+        if ((st = workspace(1, 0, w))) return st;
+        s = w->stream;
+    }
+    return launch_vsample(pb, tune, s);
+}
+
+int mcubes_rebin_dev(int d, const double *d_grid_in, const double *d_C, double *d_grid_out, void *stream)
+{
+    if (d < 1 || d > MCUBES_DMAX) return MCUBES_ERR_UNSUPPORTED_DIM;
+    if (!d_grid_in || !d_C || !d_grid_out || d_grid_in == d_grid_out) return MCUBES_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) {
+        Workspace *w = nullptr;
+        int st = workspace(1, 0, w);
+        if (st) return st;
+        s = w->stream;
+    }
+    return cuda_status((cudaError_t)launch_rebin(d, d_grid_in, d_C, d_grid_out, 1.5, s));
+}
+
+size_t mcubes_workspace_bytes(int d)
+{
+    if (d < 1 || d > MCUBES_DMAX) return 0;
+    const size_t c = sizeof(double) * (size_t)d * kNB;
+    const size_t c_al = (c + 255) & ~(size_t)255;
+    return c_al + 256;   // C, then the two sums
+}
+
+int mcubes_iteration_dev(int integrand_id, const double *params, int d, int64_t ncall, uint64_t seed,
+                         int iteration, uint32_t job, int adjust, int precision, const double *d_grid_in,
+                         double *d_grid_out, double *d_result, const double *d_prev, void *d_workspace,
+                         size_t workspace_bytes, const mcubes_tuning *tune, void *stream)
+{
+    Problem pb;
+    int st = prepare(integrand_id, params, d, ncall, seed, iteration, job, adjust, precision, pb);
+    if (st) return st;
+    if (!d_grid_in || !d_grid_out || !d_result || d_grid_in == d_grid_out) return MCUBES_ERR_INVALID_ARG;
+    const size_t need = mcubes_workspace_bytes(d);
+    if (!d_workspace || workspace_bytes < need || ((uintptr_t)d_workspace & 255u)) return MCUBES_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) {
+        Workspace *w = nullptr;
+        if ((st = workspace(1, 0, w))) return st;
+        s = w->stream;
+    }
+    double *C = (double *)d_workspace;
+    double *sums = (double *)((char *)d_workspace + (need - 256));
+    MC_TRY(cudaMemsetAsync(d_workspace, 0, need, s));
+    VsampleParams &P = pb.P;
+    P.grid = d_grid_in;
+    P.C = C;
+    P.sums = sums;
+    P.prev = d_prev;
+    P.prev_scale = 1.0;
+    if ((st = launch_vsample(pb, tune, s))) return st;
+    if (adjust) {
+        MC_TRY(launch_rebin(d, d_grid_in, C, d_grid_out, 1.5, s));
+    } else {
+        MC_TRY(cudaMemcpyAsync(d_grid_out, d_grid_in, sizeof(double) * d * kGridStride, cudaMemcpyDeviceToDevice, s));
+    }
+    finalize_kernel<<<1, 32, 0, s>>>(sums, d_result, 1.0 / (double)pb.m);
+    MC_TRY(cudaGetLastError());
+    return MCUBES_OK;
+}
+
+}  // extern "C"

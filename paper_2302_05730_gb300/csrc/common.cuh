@@ -1,0 +1,87 @@
+// Device-side building blocks shared by the m-Cubes kernels: constants, the launch parameter
+// block of the V-Sample kernel, and the counter-based Philox4x32-10 generator.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcubes {
+
+constexpr int kNB = 500;     // VEGAS bins per axis (Algorithm 2: B[500 d], C[500 d])
+constexpr int kDMax = 16;
+constexpr int kMaxBlockThreads = 256;   // V-Sample block size limit (launch bounds)
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 4-word counter, 2-word key, ten rounds
+// of the Philox S-box. Round: multiply words 0 and 2 by the two published constants (full
+// 64-bit products), exchange halves and xor the high halves with words 1, 3 and the key;
+// the key is bumped by the two Weyl increments between rounds.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+struct Words4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                         uint32_t c3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)c0;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n1 = (uint32_t)p1;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        const uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return Words4{c0, c1, c2, c3};
+}
+
+// Integrand parameters as the kernels consume them. The FP64 path reads a and u as given;
+// the FP32 path reads pre-scaled single-precision forms prepared on the host (see
+// integrands.cuh for what each family stores).
+struct IntegrandParams {
+    double a[kDMax];
+    double u[kDMax];
+    double b[kDMax];   // FP64 auxiliary per axis (product peak: 1 / a^2)
+    float fa[kDMax];
+    float fu[kDMax];
+    float fb[kDMax];   // FP32 auxiliary per axis (discontinuous: min(u, 1))
+    float fc;          // FP32 scalar (oscillatory: u_0 mod 1)
+    int d;
+};
+
+// Everything one V-Sample launch needs, passed by value.
+struct VsampleParams {
+    const double *grid;      // d x (kNB + 1)
+    double *C;               // d x kNB, accumulated (adjust) -- may be null otherwise
+    double *sums;            // [2]: sum_t I_t, sum_t V_t (accumulated)
+    const double *prev;      // previous iteration's estimate (prev[0] * prev_scale = I) or null
+    double prev_scale;
+    double *probe;           // per-cube probe output or null
+    uint32_t probe_mask;     // cube t is probed when (t & probe_mask) == 0
+    uint32_t probe_shift;
+    uint32_t m;              // sub-cubes
+    uint32_t p;              // samples per sub-cube
+    uint32_t g;              // strata per axis
+    uint32_t key0, key1;     // Philox key = seed
+    uint32_t ctr2_hi;        // iteration << 16
+    uint32_t job;            // counter word 3
+    int adjust;
+    double R;                // nd / g (FP64)
+    float R32;               // (float)(nd / g)
+    double ycap;             // largest double below nd
+    float ycap32;            // largest float below nd
+    double inv_p;            // 1 / p
+    double inv_pp1;          // 1 / (p (p - 1))
+    double fscale;           // FP32 path: f = fscale * (kernel's scaled integrand)
+    double log_fscale;       // log(fscale), or 0
+    IntegrandParams ip;
+};
+
+}  // namespace mcubes

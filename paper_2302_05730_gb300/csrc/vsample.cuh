@@ -1,0 +1,319 @@
+// The m-Cubes V-Sample kernel (paper Sec. 3.2, Algorithm 2), written for sm_103a.
+//
+// Work decomposition. A persistent grid (blocks = SMs x resident blocks). Thread j of the
+// whole grid owns the contiguous sub-cube range [j m / N, (j+1) m / N) (N threads). Its
+// strata digits are decomposed once and then advanced by +1 with carry.
+//
+// Per sample (Algorithm 2's inner loop):
+//   1. Philox4x32-10 draws with counter (t, q, it << 16 | j, job) and key = seed;
+//   2. the VEGAS map through the grid staged in shared memory, as (B_k, Delta_k) pairs;
+//   3. the integrand, fed coordinate by coordinate;
+//   4. the sub-cube sums;
+//   5. on adjusting iterations, the bin contributions w^2, added to a block-private
+//      shared-memory histogram.
+//
+// Per block at the end:
+//   - warp-shuffle and shared-memory reduction of the thread sums, then two FP64 global
+//     atomics into sums[0..1] (Algorithm 2's AtomicAdd into r);
+//   - the private histogram flushed to the global FP64 bin contributions C with one atomic
+//     per non-empty bin.
+//
+// FP64 path: every step in double. The point uses the exact operation sequence of the
+// definition, so the bins match a CPU evaluation bit for bit:
+//   yn = min((c + u) R, largest double below nd), k = floor(yn), delta = yn - k,
+//   x = fma(Delta_k, delta, B_k).
+// Its Jacobian factor nd^d is applied once per block.
+//
+// FP32 path: the same sequence in single precision, with u on 23 bits, so that the bin and
+// the point match a CPU single-precision evaluation bit for bit. Then:
+//   - the scaled integrand f/F (fast SFU math);
+//   - per sub-cube shifted sums (w - w_0), combined per sub-cube in FP64;
+//   - the histogram in single precision, holding (w sigma)^2 with sigma = F / |I_prev|.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "integrands.cuh"
+
+namespace mcubes {
+
+template <bool F32>
+struct Prec;
+template <>
+struct Prec<false> {
+    using T = double;
+    using T2 = double2;
+};
+template <>
+struct Prec<true> {
+    using T = float;
+    using T2 = float2;
+};
+
+// Shared-memory bytes of one block: the (B, Delta) table and, when adjusting, the histogram.
+template <bool F32>
+__host__ __device__ constexpr size_t vsample_smem_bytes(int d, bool adjust)
+{
+    return (size_t)d * kNB * (sizeof(typename Prec<F32>::T2) + (adjust ? sizeof(typename Prec<F32>::T) : 0));
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of two doubles; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch /* 2*32 */)
+{
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        scratch[warp] = a;
+        scratch[32 + warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = lane < nw ? scratch[lane] : 0.0;
+        b = lane < nw ? scratch[32 + lane] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+}
+
+template <int D, int FID, bool F32>
+__global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const VsampleParams P)
+{
+    using T = typename Prec<F32>::T;
+    using T2 = typename Prec<F32>::T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *tab = reinterpret_cast<T2 *>(smem_raw);
+    T *hist = reinterpret_cast<T *>(smem_raw + (size_t)D * kNB * sizeof(T2));
+    __shared__ double red_scratch[64];
+
+    const bool adjust = P.adjust != 0;
+
+    // ---- stage the grid as (B_k, Delta_k) and clear the private histogram
+    for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
+        const int i = e / kNB;
+        const int k = e - i * kNB;
+        const double b0 = P.grid[i * (kNB + 1) + k];
+        const double b1 = P.grid[i * (kNB + 1) + k + 1];
+        T2 v;
+        v.x = (T)b0;
+        v.y = (T)(b1 - b0);
+        tab[e] = v;
+        if (adjust) hist[e] = T(0);
+    }
+    __syncthreads();
+
+    // ---- this thread's sub-cube range
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t t = (uint32_t)((gtid * P.m) / nthreads);
+    const uint32_t t_end = (uint32_t)(((gtid + 1) * P.m) / nthreads);
+
+    // strata digits c_i (axis 0 fastest) and c_i - 1 in the path's precision
+    uint32_t dig[D];
+    T cm1[D];
+    {
+        uint32_t rest = t;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            dig[i] = rest % P.g;
+            rest /= P.g;
+            cm1[i] = (T)dig[i] - T(1);
+        }
+    }
+
+    const T R = F32 ? (T)P.R32 : (T)P.R;
+    const T ycap = F32 ? (T)P.ycap32 : (T)P.ycap;
+    const T magic = F32 ? (T)8388608.0f : (T)4503599627370496.0;   // 2^23 / 2^52
+
+    // FP32 histogram scale sigma = F / |I_prev| (1 when unknown)
+    float hsig = 1.0f;
+    if (F32 && adjust && P.prev != nullptr) {
+        const double ip = fabs(P.prev[0] * P.prev_scale);
+        if (ip > 0.0 && ip < 1e300 && P.fscale > 0.0) {
+            const double s = P.fscale / ip;
+            if (s > 1e-30 && s < 1e30) hsig = (float)s;
+        }
+    }
+
+    double sI = 0.0, sV = 0.0;
+    const uint32_t p = P.p;
+
+    for (; t < t_end; ++t) {
+        T S1 = T(0), S2 = T(0), w0 = T(0);   // FP64: plain sums; FP32: w0 and shifted sums
+
+        for (uint32_t q = 0; q < p; ++q) {
+            Integrand64<FID, D> f64;
+            Integrand32<FID, D> f32;
+            T J = T(1);
+            int kofs[D];
+
+            constexpr int kDimsPerCall = F32 ? 4 : 2;
+            constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
+#pragma unroll
+            for (int j = 0; j < kCalls; ++j) {
+                const Words4 r = philox4x32_10(t, q, P.ctr2_hi | (uint32_t)j, P.job, P.key0, P.key1);
+                const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int h = 0; h < kDimsPerCall; ++h) {
+                    const int i = j * kDimsPerCall + h;
+                    if (i < D) {
+                        // f = 1 + u exactly; (c - 1) + f rounds like c + u
+                        T f;
+                        if constexpr (F32) {
+                            f = __uint_as_float((wv[h] & 0x7FFFFFu) | 0x3F800000u);
+                        } else {
+                            f = __hiloint2double((int)((wv[2 * h] & 0xFFFFFu) | 0x3FF00000u), (int)wv[2 * h + 1]);
+                        }
+                        T yn;
+                        if constexpr (F32) {
+                            yn = __fmul_rn(__fadd_rn(cm1[i], f), R);
+                            yn = fminf(yn, ycap);
+                        } else {
+                            yn = __dmul_rn(__dadd_rn(cm1[i], f), R);
+                            yn = fmin(yn, ycap);
+                        }
+                        // floor(yn) for 0 <= yn < 2^23 (2^52): add the magic number rounding down
+                        T kb;
+                        int k;
+                        if constexpr (F32) {
+                            kb = __fadd_rd(yn, magic);
+                            k = (int)(__float_as_uint(kb) & 0x7FFFFFu);
+                            kb = __fsub_rn(kb, magic);
+                        } else {
+                            kb = __dadd_rd(yn, magic);
+                            k = __double2loint(kb);
+                            kb = __dsub_rn(kb, magic);
+                        }
+                        const T delta = yn - kb;     // exact
+                        const T2 bw = tab[i * kNB + k];
+                        T x;
+                        if constexpr (F32) {
+                            x = __fmaf_rn(bw.y, delta, bw.x);
+                            f32.add(i, x, P.ip);
+                        } else {
+                            x = __fma_rn(bw.y, delta, bw.x);
+                            f64.add(i, x, P.ip);
+                        }
+                        J *= bw.y;
+                        if constexpr (F32) {
+                            // keep J near 1: fold nd^4 in after every fourth axis
+                            if ((i & 3) == 3) J *= 6.25e10f;
+                        }
+                        kofs[i] = i * kNB + k;
+                    }
+                }
+            }
+            T w;
+            if constexpr (F32) {
+                constexpr int rem = D & 3;
+                if (rem == 1) J *= 500.0f;
+                if (rem == 2) J *= 250000.0f;
+                if (rem == 3) J *= 125000000.0f;
+                w = f32.finish(P.ip) * J;
+            } else {
+                w = f64.finish(P.ip) * J;   // Jacobian without nd^d (applied per block)
+            }
+
+            if constexpr (F32) {
+                if (q == 0) {
+                    w0 = w;
+                } else {
+                    const float dv = w - w0;
+                    S1 += dv;
+                    S2 = fmaf(dv, dv, S2);
+                }
+            } else {
+                S1 += w;
+                S2 = fma(w, w, S2);
+            }
+
+            if (adjust) {
+                T h;
+                if constexpr (F32) {
+                    const float ws = w * hsig;
+                    h = ws * ws;
+                } else {
+                    h = w * w;
+                }
+#pragma unroll
+                for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], h);
+            }
+        }
+
+        // per sub-cube mean and variance (Algorithm 2 UpdateVariance), FP64
+        double It, Vt;
+        if constexpr (F32) {
+            const double dw0 = (double)w0, d1 = (double)S1, d2 = (double)S2;
+            It = fma(d1, P.inv_p, dw0);
+            Vt = fma(-d1 * P.inv_p, d1, d2);
+        } else {
+            It = S1 * P.inv_p;
+            Vt = fma(-S1 * P.inv_p, S1, S2);
+        }
+        Vt = Vt > 0.0 ? Vt : 0.0;
+        sI += It;
+        sV += Vt;
+        if (P.probe != nullptr && (t & P.probe_mask) == 0) {
+            // probe values on the final scale
+            double sc, sc2;
+            if constexpr (F32) {
+                sc = P.fscale;
+                sc2 = P.fscale * P.fscale;
+            } else {
+                sc = P.fscale;   // nd^d on the FP64 path
+                sc2 = P.fscale * P.fscale;
+            }
+            P.probe[2 * (size_t)(t >> P.probe_shift)] = It * sc;
+            P.probe[2 * (size_t)(t >> P.probe_shift) + 1] = Vt * P.inv_pp1 * sc2;
+        }
+
+        // advance the strata digits to sub-cube t + 1
+        bool carry = true;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            if (carry) {
+                if (++dig[i] < P.g) {
+                    cm1[i] += T(1);
+                    carry = false;
+                } else {
+                    dig[i] = 0;
+                    cm1[i] = T(-1);
+                }
+            }
+        }
+    }
+
+    // ---- block reduction, then two FP64 global atomics (Algorithm 2, AtomicAdd into r)
+    block_sum2(sI, sV, red_scratch);
+    if (threadIdx.x == 0) {
+        atomicAdd(&P.sums[0], sI * P.fscale);
+        atomicAdd(&P.sums[1], sV * P.inv_pp1 * P.fscale * P.fscale);
+    }
+
+    // ---- flush the private histogram into the global bin contributions
+    if (adjust) {
+        __syncthreads();
+        double cscale;
+        if constexpr (F32) {
+            const double r = P.fscale / (double)hsig;
+            cscale = r * r;
+        } else {
+            cscale = P.fscale * P.fscale;
+        }
+        for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
+            const T v = hist[e];
+            if (v != T(0)) atomicAdd(&P.C[e], (double)v * cscale);
+        }
+    }
+}
+
+}  // namespace mcubes

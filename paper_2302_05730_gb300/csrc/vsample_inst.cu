@@ -1,0 +1,99 @@
+// One (precision, integrand) slice of the V-Sample kernel instances, for d = 1..16. Compiled
+// once per slice with -DMCUBES_F32=0|1 -DMCUBES_FID=0..7 so the instances build in parallel.
+#include <atomic>
+
+#include "internal.h"
+#include "vsample.cuh"
+
+#ifndef MCUBES_F32
+#error "MCUBES_F32 must be defined"
+#endif
+#ifndef MCUBES_FID
+#error "MCUBES_FID must be defined"
+#endif
+
+#if MCUBES_F32
+#define MCUBES_PREC f32
+#else
+#define MCUBES_PREC f64
+#endif
+#define MCUBES_CAT2(a, b, c) launch_vsample_##a##_##b
+#define MCUBES_CAT(a, b) MCUBES_CAT2(a, b, 0)
+#define MCUBES_LAUNCHER MCUBES_CAT(MCUBES_PREC, MCUBES_FID)
+
+namespace mcubes {
+namespace {
+
+constexpr bool kF32 = MCUBES_F32 != 0;
+constexpr int kFid = MCUBES_FID;
+
+// Per-instance launch facts, filled on first use (benign race: every writer stores the same
+// values for the same device).
+struct InstanceInfo {
+    std::atomic<int> ready{0};
+    int occ[2];   // resident blocks per SM at 256 threads, [adjust]
+};
+
+template <int D>
+int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
+{
+    static InstanceInfo info;
+    auto kern = vsample_kernel<D, kFid, kF32>;
+    const bool adjust = P.adjust != 0;
+    const size_t smem = vsample_smem_bytes<kF32>(D, adjust);
+    cudaError_t e;
+    if (!info.ready.load(std::memory_order_acquire)) {
+        const size_t smem_max = vsample_smem_bytes<kF32>(D, true);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+        if (e != cudaSuccess) return (int)e;
+        for (int a = 0; a < 2; ++a) {
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kMaxBlockThreads,
+                                                              vsample_smem_bytes<kF32>(D, a != 0));
+            if (e != cudaSuccess) return (int)e;
+            info.occ[a] = nb > 0 ? nb : 1;
+        }
+        info.ready.store(1, std::memory_order_release);
+    }
+    const int threads = req.threads;
+    int bps = req.blocks_per_sm;
+    if (bps <= 0) {
+        bps = info.occ[adjust ? 1 : 0];
+        // occupancy was computed for 256 threads; smaller blocks fit proportionally more
+        if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
+    }
+    uint64_t blocks = (uint64_t)req.num_sms * (uint64_t)bps;
+    // at least ~4 sub-cubes per thread so the per-block grid staging stays cheap
+    const uint64_t want = ((uint64_t)P.m + (uint64_t)threads * 4 - 1) / ((uint64_t)threads * 4);
+    if (want < blocks) blocks = want;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, s>>>(P);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int MCUBES_LAUNCHER(int d, const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
+{
+    switch (d) {
+    case 1: return launch_d<1>(P, req, s);
+    case 2: return launch_d<2>(P, req, s);
+    case 3: return launch_d<3>(P, req, s);
+    case 4: return launch_d<4>(P, req, s);
+    case 5: return launch_d<5>(P, req, s);
+    case 6: return launch_d<6>(P, req, s);
+    case 7: return launch_d<7>(P, req, s);
+    case 8: return launch_d<8>(P, req, s);
+    case 9: return launch_d<9>(P, req, s);
+    case 10: return launch_d<10>(P, req, s);
+    case 11: return launch_d<11>(P, req, s);
+    case 12: return launch_d<12>(P, req, s);
+    case 13: return launch_d<13>(P, req, s);
+    case 14: return launch_d<14>(P, req, s);
+    case 15: return launch_d<15>(P, req, s);
+    case 16: return launch_d<16>(P, req, s);
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mcubes

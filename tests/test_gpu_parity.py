@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA V-Sample and Rebin kernels (through the C ABI) against the CPU oracle,
+on the same seeded inputs.
+
+Tolerances (FP64 path):
+  - I: |dI| <= 1e-12 * (1/m) sum_t |I_t|. Condition-scaled, since the oscillatory family
+    changes sign.
+  - Var: |dV| <= 1e-12 V + floor. The floor is 8 eps (1/m^2) sum_t S2_t / (p (p-1)), the
+    rounding floor of S2 - S1^2/p that Algorithm 2's sum-of-squares form carries.
+  - C: 1e-12 relative per bin.
+  - Rebinned grid: 1e-13 absolute.
+FP32-eval path (point and integrand in single precision; per-cube combination and sums FP64):
+  - I and Var: 1e-5, with the same scaling.
+  - C: 1e-4 relative per bin. C is accumulated in single precision per block, with a few
+    hundred terms per bin and block.
+The bin index and the point x are decided in the same precision on both sides, so they
+match exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2302_05730_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+ALL = list(range(8))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_05730_gb300 import capi as c
+    return c
+
+
+def _params(fid, d, seed=0):
+    if fid == W.CONSTANT:
+        return W.constant_params(d, 2.5)
+    if fid == W.ADDITION:
+        return W.paper_params(fid, d)
+    return W.genz_params(fid, d, seed=seed)
+
+
+def _random_grid(d, seed):
+    rng = np.random.default_rng(seed)
+    B = np.empty((d, 501))
+    for i in range(d):
+        w = 10.0 ** rng.uniform(-3.0, 0.0, 500)
+        c = np.concatenate([[0.0], np.cumsum(w)])
+        B[i] = c / c[-1]
+        B[i, 0], B[i, -1] = 0.0, 1.0
+    return B
+
+
+# Per-sample relative error of the FP32-eval weight (single-precision point -> integrand ->
+# Jacobian, SFU exp2): a few 2^-21. Its square bounds the FP32 variance floor.
+F32_W = 2.0 ** -19
+
+
+def _tols(ref, mode):
+    """(absolute tolerance of I, relative tolerance of Var, absolute floor of Var)."""
+    m, p = ref["m"], ref["p"]
+    cI = np.abs(ref["cubeI"]).sum() / m
+    s2 = ref["cubeV"] + ref["cubeI"] ** 2 / (p - 1)          # S2_t / (p (p-1))
+    rel = 1e-12 if mode == 0 else 1e-5
+    floor = (8 * EPS if mode == 0 else 4 * F32_W ** 2) * s2.sum() / m ** 2
+    return rel * cI, rel, floor
+
+
+def _compare(gpu, ref, mode, B=None, check_grid=True):
+    tolI, rel, vfloor = _tols(ref, mode)
+    assert abs(gpu["I"] - ref["I"]) <= tolI, ("I", gpu["I"], ref["I"], tolI)
+    assert abs(gpu["Var"] - ref["Var"]) <= rel * ref["Var"] + vfloor, ("Var", gpu["Var"], ref["Var"])
+    if "C" in gpu:
+        crel = 1e-12 if mode == 0 else 1e-4
+        assert np.allclose(gpu["C"], ref["C"], rtol=crel, atol=0), \
+            ("C", np.max(np.abs(gpu["C"] - ref["C"]) / np.maximum(ref["C"], 1e-300)))
+    if check_grid and "grid" in gpu and B is not None:
+        want = oracle.rebin(B, ref["C"])
+        atol = 1e-13 if mode == 0 else 1e-6
+        assert np.allclose(gpu["grid"], want, rtol=0, atol=atol), np.max(np.abs(gpu["grid"] - want))
+
+
+# ------------------------------------------------------------------------------ Philox
+def test_philox_matches_curand_device_function_and_oracle(capi):
+    rng = np.random.default_rng(1)
+    n = 1 << 16
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [0, 0, 0, 0xFFFFFFFF]]
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    for seed in [0, 1, 0xFFFFFFFFFFFFFFFF, 0x0123456789ABCDEF]:
+        own = torch.empty_like(d_ctr)
+        ref = torch.empty_like(d_ctr)
+        capi.philox_dev(d_ctr, n, seed, 0, own)
+        capi.philox_dev(d_ctr, n, seed, 1, ref)
+        torch.cuda.synchronize()
+        a = own.cpu().numpy().view(np.uint32)
+        b = ref.cpu().numpy().view(np.uint32)
+        assert np.array_equal(a, b)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for j in list(range(4)) + list(rng.integers(0, n, 40)):
+            assert oracle.philox(ctr[j], key) == [int(v) for v in a[j]]
+
+
+# ------------------------------------------------------------------------------ one iteration
+CASES = []
+for fid in ALL:
+    for d, n in [(1, 1000), (2, 5000), (3, 30000), (5, 20000), (8, 40000)]:
+        CASES.append((fid, d, n))
+CASES += [(W.GAUSSIAN, 12, 2 * 3 ** 12), (W.C0, 16, 2 ** 17 + 7), (W.PRODUCT_PEAK, 10, 2 * 3 ** 10 + 5),
+          (W.DISCONTINUOUS, 6, 123457), (W.OSCILLATORY, 4, 31), (W.CORNER_PEAK, 2, 2),
+          (W.ADDITION, 7, 2 * 5 ** 7 + 99)]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fid,d,n", CASES)
+def test_vsample_parity(capi, fid, d, n, mode):
+    par = _params(fid, d, seed=d)
+    B = _random_grid(d, 100 + d)
+    seed, it, job = 12345 + d, 3, 0
+    gpu = capi.vsample_once(fid, par, d, n, seed, iteration=it, job=job, adjust=1, precision=mode, grid_in=B)
+    ref = oracle.vsample(fid, d, par, n, seed, it=it, job=job, mode=mode, adjust=1, B=B, per_cube=True)
+    _compare(gpu, ref, mode, B)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fid", ALL)
+def test_vsample_parity_adapted_grid(capi, fid, mode):
+    """On a grid adapted by the oracle itself (narrow bins near the peak)."""
+    d, n = 4, 60000
+    par = _params(fid, d, seed=7)
+    B = oracle.adapted_grid(fid, d, par, 20000, 3, seed=1, mode=0)
+    gpu = capi.vsample_once(fid, par, d, n, 99, iteration=5, adjust=1, precision=mode, grid_in=B)
+    ref = oracle.vsample(fid, d, par, n, 99, it=5, mode=mode, adjust=1, B=B, per_cube=True)
+    _compare(gpu, ref, mode, B)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_frozen_iteration_and_uniform_grid(capi, mode):
+    d, n, fid = 5, 77777, W.GAUSSIAN
+    par = _params(fid, d)
+    gpu = capi.vsample_once(fid, par, d, n, 5, iteration=9, job=3, adjust=0, precision=mode)
+    ref = oracle.vsample(fid, d, par, n, 5, it=9, job=3, mode=mode, adjust=0, per_cube=True)
+    assert "C" not in gpu and "grid" not in gpu
+    _compare(gpu, ref, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_constant_integrand_exact(capi, mode):
+    for d in [1, 4, 9]:
+        par = W.constant_params(d, 3.25)
+        g, m, p = capi.stratify(d, 50000)
+        r = capi.vsample_once(W.CONSTANT, par, d, 50000, 1, adjust=0, precision=mode)
+        tolI = 1e-13 if mode == 0 else 1e-6
+        assert abs(r["I"] - 3.25) <= tolI * 3.25
+        floor = (8 * EPS if mode == 0 else 4 * F32_W ** 2) * 3.25 ** 2 / ((p - 1) * m)
+        assert r["Var"] <= floor
+
+
+# ------------------------------------------------------------------------------ whole runs
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fid,d", [(W.GAUSSIAN, 3), (W.OSCILLATORY, 5), (W.PRODUCT_PEAK, 6), (W.C0, 8),
+                                   (W.CORNER_PEAK, 5), (W.DISCONTINUOUS, 4)])
+def test_integrate_parity(capi, fid, d, mode):
+    """Several adjusting and frozen iterations: the map is continuous in the grid and the bins
+    depend only on the draws, so rounding-level grid differences stay at rounding level."""
+    par = _params(fid, d, seed=11)
+    n = 100000
+    g = capi.integrate(fid, par, d, n, 6, 3, seed=4, precision=mode, return_iters=True, return_grid=True)
+    est, sig, chi2, iI, iV = oracle.integrate(fid, d, par, n, 6, 3, seed=4, mode=mode)
+    rel = 1e-10 if mode == 0 else 2e-5
+    scale = max(abs(est), sig)
+    assert abs(g["estimate"] - est) <= rel * scale, (g["estimate"], est)
+    assert math.isclose(g["error"], sig, rel_tol=rel * 100)
+    assert np.allclose(g["iters"][:, 0], iI, rtol=rel * 10, atol=rel * np.abs(iI).max())
+    assert g["samples_per_iter"] == np.prod(capi.stratify(d, n)[1:])
+
+
+def test_config1_gaussian_full_run(capi):
+    """The d = 3 Gaussian, a_i = 10, u_i = 1/2, 1e6 samples/iteration, 10 iterations (5 adjust),
+    seed 0: the GPU run equals the oracle's and the closed form lies within its error."""
+    d = 3
+    par = W.gaussian_params(d, 10.0)
+    g = capi.integrate(W.GAUSSIAN, par, d, 10 ** 6, 10, 5, 0, precision=0, return_iters=True)
+    est, sig, chi2, iI, iV = oracle.integrate(W.GAUSSIAN, d, par, 10 ** 6, 10, 5, 0, mode=0)
+    assert abs(g["estimate"] - est) <= 1e-10 * est
+    assert np.allclose(g["iters"][:, 1], iV, rtol=1e-8)
+    exact = (math.sqrt(math.pi) / 10 * math.erf(5.0)) ** 3
+    assert abs(g["estimate"] - exact) < 4 * g["error"]
+
+
+# ------------------------------------------------------------------------------ device API
+def test_device_iteration_matches_host_call(capi):
+    d, n, fid = 6, 300000, W.C0
+    par = _params(fid, d)
+    B = _random_grid(d, 3)
+    dev = torch.device("cuda")
+    g_in = torch.from_numpy(B).to(dev)
+    g_out = torch.empty_like(g_in)
+    res = torch.zeros(2, dtype=torch.float64, device=dev)
+    ws = torch.empty(capi.workspace_bytes(d) // 8 + 64, dtype=torch.float64, device=dev)
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    for mode in (0, 1):
+        capi.iteration_dev(fid, par, d, n, 8, 1, 0, 1, mode, g_in, g_out, res, None, aligned,
+                           capi.workspace_bytes(d), stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        h = capi.vsample_once(fid, par, d, n, 8, iteration=1, adjust=1, precision=mode, grid_in=B)
+        r = res.cpu().numpy()
+        assert math.isclose(r[0], h["I"], rel_tol=1e-13)
+        assert math.isclose(r[1], h["Var"], rel_tol=1e-11)
+        assert np.allclose(g_out.cpu().numpy(), h["grid"], rtol=0, atol=1e-14)
+
+
+def test_probe_outputs_match_oracle_cubes(capi):
+    d, n, fid = 5, 10 ** 6, W.PRODUCT_PEAK
+    par = _params(fid, d)
+    B = _random_grid(d, 5)
+    g, m, p = capi.stratify(d, n)
+    shift = 10
+    dev = torch.device("cuda")
+    probe = torch.full(((m >> shift) + 1, 2), -1.0, dtype=torch.float64, device=dev)
+    sums = torch.zeros(2, dtype=torch.float64, device=dev)
+    C = torch.zeros(d * 500, dtype=torch.float64, device=dev)
+    for mode in (0, 1):
+        probe.fill_(-1.0)
+        sums.zero_()
+        capi.vsample_dev(fid, par, d, n, 3, 0, 0, 1, mode, torch.from_numpy(B).to(dev), C, sums,
+                         d_probe=probe, probe_shift=shift)
+        torch.cuda.synchronize()
+        pr = probe.cpu().numpy()
+        for t in range(0, m, 1 << shift):
+            ref = oracle.vsample(fid, d, par, n, 3, it=0, mode=mode, adjust=0, B=B, t0=t, t1=t + 1, per_cube=True)
+            rel = 1e-12 if mode == 0 else 1e-5
+            I_ref, V_ref = ref["cubeI"][0], ref["cubeV"][0]
+            assert abs(pr[t >> shift, 0] - I_ref) <= rel * abs(I_ref) + 1e-300
+            vf = (8 * EPS if mode == 0 else 4 * F32_W ** 2) * (V_ref + I_ref ** 2 / (p - 1))
+            # a single cube has no averaging: FP32 differences of nearly equal weights carry
+            # the weights' own rounding, bounded by 2 |dw| |w| F32_W
+            vr = rel if mode == 0 else 4 * F32_W * math.sqrt(abs(I_ref) ** 2 / max(V_ref, 1e-300))
+            assert abs(pr[t >> shift, 1] - V_ref) <= vr * V_ref + vf
+
+
+# ------------------------------------------------------------------------------ errors
+def test_nonfinite_integrand_reported(capi):
+    d = 1
+    par = np.array([1000.0, 1.0])   # exp(1000 x) overflows for x > 0.71
+    with pytest.raises(capi.McubesError) as e:
+        capi.vsample_once(W.DISCONTINUOUS, par, d, 1000, 1, adjust=0, precision=0)
+    assert e.value.status == 6
+    with pytest.raises(capi.McubesError) as e:    # FP32-eval: its scale factor exp(1000) is rejected
+        capi.vsample_once(W.DISCONTINUOUS, par, d, 1000, 1, adjust=0, precision=1)
+    assert e.value.status == 1
+
+
+def test_invalid_arguments(capi):
+    par = np.ones(4)
+    with pytest.raises(capi.McubesError):
+        capi.vsample_once(9, par, 2, 100, 1)
+    with pytest.raises(capi.McubesError):
+        capi.vsample_once(0, par, 2, 1, 1)
+    with pytest.raises(capi.McubesError):
+        capi.integrate(0, par, 2, 100, 3, 4, 1)
+    bad = oracle.uniform_grid(2)
+    bad[0, 10] = bad[0, 9]
+    with pytest.raises(capi.McubesError):
+        capi.vsample_once(0, par, 2, 100, 1, grid_in=bad)
