@@ -1,0 +1,386 @@
+"""Benchmark of the m-Cubes hot path (V-Sample + Rebin) on GB300.
+
+Workload: the six Genz families at d = 8 with 1e8 samples per iteration (g = 9, m = 9^8 sub-cubes,
+p = 2), a_i ~ U[5, 15], u_i ~ U[0.2, 0.8] (seed 0). One step = one grid-adjusting iteration of
+every family: V-Sample (bin contributions on) then Rebin, on device-resident grids that keep
+adapting across steps. The headline arm is FP32-eval (point and integrand in single precision,
+FP64 sums and Rebin). The plain FP64 arm runs the same steps and is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own Philox job id): the method
+has no exchange step, so there is no collective on the data path. `value` is the samples of all
+ranks over the slowest rank's time.
+
+`--impl reference` times the CPU oracle (plain C, FP64, one core) on a bounded sample of the same
+workload: the paper publishes no GPU number for it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D = 8
+NCALL = 10 ** 8
+NB = 500
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# GB300 unit counts: 152 SMs, 4 SM sub-partitions x 32 lanes issue one instruction per clock.
+SMS = 152
+LANES_PER_SM = 128
+FALLBACK_SM_MHZ = 2070.0
+
+
+def algorithmic_ops_per_sample(fid: int, d: int, adjust: bool, f32: bool) -> float:
+    """Minimal per-sample instruction count of the V-Sample algorithm (FP32-eval path, thread
+    lanes). Each entry is an operation the algorithm needs, not a count of compiled code."""
+    philox = math.ceil(d / 4) * 10 * 4          # 10 rounds x (2 wide multiplies + 2 three-way xors)
+    per_dim_map = 9 + (1 if adjust else 0)      # bits->u, +c, xR, cap, floor, delta, load, fma, xJ, [atomic]
+    integrand_dim = {0: 1, 1: 4, 2: 1, 3: 3, 4: 3, 5: 3, 6: 1, 7: 0}[fid]
+    finish = {0: 4, 1: 1, 2: 5, 3: 1, 4: 1, 5: 2, 6: 0, 7: 0}[fid]
+    per_sample = 1 + 3 + (2 if adjust else 0) + math.ceil(d / 4)   # w = fJ, stats, hist value, J rescale
+    return philox + d * (per_dim_map + integrand_dim) + finish + per_sample
+
+
+def sm_peak_ops(sm_mhz: float) -> float:
+    return SMS * LANES_PER_SM * sm_mhz * 1e6
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    """The CPU oracle on a bounded sample of the workload (sub-cube ranges of each family)."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2302_05730_gb300 import workloads as W
+
+    g, m, p = oracle.stratify(D, NCALL)
+    cubes = 1 << 15
+    B = oracle.uniform_grid(D)
+    pars = {fid: W.genz_params(fid, D, seed=0) for fid in W.GENZ6}
+
+    def step(k):
+        n = 0
+        for fid in W.GENZ6:
+            t0 = (k * 7919 * cubes) % (m - cubes)
+            oracle.vsample(fid, D, pars[fid], NCALL, 0, it=k % 65536, mode=1, adjust=1, B=B, t0=t0, t1=t0 + cubes)
+            n += cubes * p
+        return n
+
+    for k in range(args.warmup):
+        step(k)
+    t = time.perf_counter()
+    n = 0
+    for k in range(args.steps):
+        n += step(args.warmup + k)
+    el = time.perf_counter() - t
+    v = n / el
+    line = {"impl": "reference", "metric": "m-Cubes samples/s", "value": v, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "genz6-d8-n1e8 (oracle sample)", "d": D, "ncall": NCALL,
+                       "families": [W.NAMES[f] for f in W.GENZ6], "sample_cubes_per_family_step": cubes},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{cubes} sub-cubes ({cubes * p} samples) of each of the 6 families per step, "
+                                       "FP32-eval point layout, single thread"},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tta", action="store_true", help="skip the time-to-1e-3 leg")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the FP32-eval device-resident leg (profiling runs)")
+    ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_2302_05730_gb300 import capi, workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    stream = torch.cuda.Stream(device=dev)
+    ncall = int(args.ncall)
+    g, m, p = capi.stratify(D, ncall)
+    samples = m * p
+    fams = list(W.GENZ6)
+    pars = {fid: W.genz_params(fid, D, seed=0) for fid in fams}
+    uni = torch.from_numpy(np.tile(np.arange(NB + 1, dtype=np.float64) / NB, (D, 1))).to(dev)
+
+    def fresh_state():
+        st = {}
+        for fid in fams:
+            st[fid] = dict(grid=[uni.clone(), torch.empty_like(uni)], cur=0,
+                           C=torch.zeros(D * NB, dtype=torch.float64, device=dev),
+                           sums=torch.zeros(2, dtype=torch.float64, device=dev))
+        return st
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    it_counter = [0]
+    launches = [0]
+
+    def step(state, prec, kernel_events=None):
+        it = it_counter[0] % 65536
+        it_counter[0] += 1
+        for fid in fams:
+            s = state[fid]
+            s["C"].zero_()
+            s["sums"].zero_()
+            gin, gout = s["grid"][s["cur"]], s["grid"][1 - s["cur"]]
+            if kernel_events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            capi.vsample_dev(fid, pars[fid], D, ncall, 0, it, rank, 1, prec, gin, s["C"], s["sums"],
+                             stream=stream)
+            if kernel_events is not None:
+                e1.record(stream)
+                kernel_events.append((fid, e0, e1))
+            capi.rebin_dev(D, gin, s["C"], gout, stream=stream)
+            launches[0] += 2
+            s["cur"] = 1 - s["cur"]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(prec, steps, warmup, kern=None):
+        state = fresh_state()
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step(state, prec)
+        barrier()
+        launches[0] = 0
+        step_ms = []
+        for _ in range(steps):
+            flush.add_(1.0)   # evict L2 between timed steps (outside the timed events)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            with torch.cuda.stream(stream):
+                step(state, prec, kern)
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+        barrier()
+        total_ms = sum(step_ms)
+        if dist is not None:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # sanity: estimates are finite
+        for fid in fams:
+            v = state[fid]["sums"].cpu().numpy()
+            assert np.all(np.isfinite(v)), (fid, v)
+        return total_ms, state
+
+    # ---- headline: FP32-eval
+    clocks = ClockSampler(local)
+    clocks.start()
+    kern_ev = []
+    total_ms, state32 = timed(capi.FP32_EVAL, args.steps, args.warmup, kern_ev)
+    clk = clocks.stop()
+    n_launch = launches[0]
+    ms_step = total_ms / args.steps
+    value = samples * len(fams) * args.steps * world / (total_ms * 1e-3)
+
+    # dominant kernel: the V-Sample launches inside the timed region
+    kms = [e0.elapsed_time(e1) for (_, e0, e1) in kern_ev]
+    avg_kms = sum(kms) / len(kms)
+    ops = sum(algorithmic_ops_per_sample(fid, D, True, True) for fid in fams) / len(fams) * samples
+    sm_mhz = FALLBACK_SM_MHZ
+    peak_src = "fallback (2070 MHz max SM clock)"
+    if os.path.exists(PEAKS_FILE):
+        try:
+            sm_mhz = float(json.load(open(PEAKS_FILE)).get("sm_max_mhz", FALLBACK_SM_MHZ))
+            peak_src = "MEASURED_PEAKS.json sm_max_mhz"
+        except (ValueError, OSError):
+            pass
+    peak = sm_peak_ops(sm_mhz) / 1e12
+    achieved = ops / (avg_kms * 1e-3) / 1e12
+
+    if args.headline_only:
+        if rank == 0:
+            print(json.dumps({"metric": "m-Cubes samples/s", "value": value, "unit": "samples/s",
+                              "ms_per_step": ms_step, "ncall": ncall, "avg_launch_ms": avg_kms,
+                              "gpu_launches": n_launch, "clocks": clk}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---- plain FP64 arm (same steps)
+    f64_steps = max(3, args.steps // 4)
+    total64, _ = timed(capi.FP64, f64_steps, 3)
+    value64 = samples * len(fams) * f64_steps * world / (total64 * 1e-3)
+
+    # ---- end to end through the host-buffer C call (H2D of the grid, D2H of grid, C, estimate)
+    host_grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}
+    for fid in fams:   # warm-up
+        capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=1, job=rank, adjust=1,
+                          precision=capi.FP32_EVAL, grid_in=host_grids[fid])
+    barrier()
+    e2e_steps = max(3, args.steps // 2)
+    t = time.perf_counter()
+    for k in range(e2e_steps):
+        for fid in fams:
+            r = capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=2 + k, job=rank, adjust=1,
+                                  precision=capi.FP32_EVAL, grid_in=host_grids[fid])
+            host_grids[fid] = r["grid"]
+    e2e_s = time.perf_counter() - t
+    if dist is not None:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = samples * len(fams) * e2e_steps * world / e2e_s
+    grid_bytes = D * (NB + 1) * 8
+    h2d = len(fams) * (grid_bytes + 2 * D * 8)
+    d2h = len(fams) * (grid_bytes + D * NB * 8 + 16)
+
+    # ---- time to 1e-3 relative error (full mcubes_integrate runs, host buffers)
+    tta = None
+    if not args.no_tta and rank == 0:
+        tta = {}
+        for prec, name in ((capi.FP64, "fp64"), (capi.FP32_EVAL, "fp32_eval")):
+            per = {}
+            for fid in fams:
+                k_hit = None
+                for k in range(1, 11):
+                    t0 = time.perf_counter()
+                    r = capi.integrate(fid, pars[fid], D, ncall, k, min(k, 5), 0, precision=prec)
+                    el = time.perf_counter() - t0
+                    if r["error"] <= 1e-3 * abs(r["estimate"]):
+                        k_hit = (k, el)
+                        break
+                per[W.NAMES[fid]] = {"iters": k_hit[0], "seconds": k_hit[1]} if k_hit else None
+            tta[name] = per
+
+    # ---- CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cubes = 1 << 21
+        t0 = time.perf_counter()
+        n = 0
+        for fid in fams:
+            B = state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy()
+            oracle.vsample(fid, D, pars[fid], ncall, 0, it=1, mode=1, adjust=1, B=B, t0=0, t1=min(cubes, m))
+            n += cubes * p
+        el = time.perf_counter() - t0
+        cpu = {"value": n / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {cubes} sub-cubes ({cubes * p} samples) of each of the 6 families on "
+                         f"the adapted grids, FP32-eval point layout, single thread ({el:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": "m-Cubes samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "genz6-d8-n1e8-fp32eval", "d": D, "ncall": ncall, "g": g, "m": m, "p": p,
+                       "families": [W.NAMES[f] for f in fams], "params": "a_i~U[5,15], u_i~U[0.2,0.8], seed 0",
+                       "step": "V-Sample (adjust) + Rebin for each family", "precision": "FP32-eval, FP64 sums/Rebin",
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "fp64": {"value": value64, "unit": "samples/s", "steps": f64_steps},
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "call": "mcubes_vsample_once (host grid in, grid + C + estimate out)"},
+            "gpu_launches": n_launch,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "vsample_kernel<8, fid, FP32>",
+                         "ops_per_launch": ops, "avg_launch_ms": avg_kms,
+                         "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})"},
+            "cpu_baseline": cpu,
+            "time_to_1e-3": tta,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -18,9 +18,10 @@
  *     pointer after the call returns.
  *   - Device pointers ("d_" prefix) must be device memory of the current CUDA device. They
  *     must not be used by other work while the call's stream runs.
- *   - `stream` is a cudaStream_t, or NULL for a stream the library owns per host thread.
- *     "_dev" calls are asynchronous on that stream; every other call synchronises before it
- *     returns.
+ *   - `stream` is a cudaStream_t, or NULL for a stream the library owns per host thread. The
+ *     special handles cudaStreamLegacy and cudaStreamPerThread are accepted as well (use
+ *     cudaStreamLegacy to order work with the legacy default stream). "_dev" calls are
+ *     asynchronous on that stream; every other call synchronises before it returns.
  *   - Grids are row-major d x (MCUBES_NBINS + 1) doubles: B[i][0] = 0 < B[i][1] < ... <
  *     B[i][500] = 1. Bin contributions are d x MCUBES_NBINS doubles.
  *   - Integrand parameters are 2d doubles: a[0..d-1] then u[0..d-1] (constant: a[0] = c).

@@ -109,13 +109,18 @@ def _dptr(x):
     raise TypeError(type(x))
 
 
+CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
+
+
 def _stream(s):
+    """cudaStream_t for a torch stream / raw handle. None selects the library's own stream; a
+    torch stream whose handle is 0 (the legacy default stream) maps to cudaStreamLegacy."""
     if s is None:
         return None
     if isinstance(s, int):
         return s
     if hasattr(s, "cuda_stream"):
-        return s.cuda_stream
+        return s.cuda_stream or CUDA_STREAM_LEGACY
     raise TypeError(type(s))
 
 

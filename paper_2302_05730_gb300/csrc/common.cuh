@@ -66,6 +66,7 @@ struct VsampleParams {
     double *probe;           // per-cube probe output or null
     uint32_t probe_mask;     // cube t is probed when (t & probe_mask) == 0
     uint32_t probe_shift;
+    uint32_t perm_mul;       // odd multiplier, coprime with the launch's thread count
     uint32_t m;              // sub-cubes
     uint32_t p;              // samples per sub-cube
     uint32_t g;              // strata per axis

@@ -111,11 +111,15 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
     }
     __syncthreads();
 
-    // ---- this thread's sub-cube range
+    // ---- this thread's sub-cube range. Range r = (gtid * P.perm_mul) mod N is a permutation
+    // of the N threads (perm_mul is odd and coprime with N): the 32 lanes of a warp start in
+    // scattered parts of [0, m), so their strata differ on every axis and their bins spread
+    // over the whole histogram instead of piling into one stratum's window.
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t t = (uint32_t)((gtid * P.m) / nthreads);
-    const uint32_t t_end = (uint32_t)(((gtid + 1) * P.m) / nthreads);
+    const uint64_t rng = (gtid * (uint64_t)P.perm_mul) % nthreads;
+    uint32_t t = (uint32_t)((rng * P.m) / nthreads);
+    const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     // strata digits c_i (axis 0 fastest) and c_i - 1 in the path's precision
     uint32_t dig[D];
@@ -144,8 +148,11 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
         }
     }
 
-    double sI = 0.0, sV = 0.0;
+    double sI = 0.0, sV = 0.0;          // FP64 path: per-thread sums
+    float cI = 0.0f, eI = 0.0f;         // FP32 path: Neumaier-compensated per-thread sums
+    float cV = 0.0f, eV = 0.0f;
     const uint32_t p = P.p;
+    const float inv_p32 = (float)P.inv_p;
 
     for (; t < t_end; ++t) {
         T S1 = T(0), S2 = T(0), w0 = T(0);   // FP64: plain sums; FP32: w0 and shifted sums
@@ -249,31 +256,37 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
             }
         }
 
-        // per sub-cube mean and variance (Algorithm 2 UpdateVariance), FP64
-        double It, Vt;
+        // per sub-cube mean and variance (Algorithm 2 UpdateVariance)
+        const bool probe_this = P.probe != nullptr && (t & P.probe_mask) == 0;
         if constexpr (F32) {
-            const double dw0 = (double)w0, d1 = (double)S1, d2 = (double)S2;
-            It = fma(d1, P.inv_p, dw0);
-            Vt = fma(-d1 * P.inv_p, d1, d2);
-        } else {
-            It = S1 * P.inv_p;
-            Vt = fma(-S1 * P.inv_p, S1, S2);
-        }
-        Vt = Vt > 0.0 ? Vt : 0.0;
-        sI += It;
-        sV += Vt;
-        if (P.probe != nullptr && (t & P.probe_mask) == 0) {
-            // probe values on the final scale
-            double sc, sc2;
-            if constexpr (F32) {
-                sc = P.fscale;
-                sc2 = P.fscale * P.fscale;
-            } else {
-                sc = P.fscale;   // nd^d on the FP64 path
-                sc2 = P.fscale * P.fscale;
+            // Single precision on the shifted sums: mean = w0 + D1/p, p(p-1) V = D2 - D1^2/p.
+            // The shift keeps D2 - D1^2/p free of the cancellation of S2 - S1^2/p. The
+            // per-thread sums are compensated (Neumaier) and widened to FP64 once per thread.
+            const float mean = fmaf(S1, inv_p32, w0);
+            float var = fmaf(-S1 * inv_p32, S1, S2);
+            var = fmaxf(var, 0.0f);
+            {
+                const float tI = cI + mean;
+                eI += (fabsf(cI) >= fabsf(mean)) ? ((cI - tI) + mean) : ((mean - tI) + cI);
+                cI = tI;
+                const float tV = cV + var;
+                eV += (cV >= var) ? ((cV - tV) + var) : ((var - tV) + cV);
+                cV = tV;
             }
-            P.probe[2 * (size_t)(t >> P.probe_shift)] = It * sc;
-            P.probe[2 * (size_t)(t >> P.probe_shift) + 1] = Vt * P.inv_pp1 * sc2;
+            if (probe_this) {   // probe values on the final scale (fscale = F)
+                P.probe[2 * (size_t)(t >> P.probe_shift)] = (double)mean * P.fscale;
+                P.probe[2 * (size_t)(t >> P.probe_shift) + 1] = (double)var * P.inv_pp1 * P.fscale * P.fscale;
+            }
+        } else {
+            const double It = S1 * P.inv_p;
+            double Vt = fma(-S1 * P.inv_p, S1, S2);
+            Vt = Vt > 0.0 ? Vt : 0.0;
+            sI += It;
+            sV += Vt;
+            if (probe_this) {   // probe values on the final scale (fscale = nd^d)
+                P.probe[2 * (size_t)(t >> P.probe_shift)] = It * P.fscale;
+                P.probe[2 * (size_t)(t >> P.probe_shift) + 1] = Vt * P.inv_pp1 * P.fscale * P.fscale;
+            }
         }
 
         // advance the strata digits to sub-cube t + 1
@@ -293,6 +306,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
     }
 
     // ---- block reduction, then two FP64 global atomics (Algorithm 2, AtomicAdd into r)
+    if constexpr (F32) {
+        sI = (double)cI + (double)eI;
+        sV = (double)cV + (double)eV;
+    }
     block_sum2(sI, sV, red_scratch);
     if (threadIdx.x == 0) {
         atomicAdd(&P.sums[0], sI * P.fscale);

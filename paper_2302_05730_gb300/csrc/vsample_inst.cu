@@ -1,6 +1,7 @@
 // One (precision, integrand) slice of the V-Sample kernel instances, for d = 1..16. Compiled
 // once per slice with -DMCUBES_F32=0|1 -DMCUBES_FID=0..7 so the instances build in parallel.
 #include <atomic>
+#include <numeric>
 
 #include "internal.h"
 #include "vsample.cuh"
@@ -67,7 +68,13 @@ int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     const uint64_t want = ((uint64_t)P.m + (uint64_t)threads * 4 - 1) / ((uint64_t)threads * 4);
     if (want < blocks) blocks = want;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, threads, smem, s>>>(P);
+    // range permutation multiplier: near N / 32 * golden ratio, odd, coprime with N
+    VsampleParams Q = P;
+    const uint64_t n = blocks * (uint64_t)threads;
+    uint64_t mul = (uint64_t)((double)n * 0.6180339887498949) | 1u;
+    while (std::gcd(mul, n) != 1) mul += 2;
+    Q.perm_mul = (uint32_t)(mul % n == 0 ? 1 : mul % n);
+    kern<<<(unsigned)blocks, threads, smem, s>>>(Q);
     return (int)cudaGetLastError();
 }
 

@@ -6,12 +6,22 @@ Tolerances (FP64 path):
     changes sign.
   - Var: |dV| <= 1e-12 V + floor. The floor is 8 eps (1/m^2) sum_t S2_t / (p (p-1)), the
     rounding floor of S2 - S1^2/p that Algorithm 2's sum-of-squares form carries.
-  - C: 1e-12 relative per bin.
+  - C: 1e-12 relative per bin, plus 1e-14 of the axis' mean bin. The floor covers bins whose
+    few weights sit near a zero of the oscillatory family, where libm cos and CUDA cos
+    differ in relative terms.
   - Rebinned grid: 1e-13 absolute.
 FP32-eval path (point and integrand in single precision; per-cube combination and sums FP64):
   - I and Var: 1e-5, with the same scaling.
-  - C: 1e-4 relative per bin. C is accumulated in single precision per block, with a few
-    hundred terms per bin and block.
+  - C: 1e-4 relative per bin, plus 1e-6 of the axis' mean bin. C is accumulated in single
+    precision per block. Bins whose weights underflow single precision, or sit near a zero
+    of the oscillatory family, fall under the floor. Rebin only sees C_k / sum C.
+  - Rebinned grid: the Rebin kernel is FP64 in both modes and is checked on the GPU's own C
+    (1e-13). Bins whose contribution underflows single precision are exactly zero on the GPU.
+    The VEGAS damping still gives a bin with rho = 1e-300 the weight (1/ln(1/rho))^1.5 ~ 5e-5,
+    so the grid refined from the oracle's FP64 C can differ visibly in such tails.
+  - Whole runs: the grids are refined from single-precision bin contributions, so the two
+    runs sample slightly different grids. The estimates then agree to a fraction of their
+    statistical error (0.2 sigma), not to 1e-5.
 The bin index and the point x are decided in the same precision on both sides, so they
 match exactly.
 """
@@ -78,13 +88,17 @@ def _compare(gpu, ref, mode, B=None, check_grid=True):
     assert abs(gpu["I"] - ref["I"]) <= tolI, ("I", gpu["I"], ref["I"], tolI)
     assert abs(gpu["Var"] - ref["Var"]) <= rel * ref["Var"] + vfloor, ("Var", gpu["Var"], ref["Var"])
     if "C" in gpu:
-        crel = 1e-12 if mode == 0 else 1e-4
-        assert np.allclose(gpu["C"], ref["C"], rtol=crel, atol=0), \
-            ("C", np.max(np.abs(gpu["C"] - ref["C"]) / np.maximum(ref["C"], 1e-300)))
+        crel, cfloor = (1e-12, 1e-14) if mode == 0 else (1e-4, 1e-6)
+        tol = crel * ref["C"] + cfloor * ref["C"].mean(axis=1, keepdims=True)
+        err = np.abs(gpu["C"] - ref["C"])
+        assert np.all(err <= tol), ("C", float(np.max(err / tol)), float(np.max(err / np.maximum(ref["C"], 1e-300))))
     if check_grid and "grid" in gpu and B is not None:
-        want = oracle.rebin(B, ref["C"])
-        atol = 1e-13 if mode == 0 else 1e-6
-        assert np.allclose(gpu["grid"], want, rtol=0, atol=atol), np.max(np.abs(gpu["grid"] - want))
+        # Rebin kernel (FP64 in both modes) against the oracle's Rebin of the same C
+        same = oracle.rebin(B, gpu["C"])
+        assert np.allclose(gpu["grid"], same, rtol=0, atol=1e-13), np.max(np.abs(gpu["grid"] - same))
+        if mode == 0:
+            want = oracle.rebin(B, ref["C"])
+            assert np.allclose(gpu["grid"], want, rtol=0, atol=1e-12), np.max(np.abs(gpu["grid"] - want))
 
 
 # ------------------------------------------------------------------------------ Philox
@@ -174,11 +188,18 @@ def test_integrate_parity(capi, fid, d, mode):
     n = 100000
     g = capi.integrate(fid, par, d, n, 6, 3, seed=4, precision=mode, return_iters=True, return_grid=True)
     est, sig, chi2, iI, iV = oracle.integrate(fid, d, par, n, 6, 3, seed=4, mode=mode)
-    rel = 1e-10 if mode == 0 else 2e-5
-    scale = max(abs(est), sig)
-    assert abs(g["estimate"] - est) <= rel * scale, (g["estimate"], est)
-    assert math.isclose(g["error"], sig, rel_tol=rel * 100)
-    assert np.allclose(g["iters"][:, 0], iI, rtol=rel * 10, atol=rel * np.abs(iI).max())
+    if mode == 0:
+        rel = 1e-10
+        assert abs(g["estimate"] - est) <= rel * max(abs(est), sig), (g["estimate"], est)
+        assert math.isclose(g["error"], sig, rel_tol=1e-8)
+        assert np.allclose(g["iters"][:, 0], iI, rtol=1e-9, atol=1e-10 * np.abs(iI).max())
+    else:
+        assert abs(g["estimate"] - est) <= 0.2 * sig + 1e-5 * abs(est), (g["estimate"], est, sig)
+        assert math.isclose(g["error"], sig, rel_tol=0.05)
+        # the first iteration samples the same (uniform) grid: per-iteration tolerance,
+        # condition-scaled by (1/m) sum |I_t| of that iteration
+        r0 = oracle.vsample(fid, d, par, n, 4, it=0, mode=1, adjust=0, per_cube=True)
+        assert abs(g["iters"][0, 0] - iI[0]) <= 1e-5 * np.abs(r0["cubeI"]).mean()
     assert g["samples_per_iter"] == np.prod(capi.stratify(d, n)[1:])
 
 
@@ -213,9 +234,10 @@ def test_device_iteration_matches_host_call(capi):
         torch.cuda.synchronize()
         h = capi.vsample_once(fid, par, d, n, 8, iteration=1, adjust=1, precision=mode, grid_in=B)
         r = res.cpu().numpy()
-        assert math.isclose(r[0], h["I"], rel_tol=1e-13)
-        assert math.isclose(r[1], h["Var"], rel_tol=1e-11)
-        assert np.allclose(g_out.cpu().numpy(), h["grid"], rtol=0, atol=1e-14)
+        # same kernel and inputs; only the order of the floating-point atomics differs
+        assert math.isclose(r[0], h["I"], rel_tol=1e-13 if mode == 0 else 1e-9)
+        assert math.isclose(r[1], h["Var"], rel_tol=1e-11 if mode == 0 else 1e-7)
+        assert np.allclose(g_out.cpu().numpy(), h["grid"], rtol=0, atol=1e-14 if mode == 0 else 1e-8)
 
 
 def test_probe_outputs_match_oracle_cubes(capi):
