@@ -72,7 +72,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -104,6 +104,21 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (identity without torch.distributed)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_job(rank: int) -> int:
+    """Philox job id (counter word 3) of a replica: every rank draws an independent stream."""
+    return rank
 
 
 # ------------------------------------------------------------------------------ reference arm
@@ -152,7 +167,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -182,6 +197,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     stream = torch.cuda.Stream(device=dev)
+    job = replica_job(rank)
     ncall = int(args.ncall)
     g, m, p = capi.stratify(D, ncall)
     samples = m * p
@@ -213,7 +229,7 @@ def main():
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            capi.vsample_dev(fid, pars[fid], D, ncall, 0, it, rank, 1, prec, gin, s["C"], s["sums"],
+            capi.vsample_dev(fid, pars[fid], D, ncall, 0, it, job, 1, prec, gin, s["C"], s["sums"],
                              stream=stream)
             if kernel_events is not None:
                 e1.record(stream)
@@ -247,11 +263,7 @@ def main():
             b.synchronize()
             step_ms.append(a.elapsed_time(b))
         barrier()
-        total_ms = sum(step_ms)
-        if dist is not None:
-            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(step_ms), dist, dev)
         # sanity: estimates are finite
         for fid in fams:
             v = state[fid]["sums"].cpu().numpy()
@@ -300,21 +312,17 @@ def main():
     # ---- end to end through the host-buffer C call (H2D of the grid, D2H of grid, C, estimate)
     host_grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}
     for fid in fams:   # warm-up
-        capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=1, job=rank, adjust=1,
+        capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=1, job=job, adjust=1,
                           precision=capi.FP32_EVAL, grid_in=host_grids[fid])
     barrier()
     e2e_steps = max(3, args.steps // 2)
     t = time.perf_counter()
     for k in range(e2e_steps):
         for fid in fams:
-            r = capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=2 + k, job=rank, adjust=1,
+            r = capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=2 + k, job=job, adjust=1,
                                   precision=capi.FP32_EVAL, grid_in=host_grids[fid])
             host_grids[fid] = r["grid"]
-    e2e_s = time.perf_counter() - t
-    if dist is not None:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
     e2e_value = samples * len(fams) * e2e_steps * world / e2e_s
     grid_bytes = D * (NB + 1) * 8
     h2d = len(fams) * (grid_bytes + 2 * D * 8)

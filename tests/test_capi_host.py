@@ -1,0 +1,116 @@
+"""The C ABI without a GPU: the library loads, exports every function include/mcubes.h declares,
+and its host-side logic (stratification, argument checks, status codes) behaves as documented.
+None of these calls reaches a CUDA kernel."""
+import ctypes
+import importlib
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_05730_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2302_05730_gb300", "libmcubes.so")
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not os.path.exists(LIB):
+        from paper_2302_05730_gb300.build import build
+        build()
+    from paper_2302_05730_gb300 import capi as c
+    return c
+
+
+def test_library_exports_every_declared_function(capi):
+    names = capi.header_functions()
+    assert len(names) >= 12
+    raw = ctypes.CDLL(LIB)
+    for n in names:
+        assert hasattr(raw, n), n
+
+
+def test_stratify_matches_oracle(capi):
+    rng = np.random.default_rng(0)
+    for d in range(1, 17):
+        for n in [2, 3, 100, 10 ** 4, 10 ** 6, 10 ** 8] + list(rng.integers(2, 10 ** 9, 5)):
+            try:
+                want = oracle.stratify(d, int(n))
+            except ValueError:
+                with pytest.raises(capi.McubesError):
+                    capi.stratify(d, int(n))
+                continue
+            assert capi.stratify(d, int(n)) == want, (d, n)
+
+
+def test_status_strings(capi):
+    for s in range(9):
+        assert capi.status_string(s)
+    assert "unknown" in capi.status_string(99)
+
+
+def _status(call):
+    try:
+        call()
+    except Exception as e:  # noqa: BLE001
+        return getattr(e, "status", None)
+    return 0
+
+
+def test_argument_checks_return_status_codes(capi):
+    par = W.genz_params(W.GAUSSIAN, 3)
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 0, 1000, 3, 1, 0)) == 2
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, np.ones(34), 17, 1000, 3, 1, 0)) == 2
+    assert _status(lambda: capi.integrate(8, par, 3, 1000, 3, 1, 0)) == 3
+    assert _status(lambda: capi.integrate(-1, par, 3, 1000, 3, 1, 0)) == 3
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 3, 1, 3, 1, 0)) == 1       # ncall < 2
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 3, 1000, 0, 0, 0)) == 1    # itmax < 1
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 3, 1000, 3, 4, 0)) == 1    # iter_adjust > itmax
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 3, 1000, 3, 1, 0, precision=2)) == 1
+    bad = par.copy()
+    bad[1] = np.nan
+    assert _status(lambda: capi.integrate(W.GAUSSIAN, bad, 3, 1000, 3, 1, 0)) == 1
+    # FP32-eval needs g <= 2^24
+    assert _status(lambda: capi.vsample_once(W.GAUSSIAN, W.genz_params(W.GAUSSIAN, 1), 1, 2 ** 26, 0,
+                                             precision=1)) == 1
+    # grids must run 0 < ... < 1
+    g = oracle.uniform_grid(3)
+    g[1, 7] = g[1, 8]
+    assert _status(lambda: capi.vsample_once(W.GAUSSIAN, par, 3, 1000, 0, grid_in=g)) == 1
+    # device calls: workspace, aliasing and probe checks happen before any CUDA call
+    assert _status(lambda: capi.iteration_dev(W.GAUSSIAN, par, 3, 1000, 0, 0, 0, 1, 0, 1 << 20, 2 << 20,
+                                              3 << 20, None, 4 << 20, 16)) == 8
+    assert _status(lambda: capi.iteration_dev(W.GAUSSIAN, par, 3, 1000, 0, 0, 0, 1, 0, 1 << 20, 2 << 20,
+                                              3 << 20, None, (4 << 20) + 8, 1 << 20)) == 8
+    assert _status(lambda: capi.iteration_dev(W.GAUSSIAN, par, 3, 1000, 0, 0, 0, 1, 0, 1 << 20, 1 << 20,
+                                              3 << 20, None, 4 << 20, 1 << 20)) == 1
+    assert _status(lambda: capi.vsample_dev(W.GAUSSIAN, par, 3, 1000, 0, 0, 0, 1, 0, 1 << 20, None,
+                                            3 << 20)) == 1
+    assert _status(lambda: capi.vsample_dev(W.GAUSSIAN, par, 3, 1000, 0, 0, 0, 0, 0, 1 << 20, None,
+                                            3 << 20, d_probe=5 << 20, probe_shift=32)) == 1
+    assert _status(lambda: capi.rebin_dev(3, 1 << 20, 2 << 20, 1 << 20)) == 1
+    assert _status(lambda: capi.rebin_dev(0, 1 << 20, 2 << 20, 3 << 20)) == 2
+
+
+def test_workspace_bytes(capi):
+    assert capi.workspace_bytes(0) == 0 and capi.workspace_bytes(17) == 0
+    for d in range(1, 17):
+        b = capi.workspace_bytes(d)
+        assert b % 256 == 0 and b >= d * 500 * 8 + 16
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2302_05730_gb300._capi as mod
+    src = open(mod.__file__).read()
+    fake = tmp_path / "_capi_probe.py"
+    fake.write_text(src.replace('LIB_PATH = os.path.join(_HERE, "libmcubes.so")',
+                                'LIB_PATH = os.path.join(_HERE, "missing-libmcubes.so")'))
+    sys.path.insert(0, str(tmp_path))
+    try:
+        with pytest.raises(ImportError):
+            importlib.import_module("_capi_probe")
+    finally:
+        sys.path.remove(str(tmp_path))
