@@ -184,6 +184,31 @@ int mcubes_iteration_dev(int integrand_id, const double *params, int d, int64_t 
                          const double *d_prev, void *d_workspace, size_t workspace_bytes,
                          const mcubes_tuning *tune, void *stream);
 
+/* mcubes_iteration_dev without caller scratch. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they run an iteration. Examples:
+ * an application whose memory pool already owns the whole device, or a latency-critical loop
+ * where cudaMalloc/cudaFree would stall or synchronise the device.
+ *   - The scratch (bin-contribution accumulator and sums) is a fixed array inside the library
+ *     of mcubes_static_scratch_bytes() bytes (64,256: enough for d <= 16). Every GPU that loads
+ *     the library holds it until the process exits.
+ *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, once
+ *     per device, with that device current). Make that first call before any stream capture.
+ *   - Every call shares the one array per device. The call clears it before use, but two calls
+ *     whose work overlaps on the GPU (different streams, no ordering) race on it.
+ *   - `stream` NULL means the legacy default stream here, not the library's own stream (creating
+ *     that stream would allocate).
+ * Arguments and results as mcubes_iteration_dev.
+ * Errors: as mcubes_iteration_dev; WORKSPACE if the iteration needs more scratch than the array
+ * holds; CUDA if the address lookup fails. */
+int mcubes_iteration_dev_static(int integrand_id, const double *params, int d, int64_t ncall,
+                                uint64_t seed, int iteration, uint32_t job, int adjust, int precision,
+                                const double *d_grid_in, double *d_grid_out, double *d_result,
+                                const double *d_prev, const mcubes_tuning *tune, void *stream);
+
+/* Size in bytes of the fixed scratch array behind mcubes_iteration_dev_static. */
+size_t mcubes_static_scratch_bytes(void);
+
 /* Philox4x32-10 on the device, for checking the generator. out[4j..4j+3] = Philox(ctr[4j..4j+3],
  * key = (seed mod 2^32, seed >> 32)) for j < n.
  *   impl 0: the library's own generator (the one the sampler uses).

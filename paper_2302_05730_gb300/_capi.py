@@ -68,6 +68,9 @@ def _load():
         "mcubes_workspace_bytes": (ctypes.c_size_t, [i32]),
         "mcubes_iteration_dev": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, vp, vp, vp, vp, vp,
                                        ctypes.c_size_t, ctypes.POINTER(Tuning), vp]),
+        "mcubes_iteration_dev_static": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, vp, vp, vp, vp,
+                                              ctypes.POINTER(Tuning), vp]),
+        "mcubes_static_scratch_bytes": (ctypes.c_size_t, []),
         "mcubes_philox_dev": (i32, [vp, u64, u64, i32, vp, vp]),
         "mcubes_status_string": (ctypes.c_char_p, [i32]),
         "mcubes_last_cuda_error": (i32, []),
@@ -228,6 +231,22 @@ def iteration_dev(fid, params, d, ncall, seed, iteration, job, adjust, precision
                                    _dptr(d_prev), _dptr(d_workspace), int(workspace_bytes), _tune(tune),
                                    _stream(stream))
     _check(st, "iteration_dev")
+
+
+def iteration_dev_static(fid, params, d, ncall, seed, iteration, job, adjust, precision, d_grid_in,
+                         d_grid_out, d_result, d_prev=None, tune=None, stream=None):
+    """mcubes_iteration_dev with the library's fixed scratch array: the call allocates no device
+    memory, for callers that cannot allocate at that point. Calls that overlap on the GPU share,
+    and race on, that one array."""
+    par, pp = _hd(params)
+    st = _lib.mcubes_iteration_dev_static(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
+                                          int(adjust), precision, _dptr(d_grid_in), _dptr(d_grid_out),
+                                          _dptr(d_result), _dptr(d_prev), _tune(tune), _stream(stream))
+    _check(st, "iteration_dev_static")
+
+
+def static_scratch_bytes() -> int:
+    return int(_lib.mcubes_static_scratch_bytes())
 
 
 def philox_dev(d_ctr, n, seed, impl, d_out, stream=None):

@@ -1,0 +1,75 @@
+"""The scratch-free iteration entry point (mcubes_iteration_dev_static).
+
+Some callers cannot allocate device memory when they run an iteration: a host application whose
+memory pool owns the whole device, or a latency-critical loop where cudaMalloc/cudaFree would stall
+or synchronise the device. For them the library keeps one fixed scratch array per GPU. This test
+checks that the scratch-free call gives the same result as mcubes_iteration_dev with caller
+scratch, on two calls in a row (the array keeps the previous call's contents, so the second call
+proves it is cleared).
+
+The file name sorts last, so a run that stops at the first failure has already run every other
+test. It also passes when run alone.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_05730_gb300 import capi as c
+    return c
+
+
+def _grid(d, seed):
+    rng = np.random.default_rng(seed)
+    B = np.empty((d, 501))
+    for i in range(d):
+        c = np.concatenate([[0.0], np.cumsum(10.0 ** rng.uniform(-2.0, 0.0, 500))])
+        B[i] = c / c[-1]
+        B[i, 0], B[i, -1] = 0.0, 1.0
+    return B
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_static_scratch_iteration_matches_caller_scratch(capi, mode):
+    from paper_2302_05730_gb300 import workloads as W
+
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    assert capi.static_scratch_bytes() >= capi.workspace_bytes(16)
+    for call, (fid, d, n) in enumerate([(W.GAUSSIAN, 8, 2_000_000), (W.C0, 5, 700_001)]):
+        par = W.genz_params(fid, d, seed=3)
+        g_in = torch.from_numpy(_grid(d, 10 + call)).to(dev)
+        ref_out = torch.empty_like(g_in)
+        out = torch.empty_like(g_in)
+        ref_res = torch.zeros(2, dtype=torch.float64, device=dev)
+        res = torch.zeros(2, dtype=torch.float64, device=dev)
+        nbytes = capi.workspace_bytes(d)
+        ws = torch.empty(nbytes // 8 + 64, dtype=torch.float64, device=dev)
+        aligned = (ws.data_ptr() + 255) // 256 * 256
+        capi.iteration_dev(fid, par, d, n, 5, 2, 0, 1, mode, g_in, ref_out, ref_res, None, aligned, nbytes,
+                           stream=stream)
+        capi.iteration_dev_static(fid, par, d, n, 5, 2, 0, 1, mode, g_in, out, res, stream=stream)
+        torch.cuda.synchronize()
+        a, b = ref_res.cpu().numpy(), res.cpu().numpy()
+        # same kernels and inputs; only the order of floating-point atomics differs
+        assert math.isclose(a[0], b[0], rel_tol=1e-13 if mode == 0 else 1e-9), (a, b)
+        assert math.isclose(a[1], b[1], rel_tol=1e-11 if mode == 0 else 1e-7), (a, b)
+        assert np.allclose(ref_out.cpu().numpy(), out.cpu().numpy(), rtol=0, atol=1e-14 if mode == 0 else 1e-8)
+
+
+def test_static_scratch_rejects_out_of_range(capi):
+    dev = torch.device("cuda")
+    g = torch.zeros((17, 501), dtype=torch.float64, device=dev)
+    r = torch.zeros(2, dtype=torch.float64, device=dev)
+    with pytest.raises(capi.McubesError) as e:
+        capi.iteration_dev_static(3, np.ones(34), 17, 1000, 1, 0, 0, 1, 0, g, torch.empty_like(g), r)
+    assert e.value.status == 2   # UNSUPPORTED_DIM: more than the array's 16 dimensions
