@@ -209,6 +209,58 @@ int mcubes_iteration_dev_static(int integrand_id, const double *params, int d, i
 /* Size in bytes of the fixed scratch array behind mcubes_iteration_dev_static. */
 size_t mcubes_static_scratch_bytes(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches of independent integrations (the target's batched form; the paper runs one
+ * integration at a time). Every job runs mcubes_integrate's iteration schedule, all jobs
+ * together: each iteration launches one persistent V-Sample kernel per (d, integrand) class and
+ * one Rebin kernel for all (job, axis) pairs. The whole schedule is captured once into a CUDA
+ * graph and launched as one graph. Job j draws with Philox counter word 3 = j and key = its
+ * seed, so it reproduces mcubes_vsample_once(..., job = j) iteration by iteration.
+ * --------------------------------------------------------------------------------------- */
+typedef struct mcubes_job {
+    int32_t integrand_id;
+    int32_t d;                 /* 1..MCUBES_DMAX */
+    int64_t ncall;             /* samples per iteration (>= 2) */
+    const double *params;      /* 2d doubles (host), copied */
+    uint64_t seed;
+} mcubes_job;
+
+/* Launch shape of the batched V-Sample kernel per dimension d (index d; entry 0 unused).
+ * Zero entries take the defaults (256 threads, 4 sub-cubes per thread per tile, block-private
+ * histogram). A tile is block_threads x cubes_per_thread consecutive sub-cubes of one job.
+ * hist_mode 0: block-private shared-memory histogram, flushed once per job and block.
+ * hist_mode 1: FP64 atomics straight into the job's global bin contributions. */
+typedef struct mcubes_batch_tuning {
+    int32_t block_threads[MCUBES_DMAX + 1];
+    int32_t cubes_per_thread[MCUBES_DMAX + 1];
+    int32_t hist_mode[MCUBES_DMAX + 1];
+} mcubes_batch_tuning;
+
+/* Integrate n_jobs independent problems together on the current device.
+ *   itmax, iter_adjust: as mcubes_integrate, shared by all jobs.
+ *   precision: MCUBES_FP64 or MCUBES_FP32_EVAL.
+ *   tune: NULL for defaults, or the output of mcubes_tune_batch.
+ *   stream: cudaStream_t the work is ordered after and before (NULL: the library stream). The
+ *     graph itself runs on a library stream.
+ *   out: n_jobs results.
+ *   iter_out: NULL or n_jobs x itmax x 2 doubles (I_it, Var_it), job-major.
+ * Device memory for grids, bin contributions and sums is allocated for the call and freed before
+ * it returns. Synchronous.
+ * Errors: INVALID_ARG (n_jobs < 1, NULL jobs/out, a job's arguments as mcubes_integrate_ex),
+ * UNSUPPORTED_DIM, UNKNOWN_INTEGRAND, ALLOC, CUDA, NONFINITE (a job's estimate is not finite; the
+ * other jobs' results are still written, and each result's status says which failed). */
+int mcubes_integrate_batch(int n_jobs, const mcubes_job *jobs, int itmax, int iter_adjust, int precision,
+                           const mcubes_batch_tuning *tune, void *stream, mcubes_result *out,
+                           double *iter_out);
+
+/* Autotuner of the batched V-Sample kernel. For every dimension present in the batch, it times
+ * one grid-adjusting V-Sample pass over that dimension's jobs on the device. Candidates:
+ * block_threads in {128, 256}, cubes_per_thread in {1, 2, 4, 8, 16}, hist_mode in {0, 1}. The
+ * fastest of each goes into *out; dimensions not present keep zeros (defaults). Synchronous;
+ * allocates and frees its own device memory.
+ * Errors: as mcubes_integrate_batch. */
+int mcubes_tune_batch(int n_jobs, const mcubes_job *jobs, int precision, mcubes_batch_tuning *out);
+
 /* Philox4x32-10 on the device, for checking the generator. out[4j..4j+3] = Philox(ctr[4j..4j+3],
  * key = (seed mod 2^32, seed >> 32)) for j < n.
  *   impl 0: the library's own generator (the one the sampler uses).

@@ -49,6 +49,21 @@ class Tuning(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("integrand_id", ctypes.c_int32), ("d", ctypes.c_int32), ("ncall", ctypes.c_int64),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32 * (DMAX + 1)),
+                ("cubes_per_thread", ctypes.c_int32 * (DMAX + 1)),
+                ("hist_mode", ctypes.c_int32 * (DMAX + 1))]
+
+    def as_dict(self):
+        return {d: dict(block_threads=self.block_threads[d], cubes_per_thread=self.cubes_per_thread[d],
+                        hist_mode=self.hist_mode[d]) for d in range(1, DMAX + 1) if self.block_threads[d]}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libmcubes.so is not built ({LIB_PATH}); run "
@@ -71,6 +86,9 @@ def _load():
         "mcubes_iteration_dev_static": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, vp, vp, vp, vp,
                                               ctypes.POINTER(Tuning), vp]),
         "mcubes_static_scratch_bytes": (ctypes.c_size_t, []),
+        "mcubes_integrate_batch": (i32, [i32, ctypes.POINTER(Job), i32, i32, i32, ctypes.POINTER(BatchTuning), vp,
+                                         ctypes.POINTER(Result), dp]),
+        "mcubes_tune_batch": (i32, [i32, ctypes.POINTER(Job), i32, ctypes.POINTER(BatchTuning)]),
         "mcubes_philox_dev": (i32, [vp, u64, u64, i32, vp, vp]),
         "mcubes_status_string": (ctypes.c_char_p, [i32]),
         "mcubes_last_cuda_error": (i32, []),
@@ -247,6 +265,50 @@ def iteration_dev_static(fid, params, d, ncall, seed, iteration, job, adjust, pr
 
 def static_scratch_bytes() -> int:
     return int(_lib.mcubes_static_scratch_bytes())
+
+
+def _jobs(jobs):
+    """ctypes job array from dicts (fid, d, ncall, params, seed); keeps the parameter arrays alive."""
+    keep = []
+    arr = (Job * len(jobs))()
+    for k, j in enumerate(jobs):
+        par = np.ascontiguousarray(j["params"], dtype=np.float64)
+        keep.append(par)
+        arr[k].integrand_id = int(j["fid"])
+        arr[k].d = int(j["d"])
+        arr[k].ncall = int(j["ncall"])
+        arr[k].params = par.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[k].seed = int(j.get("seed", 0)) & (2 ** 64 - 1)
+    return arr, keep
+
+
+def integrate_batch(jobs, itmax, iter_adjust, precision=FP64, tune=None, stream=None, return_iters=False,
+                    raise_on_error=True):
+    """Many independent integrations in one graph launch. jobs: list of dicts with fid, d, ncall,
+    params, seed. Returns a list of result dicts (and the itmax x 2 per-iteration arrays)."""
+    arr, keep = _jobs(jobs)
+    n = len(jobs)
+    res = (Result * n)()
+    iters = np.zeros((n, itmax, 2)) if return_iters else None
+    st = _lib.mcubes_integrate_batch(n, arr, itmax, iter_adjust, precision,
+                                     None if tune is None else ctypes.byref(tune), _stream(stream), res,
+                                     _hptr(iters))
+    if st != OK and (raise_on_error or st != 6):
+        raise McubesError(st, "integrate_batch")
+    out = [dict(estimate=r.estimate, error=r.error, chi2_dof=r.chi2_dof, iters_done=r.iters_done,
+                samples_per_iter=r.samples_per_iter, status=r.status) for r in res]
+    if iters is not None:
+        for k in range(n):
+            out[k]["iters"] = iters[k]
+    return out
+
+
+def tune_batch(jobs, precision=FP64) -> BatchTuning:
+    """Autotune the batched kernel's launch shape per dimension on these jobs."""
+    arr, keep = _jobs(jobs)
+    t = BatchTuning()
+    _check(_lib.mcubes_tune_batch(len(jobs), arr, precision, ctypes.byref(t)), "tune_batch")
+    return t
 
 
 def philox_dev(d_ctr, n, seed, impl, d_out, stream=None):

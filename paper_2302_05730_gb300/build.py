@@ -42,8 +42,9 @@ def _units():
         if name == "vsample_inst":
             for f32 in (0, 1):
                 for fid in range(8):
-                    units.append((f"vsample_{'f32' if f32 else 'f64'}_{fid}", src,
-                                  [f"-DMCUBES_F32={f32}", f"-DMCUBES_FID={fid}"]))
+                    for part in (0, 1):   # 0: single-job kernels, 1: batched kernels
+                        units.append((f"vsample_{'f32' if f32 else 'f64'}_{fid}_{'batch' if part else 'one'}", src,
+                                      [f"-DMCUBES_F32={f32}", f"-DMCUBES_FID={fid}", f"-DMCUBES_PART={part}"]))
         else:
             units.append((name, src, []))
     return units

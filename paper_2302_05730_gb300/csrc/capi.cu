@@ -12,8 +12,10 @@
 using namespace mcubes;
 
 namespace {
-
 thread_local int g_last_cuda_error = 0;
+}  // namespace
+
+namespace mcubes {
 
 int cuda_status(cudaError_t e)
 {
@@ -33,7 +35,7 @@ constexpr int kGridStride = kNB + 1;
 
 // ---------------------------------------------------------------------------- stratification
 // g: the largest integer with 2 g^d <= n (integer arithmetic only); m = g^d; p = max(2, n / m).
-bool pow_at_most(int64_t g, int d, int64_t limit)
+static bool pow_at_most(int64_t g, int d, int64_t limit)
 {
     int64_t v = 1;
     for (int i = 0; i < d; ++i) {
@@ -76,12 +78,6 @@ int stratify(int d, int64_t n, int64_t *g, int64_t *m, int64_t *p)
 constexpr double kLog2e = 1.4426950408889634074;
 constexpr double kSqrtLog2e = 1.2011224087864498;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-
-struct Problem {
-    int fid, d, prec;
-    int64_t g, m, p;
-    VsampleParams P;
-};
 
 int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, int iteration,
             uint32_t job, int adjust, int prec, Problem &pb)
@@ -187,7 +183,7 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
 
 using Launcher = int (*)(int, const VsampleParams &, const LaunchReq &, cudaStream_t);
 
-Launcher launcher_for(int prec, int fid)
+static Launcher launcher_for(int prec, int fid)
 {
     static const Launcher f64[8] = {launch_vsample_f64_0, launch_vsample_f64_1, launch_vsample_f64_2,
                                     launch_vsample_f64_3, launch_vsample_f64_4, launch_vsample_f64_5,
@@ -226,6 +222,10 @@ int launch_vsample(const Problem &pb, const mcubes_tuning *tune, cudaStream_t s)
     if (st) return st;
     return cuda_status((cudaError_t)launcher_for(pb.prec, pb.fid)(pb.d, pb.P, req, s));
 }
+
+}  // namespace mcubes
+
+namespace {
 
 // ---------------------------------------------------------------------------- small kernels
 __global__ void uniform_grid_kernel(double *grid, int d)

@@ -1,5 +1,6 @@
 // Grid refinement ("Rebin") of the VEGAS importance grid that m-Cubes adapts (paper Sec. 3.2,
-// which delegates the rule to VEGAS, Lepage 1978). One block of 512 threads per axis, FP64:
+// which delegates the rule to VEGAS, Lepage 1978). One block of 512 threads per axis (and, in
+// the batched form, per job and axis), FP64:
 //   1. smooth the bin contributions with a 3-point average (2-point at the ends);
 //   2. normalise by their sum D (an axis with D = 0 or non-finite keeps its grid);
 //   3. damp: r_k = ((1 - rho_k) / ln(1/rho_k))^alpha, rho_k = d_k / D (r = 0 for an empty
@@ -16,10 +17,9 @@ namespace mcubes {
 
 constexpr int kRebinThreads = 512;
 
-__global__ void __launch_bounds__(kRebinThreads) rebin_kernel(const double *__restrict__ grid_in,
-                                                            const double *__restrict__ C,
-                                                            double *__restrict__ grid_out,
-                                                            double alpha)
+// One axis: Bi (501 boundaries), Ci (500 contributions) -> Bo. Block-wide, 512 threads.
+__device__ __forceinline__ void rebin_axis(const double *__restrict__ Bi, const double *__restrict__ Ci,
+                                           double *__restrict__ Bo, double alpha)
 {
     __shared__ double Bs[kNB + 1];
     __shared__ double Cs[kNB];
@@ -28,11 +28,7 @@ __global__ void __launch_bounds__(kRebinThreads) rebin_kernel(const double *__re
     __shared__ double wsum[kRebinThreads / 32];
     __shared__ int keep;
 
-    const int axis = blockIdx.x;
     const int tid = threadIdx.x;
-    const double *Bi = grid_in + (size_t)axis * (kNB + 1);
-    const double *Ci = C + (size_t)axis * kNB;
-    double *Bo = grid_out + (size_t)axis * (kNB + 1);
 
     for (int k = tid; k <= kNB; k += blockDim.x) Bs[k] = Bi[k];
     for (int k = tid; k < kNB; k += blockDim.x) Cs[k] = Ci[k];
@@ -123,10 +119,43 @@ __global__ void __launch_bounds__(kRebinThreads) rebin_kernel(const double *__re
     }
 }
 
+__global__ void __launch_bounds__(kRebinThreads) rebin_kernel(const double *__restrict__ grid_in,
+                                                            const double *__restrict__ C,
+                                                            double *__restrict__ grid_out,
+                                                            double alpha)
+{
+    const int axis = blockIdx.x;
+    rebin_axis(grid_in + (size_t)axis * (kNB + 1), C + (size_t)axis * kNB, grid_out + (size_t)axis * (kNB + 1),
+               alpha);
+}
+
+// Many (job, axis) pairs: block b refines axis block_axis[b] of job block_job[b].
+__global__ void __launch_bounds__(kRebinThreads) rebin_batch_kernel(const uint32_t *__restrict__ block_job,
+                                                                  const uint32_t *__restrict__ block_axis,
+                                                                  const double *const *__restrict__ grid_in,
+                                                                  const double *const *__restrict__ C,
+                                                                  double *const *__restrict__ grid_out,
+                                                                  double alpha)
+{
+    const uint32_t j = block_job[blockIdx.x];
+    const uint32_t a = block_axis[blockIdx.x];
+    rebin_axis(grid_in[j] + (size_t)a * (kNB + 1), C[j] + (size_t)a * kNB, grid_out[j] + (size_t)a * (kNB + 1),
+               alpha);
+}
+
 int launch_rebin(int d, const double *d_grid_in, const double *d_C, double *d_grid_out,
                  double alpha, cudaStream_t stream)
 {
     rebin_kernel<<<d, kRebinThreads, 0, stream>>>(d_grid_in, d_C, d_grid_out, alpha);
+    return (int)cudaGetLastError();
+}
+
+int launch_rebin_batch(int n_blocks, const uint32_t *block_job, const uint32_t *block_axis,
+                       const double *const *grid_in, const double *const *C, double *const *grid_out,
+                       double alpha, cudaStream_t stream)
+{
+    if (n_blocks <= 0) return (int)cudaSuccess;
+    rebin_batch_kernel<<<n_blocks, kRebinThreads, 0, stream>>>(block_job, block_axis, grid_in, C, grid_out, alpha);
     return (int)cudaGetLastError();
 }
 

@@ -85,41 +85,60 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch
     }
 }
 
-template <int D, int FID, bool F32>
-__global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const VsampleParams P)
+// Per-thread accumulators of one job's sub-cubes.
+struct ThreadSums {
+    double sI = 0.0, sV = 0.0;      // FP64 path
+    float cI = 0.0f, eI = 0.0f;     // FP32 path: Neumaier-compensated sums of the cube means
+    float cV = 0.0f, eV = 0.0f;     // ... and of the cube variances (times p (p-1))
+};
+
+// Stage a grid into shared memory as (B_k, Delta_k) pairs and clear the histogram. Block-wide.
+template <int D, bool F32>
+__device__ __forceinline__ void stage_grid(const double *grid, typename Prec<F32>::T2 *tab,
+                                           typename Prec<F32>::T *hist, bool clear_hist)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2 *tab = reinterpret_cast<T2 *>(smem_raw);
-    T *hist = reinterpret_cast<T *>(smem_raw + (size_t)D * kNB * sizeof(T2));
-    __shared__ double red_scratch[64];
-
-    const bool adjust = P.adjust != 0;
-
-    // ---- stage the grid as (B_k, Delta_k) and clear the private histogram
     for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
         const int i = e / kNB;
         const int k = e - i * kNB;
-        const double b0 = P.grid[i * (kNB + 1) + k];
-        const double b1 = P.grid[i * (kNB + 1) + k + 1];
+        const double b0 = grid[i * (kNB + 1) + k];
+        const double b1 = grid[i * (kNB + 1) + k + 1];
         T2 v;
         v.x = (T)b0;
         v.y = (T)(b1 - b0);
         tab[e] = v;
-        if (adjust) hist[e] = T(0);
+        if (clear_hist) hist[e] = T(0);
     }
     __syncthreads();
+}
 
-    // ---- this thread's sub-cube range. Range r = (gtid * P.perm_mul) mod N is a permutation
-    // of the N threads (perm_mul is odd and coprime with N): the 32 lanes of a warp start in
-    // scattered parts of [0, m), so their strata differ on every axis and their bins spread
-    // over the whole histogram instead of piling into one stratum's window.
-    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t rng = (gtid * (uint64_t)P.perm_mul) % nthreads;
-    uint32_t t = (uint32_t)((rng * P.m) / nthreads);
-    const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
+// FP32 histogram scale sigma = F / |I_prev| (1 when unknown).
+template <bool F32>
+__device__ __forceinline__ float histogram_scale(const VsampleParams &P)
+{
+    float hsig = 1.0f;
+    if (F32 && P.adjust && P.prev != nullptr) {
+        const double ip = fabs(P.prev[0] * P.prev_scale);
+        if (ip > 0.0 && ip < 1e300 && P.fscale > 0.0) {
+            const double s = P.fscale / ip;
+            if (s > 1e-30 && s < 1e30) hsig = (float)s;
+        }
+    }
+    return hsig;
+}
+
+// Algorithm 2's loop over this thread's sub-cubes [t, t_end): draws, map, integrand, per-cube
+// statistics and bin contributions. kGlobalHist routes the contributions straight to the
+// job's global C (FP64 atomics) instead of the block's shared histogram.
+template <int D, int FID, bool F32, bool kGlobalHist>
+__device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t, const uint32_t t_end,
+                                             const typename Prec<F32>::T2 *tab, typename Prec<F32>::T *hist,
+                                             const float hsig, ThreadSums &acc)
+{
+    using T = typename Prec<F32>::T;
+    using T2 = typename Prec<F32>::T2;
+    const bool adjust = P.adjust != 0;
 
     // strata digits c_i (axis 0 fastest) and c_i - 1 in the path's precision
     uint32_t dig[D];
@@ -137,22 +156,18 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
     const T R = F32 ? (T)P.R32 : (T)P.R;
     const T ycap = F32 ? (T)P.ycap32 : (T)P.ycap;
     const T magic = F32 ? (T)8388608.0f : (T)4503599627370496.0;   // 2^23 / 2^52
-
-    // FP32 histogram scale sigma = F / |I_prev| (1 when unknown)
-    float hsig = 1.0f;
-    if (F32 && adjust && P.prev != nullptr) {
-        const double ip = fabs(P.prev[0] * P.prev_scale);
-        if (ip > 0.0 && ip < 1e300 && P.fscale > 0.0) {
-            const double s = P.fscale / ip;
-            if (s > 1e-30 && s < 1e30) hsig = (float)s;
-        }
-    }
-
-    double sI = 0.0, sV = 0.0;          // FP64 path: per-thread sums
-    float cI = 0.0f, eI = 0.0f;         // FP32 path: Neumaier-compensated per-thread sums
-    float cV = 0.0f, eV = 0.0f;
     const uint32_t p = P.p;
     const float inv_p32 = (float)P.inv_p;
+    // global-histogram scale (FP32: (F / sigma)^2; FP64: nd^(2d))
+    double gscale = 0.0;
+    if constexpr (kGlobalHist) {
+        if constexpr (F32) {
+            const double r = P.fscale / (double)hsig;
+            gscale = r * r;
+        } else {
+            gscale = P.fscale * P.fscale;
+        }
+    }
 
     for (; t < t_end; ++t) {
         T S1 = T(0), S2 = T(0), w0 = T(0);   // FP64: plain sums; FP32: w0 and shifted sums
@@ -251,8 +266,14 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
                 } else {
                     h = w * w;
                 }
+                if constexpr (kGlobalHist) {
+                    const double hg = (double)h * gscale;
 #pragma unroll
-                for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], h);
+                    for (int i = 0; i < D; ++i) atomicAdd(&P.C[kofs[i]], hg);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], h);
+                }
             }
         }
 
@@ -266,12 +287,12 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
             float var = fmaf(-S1 * inv_p32, S1, S2);
             var = fmaxf(var, 0.0f);
             {
-                const float tI = cI + mean;
-                eI += (fabsf(cI) >= fabsf(mean)) ? ((cI - tI) + mean) : ((mean - tI) + cI);
-                cI = tI;
-                const float tV = cV + var;
-                eV += (cV >= var) ? ((cV - tV) + var) : ((var - tV) + cV);
-                cV = tV;
+                const float tI = acc.cI + mean;
+                acc.eI += (fabsf(acc.cI) >= fabsf(mean)) ? ((acc.cI - tI) + mean) : ((mean - tI) + acc.cI);
+                acc.cI = tI;
+                const float tV = acc.cV + var;
+                acc.eV += (acc.cV >= var) ? ((acc.cV - tV) + var) : ((var - tV) + acc.cV);
+                acc.cV = tV;
             }
             if (probe_this) {   // probe values on the final scale (fscale = F)
                 P.probe[2 * (size_t)(t >> P.probe_shift)] = (double)mean * P.fscale;
@@ -281,8 +302,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
             const double It = S1 * P.inv_p;
             double Vt = fma(-S1 * P.inv_p, S1, S2);
             Vt = Vt > 0.0 ? Vt : 0.0;
-            sI += It;
-            sV += Vt;
+            acc.sI += It;
+            acc.sV += Vt;
             if (probe_this) {   // probe values on the final scale (fscale = nd^d)
                 P.probe[2 * (size_t)(t >> P.probe_shift)] = It * P.fscale;
                 P.probe[2 * (size_t)(t >> P.probe_shift) + 1] = Vt * P.inv_pp1 * P.fscale * P.fscale;
@@ -304,20 +325,28 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
             }
         }
     }
+}
 
-    // ---- block reduction, then two FP64 global atomics (Algorithm 2, AtomicAdd into r)
+// Block reduction of the thread sums, two FP64 global atomics into P.sums (Algorithm 2,
+// AtomicAdd into r), then the flush of the private histogram into P.C. Block-wide; leaves the
+// histogram free for reuse (ends with a barrier).
+template <int D, bool F32>
+__device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums &acc,
+                                             typename Prec<F32>::T *hist, bool flush_hist, float hsig,
+                                             double *red_scratch)
+{
+    using T = typename Prec<F32>::T;
+    double sI = acc.sI, sV = acc.sV;
     if constexpr (F32) {
-        sI = (double)cI + (double)eI;
-        sV = (double)cV + (double)eV;
+        sI = (double)acc.cI + (double)acc.eI;
+        sV = (double)acc.cV + (double)acc.eV;
     }
     block_sum2(sI, sV, red_scratch);
     if (threadIdx.x == 0) {
         atomicAdd(&P.sums[0], sI * P.fscale);
         atomicAdd(&P.sums[1], sV * P.inv_pp1 * P.fscale * P.fscale);
     }
-
-    // ---- flush the private histogram into the global bin contributions
-    if (adjust) {
+    if (flush_hist) {
         __syncthreads();
         double cscale;
         if constexpr (F32) {
@@ -331,6 +360,104 @@ __global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const Vsample
             if (v != T(0)) atomicAdd(&P.C[e], (double)v * cscale);
         }
     }
+    __syncthreads();
+}
+
+// One job, whole grid of persistent blocks.
+template <int D, int FID, bool F32>
+__global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const VsampleParams P)
+{
+    using T = typename Prec<F32>::T;
+    using T2 = typename Prec<F32>::T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *tab = reinterpret_cast<T2 *>(smem_raw);
+    T *hist = reinterpret_cast<T *>(smem_raw + (size_t)D * kNB * sizeof(T2));
+    __shared__ double red_scratch[64];
+
+    const bool adjust = P.adjust != 0;
+    stage_grid<D, F32>(P.grid, tab, hist, adjust);
+
+    // This thread's sub-cube range. Range r = (gtid * P.perm_mul) mod N is a permutation of
+    // the N threads (perm_mul is odd and coprime with N): the 32 lanes of a warp start in
+    // scattered parts of [0, m), so their strata differ on every axis and their bins spread
+    // over the whole histogram instead of piling into one stratum's window.
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t rng = (gtid * (uint64_t)P.perm_mul) % nthreads;
+    const uint32_t t = (uint32_t)((rng * P.m) / nthreads);
+    const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
+
+    const float hsig = histogram_scale<F32>(P);
+    ThreadSums acc;
+    sample_cubes<D, FID, F32, false>(P, t, t_end, tab, hist, hsig, acc);
+    finish_block<D, F32>(P, acc, hist, adjust, hsig, red_scratch);
+}
+
+// ------------------------------------------------------------------------------ batches
+// Many independent integrations in one launch. The host cuts every job of one (d, family)
+// class into tiles of consecutive sub-cubes. Block b takes the contiguous tile range
+// [b n / B, (b+1) n / B), so it switches job only at job boundaries. On each switch it flushes
+// the finished job's sums and histogram and stages the next job's grid.
+struct BatchJob {
+    VsampleParams P;            // per-job constants (grid, C, sums, prev are set per iteration)
+    const double *grid[2];      // ping-pong grids
+    double *C;                  // d x 500 bin contributions
+    double *sums;               // 2 x itmax per-iteration sums
+};
+
+struct BatchTile {
+    uint32_t job, c0, c1, pad;
+};
+
+template <int D, int FID, bool F32, bool kGlobalHist>
+__global__ void __launch_bounds__(kMaxBlockThreads)
+    vsample_batch_kernel(const BatchJob *__restrict__ jobs, const BatchTile *__restrict__ tiles, int n_tiles,
+                         int iteration, int parity, int adjust, uint32_t perm_mul)
+{
+    using T = typename Prec<F32>::T;
+    using T2 = typename Prec<F32>::T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *tab = reinterpret_cast<T2 *>(smem_raw);
+    T *hist = reinterpret_cast<T *>(smem_raw + (size_t)D * kNB * sizeof(T2));
+    __shared__ double red_scratch[64];
+
+    const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
+    const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
+    const bool shared_hist = adjust && !kGlobalHist;
+    // thread order inside a tile, permuted as in the single-job kernel
+    const uint32_t r = (uint32_t)(((uint64_t)threadIdx.x * perm_mul) % blockDim.x);
+
+    int cur = -1;
+    VsampleParams P;
+    float hsig = 1.0f;
+    ThreadSums acc;
+    for (int ti = tb; ti < te; ++ti) {
+        const BatchTile tile = tiles[ti];
+        if ((int)tile.job != cur) {
+            if (cur >= 0) {
+                finish_block<D, F32>(P, acc, hist, shared_hist, hsig, red_scratch);
+                acc = ThreadSums();
+            }
+            cur = (int)tile.job;
+            const BatchJob &J = jobs[cur];
+            P = J.P;
+            P.grid = J.grid[parity];
+            P.C = J.C;
+            P.sums = J.sums + 2 * iteration;
+            P.prev = iteration > 0 ? J.sums + 2 * (iteration - 1) : nullptr;
+            P.prev_scale = 1.0 / (double)P.m;
+            P.ctr2_hi = (uint32_t)iteration << 16;
+            P.adjust = adjust;
+            P.probe = nullptr;
+            hsig = histogram_scale<F32>(P);
+            stage_grid<D, F32>(P.grid, tab, hist, shared_hist);
+        }
+        const uint32_t n = tile.c1 - tile.c0;
+        const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
+        const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
+        sample_cubes<D, FID, F32, kGlobalHist>(P, t, t_end, tab, hist, hsig, acc);
+    }
+    if (cur >= 0) finish_block<D, F32>(P, acc, hist, shared_hist, hsig, red_scratch);
 }
 
 }  // namespace mcubes

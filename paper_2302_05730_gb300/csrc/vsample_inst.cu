@@ -12,6 +12,9 @@
 #ifndef MCUBES_FID
 #error "MCUBES_FID must be defined"
 #endif
+#ifndef MCUBES_PART
+#define MCUBES_PART 0   // 0: single-job kernels, 1: batched kernels
+#endif
 
 #if MCUBES_F32
 #define MCUBES_PREC f32
@@ -21,6 +24,9 @@
 #define MCUBES_CAT2(a, b, c) launch_vsample_##a##_##b
 #define MCUBES_CAT(a, b) MCUBES_CAT2(a, b, 0)
 #define MCUBES_LAUNCHER MCUBES_CAT(MCUBES_PREC, MCUBES_FID)
+#define MCUBES_BCAT2(a, b) launch_vsample_batch_##a##_##b
+#define MCUBES_BCAT(a, b) MCUBES_BCAT2(a, b)
+#define MCUBES_BATCH_LAUNCHER MCUBES_BCAT(MCUBES_PREC, MCUBES_FID)
 
 namespace mcubes {
 namespace {
@@ -78,8 +84,70 @@ int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
+#if MCUBES_PART == 1
+template <int D, bool kGlobalHist>
+int launch_batch_d(const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration, int parity,
+                   int adjust, const LaunchReq &req, cudaStream_t s)
+{
+    static InstanceInfo info;
+    auto kern = vsample_batch_kernel<D, kFid, kF32, kGlobalHist>;
+    const bool shared_hist = adjust && !kGlobalHist;
+    const size_t smem = vsample_smem_bytes<kF32>(D, shared_hist);
+    cudaError_t e;
+    if (!info.ready.load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)vsample_smem_bytes<kF32>(D, true));
+        if (e != cudaSuccess) return (int)e;
+        for (int a = 0; a < 2; ++a) {
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kMaxBlockThreads,
+                                                              vsample_smem_bytes<kF32>(D, a != 0));
+            if (e != cudaSuccess) return (int)e;
+            info.occ[a] = nb > 0 ? nb : 1;
+        }
+        info.ready.store(1, std::memory_order_release);
+    }
+    const int threads = req.threads;
+    int bps = req.blocks_per_sm;
+    if (bps <= 0) {
+        bps = info.occ[shared_hist ? 1 : 0];
+        if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
+    }
+    int blocks = req.num_sms * bps;
+    if (blocks > n_tiles) blocks = n_tiles;
+    if (blocks < 1) return (int)cudaSuccess;
+    const uint32_t perm_mul = ((uint32_t)((double)threads * 0.6180339887498949)) | 1u;
+    kern<<<blocks, threads, smem, s>>>(jobs, tiles, n_tiles, iteration, parity, adjust, perm_mul);
+    return (int)cudaGetLastError();
+}
+
+template <bool kGlobalHist>
+int launch_batch(int d, const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration, int parity,
+                 int adjust, const LaunchReq &req, cudaStream_t s)
+{
+    switch (d) {
+#define MCUBES_BATCH_CASE(DD) \
+    case DD: return launch_batch_d<DD, kGlobalHist>(jobs, tiles, n_tiles, iteration, parity, adjust, req, s);
+    MCUBES_BATCH_CASE(1) MCUBES_BATCH_CASE(2) MCUBES_BATCH_CASE(3) MCUBES_BATCH_CASE(4)
+    MCUBES_BATCH_CASE(5) MCUBES_BATCH_CASE(6) MCUBES_BATCH_CASE(7) MCUBES_BATCH_CASE(8)
+    MCUBES_BATCH_CASE(9) MCUBES_BATCH_CASE(10) MCUBES_BATCH_CASE(11) MCUBES_BATCH_CASE(12)
+    MCUBES_BATCH_CASE(13) MCUBES_BATCH_CASE(14) MCUBES_BATCH_CASE(15) MCUBES_BATCH_CASE(16)
+#undef MCUBES_BATCH_CASE
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+#endif
 }  // namespace
 
+#if MCUBES_PART == 1
+int MCUBES_BATCH_LAUNCHER(int d, const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration,
+                          int parity, int adjust, int hist_mode, const LaunchReq &req, cudaStream_t s)
+{
+    return hist_mode == 1 ? launch_batch<true>(d, jobs, tiles, n_tiles, iteration, parity, adjust, req, s)
+                          : launch_batch<false>(d, jobs, tiles, n_tiles, iteration, parity, adjust, req, s);
+}
+#else
 int MCUBES_LAUNCHER(int d, const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 {
     switch (d) {
@@ -102,5 +170,7 @@ int MCUBES_LAUNCHER(int d, const VsampleParams &P, const LaunchReq &req, cudaStr
     default: return (int)cudaErrorInvalidValue;
     }
 }
+
+#endif
 
 }  // namespace mcubes
