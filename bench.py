@@ -175,6 +175,7 @@ def main():
     ap.add_argument("--headline-only", action="store_true",
                     help="only the FP32-eval device-resident leg (profiling runs)")
     ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (4096-job) leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -346,6 +347,40 @@ def main():
                 per[W.NAMES[fid]] = {"iters": k_hit[0], "seconds": k_hit[1]} if k_hit else None
             tta[name] = per
 
+    # ---- batched form: 4096 independent Gaussian integrations, d ~ U{2..8}, a_i ~ U[5, 25],
+    # u_i ~ U[0.2, 0.8], samples/iteration log-uniform in [1e4, 1e7], 8 iterations (4 adjust),
+    # one graph launch per precision; plain FP64 one job at a time on a sample of the jobs
+    batch = None
+    if not args.no_batch and rank == 0:
+        bjobs = W.batch_jobs(4096, seed=0)
+        for k, jb in enumerate(bjobs):
+            jb["seed"] = 0
+        per_job = [int(np.prod(capi.stratify(jb["d"], jb["ncall"])[1:])) for jb in bjobs]
+        tot = sum(per_job)
+        t0 = time.perf_counter()
+        tune = capi.tune_batch(bjobs, precision=capi.FP32_EVAL)
+        tune_s = time.perf_counter() - t0
+        capi.integrate_batch(bjobs[:32], 2, 1, precision=capi.FP32_EVAL, tune=tune)
+        batch = {"jobs": len(bjobs), "samples_per_iter": tot, "iters": 8, "iter_adjust": 4, "autotune_s": tune_s,
+                 "autotuned": {str(k): v for k, v in tune.as_dict().items()}}
+        for prec, name in ((capi.FP32_EVAL, "fp32_eval"), (capi.FP64, "fp64")):
+            t0 = time.perf_counter()
+            res = capi.integrate_batch(bjobs, 8, 4, precision=prec, tune=tune, raise_on_error=False)
+            el = time.perf_counter() - t0
+            rel = np.array([r["error"] / abs(r["estimate"]) if r["estimate"] else np.inf for r in res])
+            batch[name] = {"seconds": el, "samples_per_s": 8 * tot / el,
+                           "jobs_at_1e-3": int(np.sum(rel <= 1e-3)), "median_rel_err": float(np.median(rel))}
+        # plain FP64 m-Cubes, one job at a time, on every 16th job; scaled to the whole batch
+        sample = list(range(0, len(bjobs), 16))
+        t0 = time.perf_counter()
+        for k in sample:
+            jb = bjobs[k]
+            capi.integrate(jb["fid"], jb["params"], jb["d"], jb["ncall"], 8, 4, 0, precision=capi.FP64)
+        el = time.perf_counter() - t0
+        frac = sum(per_job[k] for k in sample) / tot
+        batch["plain_fp64_sequential"] = {"seconds_sampled": el, "jobs_sampled": len(sample),
+                                          "seconds_scaled": el / frac, "samples_per_s": 8 * tot * frac / el}
+
     # ---- CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -382,6 +417,7 @@ def main():
                          "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})"},
             "cpu_baseline": cpu,
             "time_to_1e-3": tta,
+            "batch": batch,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

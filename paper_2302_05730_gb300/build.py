@@ -6,6 +6,9 @@ paper_2302_05730_gb300/libmcubes.so with the CUDA runtime linked statically, so 
 library needs only the driver. Objects are rebuilt when a source or header is newer.
 
     python -m paper_2302_05730_gb300.build [--force] [--jobs N] [--checked]
+
+MCUBES_NVCC_EXTRA adds nvcc flags to every unit (objects are not rebuilt when only it changes:
+use --force).
 """
 from __future__ import annotations
 
@@ -61,6 +64,7 @@ def build(force: bool = False, jobs: int | None = None, checked: bool = False, v
     nvcc = _nvcc()
     dep_t = _deps_mtime()
     extra = ["-DMCUBES_CHECKED=1"] if checked else []
+    extra += os.environ.get("MCUBES_NVCC_EXTRA", "").split()   # extra nvcc flags (e.g. -D overrides)
     todo, objs = [], []
     for name, src, defs in _units():
         obj = os.path.join(BUILD, name + ".o")

@@ -85,6 +85,23 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch
     }
 }
 
+// Resident blocks per SM the FP32-eval kernels are compiled for (register budget 65536 /
+// (256 x blocks)): as many as the shared memory of an adjusting block allows, at most 4. The
+// kernel is bound by shared-memory latency and throughput, so more resident warps keep more
+// requests in flight. FP64 kernels are bound by the FP64 pipe and keep the default budget.
+#ifndef MCUBES_MAX_MIN_BLOCKS
+#define MCUBES_MAX_MIN_BLOCKS 4
+#endif
+template <int D, bool F32>
+constexpr int min_blocks_per_sm()
+{
+    if (!F32) return 1;
+    const size_t smem = vsample_smem_bytes<F32>(D, true) + 1024;
+    const int fit = (int)((size_t)(227 * 1024) / smem);
+    const int b = fit < MCUBES_MAX_MIN_BLOCKS ? fit : MCUBES_MAX_MIN_BLOCKS;
+    return b < 1 ? 1 : b;
+}
+
 // Per-thread accumulators of one job's sub-cubes.
 struct ThreadSums {
     double sI = 0.0, sV = 0.0;      // FP64 path
@@ -365,7 +382,7 @@ __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums 
 
 // One job, whole grid of persistent blocks.
 template <int D, int FID, bool F32>
-__global__ void __launch_bounds__(kMaxBlockThreads) vsample_kernel(const VsampleParams P)
+__global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>())) vsample_kernel(const VsampleParams P)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
@@ -410,7 +427,7 @@ struct BatchTile {
 };
 
 template <int D, int FID, bool F32, bool kGlobalHist>
-__global__ void __launch_bounds__(kMaxBlockThreads)
+__global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()))
     vsample_batch_kernel(const BatchJob *__restrict__ jobs, const BatchTile *__restrict__ tiles, int n_tiles,
                          int iteration, int parity, int adjust, uint32_t perm_mul)
 {
