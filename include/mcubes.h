@@ -121,6 +121,30 @@ int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t n
                         void *stream, double *iter_out, const double *grid_in, double *grid_out,
                         mcubes_result *out);
 
+/* Checkpoint and resume: iterations [it_begin, it_end) of an integration of itmax iterations
+ * whose first iter_adjust iterations refine the grid. The Philox counters use the absolute
+ * iteration index, so running [0, k) and then [k, itmax) from the returned grid repeats the
+ * uninterrupted run, up to the order of floating-point sums.
+ *   grid_in: the grid before iteration it_begin (d x 501, host). NULL only for it_begin == 0
+ *     (uniform grid).
+ *   prev_estimate: the estimate of iteration it_begin - 1, or 0 if none. It only sets the
+ *     FP32-eval histogram scale.
+ *   grid_out: NULL, or d x 501 doubles that receive the grid after the range.
+ *   iter_out: 2 x (it_end - it_begin) doubles: (I_it, Var_it).
+ * Combine all iterations with mcubes_combine. FP32_EVAL additionally requires g <= 2^24.
+ * Errors: as mcubes_integrate_ex; INVALID_ARG for a bad range, a NULL iter_out, or a NULL
+ * grid_in with it_begin > 0. */
+int mcubes_integrate_range(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
+                           int iter_adjust, int it_begin, int it_end, uint64_t seed, int precision,
+                           const double *grid_in, double prev_estimate, double *grid_out, double *iter_out,
+                           void *stream);
+
+/* Inverse-variance combination of iterations [skip, n) of iter (n pairs (I_it, Var_it)), as in
+ * mcubes_integrate. skip drops early iterations, e.g. those sampled before the grid settled.
+ * Host only. Errors: INVALID_ARG (NULL pointers, n < 1, skip outside [0, n), a non-finite or
+ * negative entry). */
+int mcubes_combine(const double *iter, int n, int skip, mcubes_result *out);
+
 /* One V-Sample pass (Algorithm 2) on a caller-supplied grid, with host buffers. This is the
  * per-iteration parity hook.
  *   iteration (0..65535) and job select the Philox counters (ctr = (t, q, iteration<<16 | j, job)).

@@ -77,6 +77,8 @@ def _load():
         "mcubes_integrate_ex": (i32, [i32, dp, i32, i64, i32, i32, u64, i32, ctypes.POINTER(Tuning), vp,
                                       dp, dp, dp, ctypes.POINTER(Result)]),
         "mcubes_vsample_once": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, dp, dp, dp, dp, dp]),
+        "mcubes_integrate_range": (i32, [i32, dp, i32, i64, i32, i32, i32, i32, u64, i32, dp, dbl, dp, dp, vp]),
+        "mcubes_combine": (i32, [dp, i32, i32, ctypes.POINTER(Result)]),
         "mcubes_vsample_dev": (i32, [i32, dp, i32, i64, u64, i32, u32, i32, i32, vp, vp, vp, vp, vp, i32,
                                      ctypes.POINTER(Tuning), vp]),
         "mcubes_rebin_dev": (i32, [i32, vp, vp, vp, vp]),
@@ -200,6 +202,32 @@ def integrate(fid, params, d, ncall, itmax, iter_adjust, seed, precision=FP64, t
     if grid is not None:
         out["grid"] = grid
     return out
+
+
+def integrate_range(fid, params, d, ncall, itmax, iter_adjust, it_begin, it_end, seed, precision=FP64,
+                    grid_in=None, prev_estimate=0.0, stream=None):
+    """Iterations [it_begin, it_end) of an itmax-iteration run (checkpoint / resume). Returns
+    dict(iters (n x 2), grid (d x 501))."""
+    par, pp = _hd(params)
+    gin = gp = None
+    if grid_in is not None:
+        gin, gp = _hd(grid_in)
+    n = it_end - it_begin
+    iters = np.zeros((max(n, 1), 2))
+    grid = np.zeros((d, NBINS + 1))
+    st = _lib.mcubes_integrate_range(int(fid), pp, d, int(ncall), itmax, iter_adjust, it_begin, it_end,
+                                     int(seed) & (2 ** 64 - 1), precision, gp, float(prev_estimate), _hptr(grid),
+                                     _hptr(iters), _stream(stream))
+    _check(st, "integrate_range")
+    return dict(iters=iters[:n], grid=grid)
+
+
+def combine(iters, skip=0):
+    """Inverse-variance combination of per-iteration (I, Var) pairs from index skip on."""
+    it = np.ascontiguousarray(iters, dtype=np.float64).reshape(-1, 2)
+    res = Result()
+    _check(_lib.mcubes_combine(_hptr(it), it.shape[0], int(skip), ctypes.byref(res)), "combine")
+    return dict(estimate=res.estimate, error=res.error, chi2_dof=res.chi2_dof, iters_done=res.iters_done)
 
 
 def vsample_once(fid, params, d, ncall, seed, iteration=0, job=0, adjust=1, precision=FP64,

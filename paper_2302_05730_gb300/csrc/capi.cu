@@ -393,6 +393,82 @@ int mcubes_stratify(int d, int64_t ncall, int64_t *g, int64_t *m, int64_t *p)
     return stratify(d, ncall, g, m, p);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Iterations [it_begin, it_end) of an integration of itmax iterations whose first iter_adjust
+// iterations refine the grid. grid_in: the grid before it_begin (NULL: uniform). prev_I: the
+// estimate of iteration it_begin - 1 (0: none); it only sets the FP32-eval histogram scale.
+// Writes the per-iteration (I, Var) into I, V and, if grid_out, the grid after the range.
+int run_range(Problem &pb, int itmax, int iter_adjust, int it_begin, int it_end, const double *grid_in,
+              double prev_I, const mcubes_tuning *tune, void *stream, std::vector<double> &I,
+              std::vector<double> &V, double *grid_out)
+{
+    const int d = pb.d;
+    const int n = it_end - it_begin;
+    Workspace *w = nullptr;
+    const size_t host_bytes = sizeof(double) * (2 * (size_t)(n + 1) + (size_t)d * kGridStride);
+    int st = workspace(n + 1, host_bytes, w);
+    if (st) return st;
+    cudaStream_t s = stream ? (cudaStream_t)stream : w->stream;
+    const double m = (double)pb.m;
+
+    int cur = 0;
+    if ((st = upload_grid(grid_in, d, w->d_grid[0], w->h_pin, s))) return st;
+    // slot 0 holds the previous iteration's raw sums (for the FP32 histogram scale)
+    if ((st = cuda_status(cudaStreamSynchronize(s)))) return st;   // the staging buffer is reused below
+    w->h_pin[0] = prev_I * m;
+    w->h_pin[1] = 0.0;
+    if ((st = cuda_status(cudaMemsetAsync(w->d_iter, 0, sizeof(double) * 2 * (n + 1), s)))) return st;
+    if ((st = cuda_status(cudaMemcpyAsync(w->d_iter, w->h_pin, sizeof(double) * 2, cudaMemcpyHostToDevice, s))))
+        return st;
+    for (int it = it_begin; it < it_end; ++it) {
+        const int slot = it - it_begin + 1;
+        const int adjust = it < iter_adjust;
+        VsampleParams &P = pb.P;
+        P.grid = w->d_grid[cur];
+        P.C = w->d_C;
+        P.sums = w->d_iter + 2 * slot;
+        P.prev = (it > it_begin || prev_I != 0.0) ? w->d_iter + 2 * (slot - 1) : nullptr;   // raw sums
+        P.prev_scale = 1.0 / m;
+        P.adjust = adjust;
+        P.ctr2_hi = (uint32_t)it << 16;
+        if (adjust) {
+            if ((st = cuda_status(cudaMemsetAsync(w->d_C, 0, sizeof(double) * d * kNB, s)))) return st;
+        }
+        if ((st = launch_vsample(pb, tune, s))) return st;
+        if (adjust && it + 1 < itmax) {
+            if ((st = cuda_status((cudaError_t)launch_rebin(d, w->d_grid[cur], w->d_C, w->d_grid[1 - cur], 1.5, s))))
+                return st;
+            cur = 1 - cur;
+        }
+    }
+    double *h_iter = w->h_pin;
+    double *h_grid = w->h_pin + 2 * (n + 1);
+    if ((st = cuda_status(cudaMemcpyAsync(h_iter, w->d_iter, sizeof(double) * 2 * (n + 1), cudaMemcpyDeviceToHost, s))))
+        return st;
+    if (grid_out) {
+        if ((st = cuda_status(cudaMemcpyAsync(h_grid, w->d_grid[cur], sizeof(double) * d * kGridStride,
+                                              cudaMemcpyDeviceToHost, s))))
+            return st;
+    }
+    if ((st = cuda_status(cudaStreamSynchronize(s)))) return st;
+    I.assign(n, 0.0);
+    V.assign(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        I[k] = h_iter[2 * (k + 1)] / m;
+        V[k] = h_iter[2 * (k + 1) + 1] / (m * m);
+        if (!std::isfinite(I[k]) || !std::isfinite(V[k])) return MCUBES_ERR_NONFINITE;
+    }
+    if (grid_out) std::memcpy(grid_out, h_grid, sizeof(double) * d * kGridStride);
+    return MCUBES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
                         int iter_adjust, uint64_t seed, int precision, const mcubes_tuning *tune,
                         void *stream, double *iter_out, const double *grid_in, double *grid_out,
@@ -405,70 +481,62 @@ int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t n
     else if (itmax < 1 || itmax > 0xFFFF || iter_adjust < 0 || iter_adjust > itmax) st = MCUBES_ERR_INVALID_ARG;
     if (!st) st = prepare(integrand_id, params, d, ncall, seed, 0, 0, iter_adjust > 0, precision, pb);
     if (!st && grid_in && !grid_ok(grid_in, d)) st = MCUBES_ERR_INVALID_ARG;
+    std::vector<double> I, V;
+    if (!st) st = run_range(pb, itmax, iter_adjust, 0, itmax, grid_in, 0.0, tune, stream, I, V, grid_out);
     if (st) {
         if (out) out->status = st;
         return st;
-    }
-    auto fail = [&](int s) {
-        out->status = s;
-        return s;
-    };
-
-    Workspace *w = nullptr;
-    const size_t host_bytes = sizeof(double) * (2 * (size_t)itmax + (size_t)d * kGridStride);
-    if ((st = workspace(itmax, host_bytes, w))) return fail(st);
-    cudaStream_t s = stream ? (cudaStream_t)stream : w->stream;
-
-    int cur = 0;
-    if ((st = upload_grid(grid_in, d, w->d_grid[0], w->h_pin, s))) return fail(st);
-    if ((st = cuda_status(cudaMemsetAsync(w->d_iter, 0, sizeof(double) * 2 * itmax, s)))) return fail(st);
-    for (int it = 0; it < itmax; ++it) {
-        const int adjust = it < iter_adjust;
-        VsampleParams &P = pb.P;
-        P.grid = w->d_grid[cur];
-        P.C = w->d_C;
-        P.sums = w->d_iter + 2 * it;
-        P.prev = it > 0 ? w->d_iter + 2 * (it - 1) : nullptr;   // raw sums: I = sum / m
-        P.prev_scale = 1.0 / (double)pb.m;
-        P.adjust = adjust;
-        P.ctr2_hi = (uint32_t)it << 16;
-        if (adjust) {
-            if ((st = cuda_status(cudaMemsetAsync(w->d_C, 0, sizeof(double) * d * kNB, s)))) return fail(st);
-        }
-        if ((st = launch_vsample(pb, tune, s))) return fail(st);
-        if (adjust && it + 1 < itmax) {
-            if ((st = cuda_status((cudaError_t)launch_rebin(d, w->d_grid[cur], w->d_C, w->d_grid[1 - cur], 1.5, s))))
-                return fail(st);
-            cur = 1 - cur;
-        }
-    }
-    double *h_iter = w->h_pin;
-    double *h_grid = w->h_pin + 2 * itmax;
-    if ((st = cuda_status(cudaMemcpyAsync(h_iter, w->d_iter, sizeof(double) * 2 * itmax, cudaMemcpyDeviceToHost, s))))
-        return fail(st);
-    if (grid_out) {
-        if ((st = cuda_status(cudaMemcpyAsync(h_grid, w->d_grid[cur], sizeof(double) * d * kGridStride,
-                                              cudaMemcpyDeviceToHost, s))))
-            return fail(st);
-    }
-    if ((st = cuda_status(cudaStreamSynchronize(s)))) return fail(st);
-
-    std::vector<double> I(itmax), V(itmax);
-    const double m = (double)pb.m;
-    for (int it = 0; it < itmax; ++it) {
-        I[it] = h_iter[2 * it] / m;
-        V[it] = h_iter[2 * it + 1] / (m * m);
-        if (!std::isfinite(I[it]) || !std::isfinite(V[it])) return fail(MCUBES_ERR_NONFINITE);
     }
     if (iter_out)
         for (int it = 0; it < itmax; ++it) {
             iter_out[2 * it] = I[it];
             iter_out[2 * it + 1] = V[it];
         }
-    if (grid_out) std::memcpy(grid_out, h_grid, sizeof(double) * d * kGridStride);
     combine(I, V, out);
     out->iters_done = itmax;
     out->samples_per_iter = pb.m * pb.p;
+    out->status = MCUBES_OK;
+    return MCUBES_OK;
+}
+
+int mcubes_integrate_range(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
+                           int iter_adjust, int it_begin, int it_end, uint64_t seed, int precision,
+                           const double *grid_in, double prev_estimate, double *grid_out, double *iter_out,
+                           void *stream)
+{
+    if (itmax < 1 || itmax > 0xFFFF || iter_adjust < 0 || iter_adjust > itmax) return MCUBES_ERR_INVALID_ARG;
+    if (it_begin < 0 || it_end <= it_begin || it_end > itmax || !iter_out) return MCUBES_ERR_INVALID_ARG;
+    if (!std::isfinite(prev_estimate)) return MCUBES_ERR_INVALID_ARG;
+    if (grid_in == nullptr && it_begin > 0) return MCUBES_ERR_INVALID_ARG;   // a resumed range needs its grid
+    Problem pb;
+    int st = prepare(integrand_id, params, d, ncall, seed, 0, 0, iter_adjust > 0, precision, pb);
+    if (st) return st;
+    if (grid_in && !grid_ok(grid_in, d)) return MCUBES_ERR_INVALID_ARG;
+    std::vector<double> I, V;
+    st = run_range(pb, itmax, iter_adjust, it_begin, it_end, grid_in, prev_estimate, nullptr, stream, I, V, grid_out);
+    if (st) return st;
+    for (int k = 0; k < it_end - it_begin; ++k) {
+        iter_out[2 * k] = I[k];
+        iter_out[2 * k + 1] = V[k];
+    }
+    return MCUBES_OK;
+}
+
+int mcubes_combine(const double *iter, int n, int skip, mcubes_result *out)
+{
+    if (!iter || !out || n < 1 || skip < 0 || skip >= n) return MCUBES_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    std::vector<double> I, V;
+    for (int k = skip; k < n; ++k) {
+        if (!std::isfinite(iter[2 * k]) || !std::isfinite(iter[2 * k + 1]) || iter[2 * k + 1] < 0.0) {
+            out->status = MCUBES_ERR_INVALID_ARG;
+            return MCUBES_ERR_INVALID_ARG;
+        }
+        I.push_back(iter[2 * k]);
+        V.push_back(iter[2 * k + 1]);
+    }
+    combine(I, V, out);
+    out->iters_done = n - skip;
     out->status = MCUBES_OK;
     return MCUBES_OK;
 }

@@ -114,3 +114,41 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
             importlib.import_module("_capi_probe")
     finally:
         sys.path.remove(str(tmp_path))
+
+
+def test_combine_matches_inverse_variance_weighting(capi):
+    rng = np.random.default_rng(4)
+    I = rng.normal(2.0, 0.01, 9)
+    V = rng.uniform(1e-6, 1e-4, 9)
+    it = np.stack([I, V], axis=1)
+    for skip in (0, 1, 4, 8):
+        r = capi.combine(it, skip=skip)
+        w = 1.0 / V[skip:]
+        est = np.average(I[skip:], weights=w)
+        assert abs(r["estimate"] - est) <= 1e-14 * abs(est)
+        assert abs(r["error"] - np.sqrt(1.0 / w.sum())) <= 1e-14
+        n = len(w)
+        chi = np.sum(w * (I[skip:] - est) ** 2) / (n - 1) if n > 1 else 0.0
+        assert abs(r["chi2_dof"] - chi) <= 1e-12 * max(chi, 1.0)
+        assert r["iters_done"] == 9 - skip
+    # zero-variance iterations dominate: their mean, error 0
+    it2 = it.copy()
+    it2[3, 1] = 0.0
+    it2[5, 1] = 0.0
+    r = capi.combine(it2)
+    assert r["estimate"] == (it2[3, 0] + it2[5, 0]) / 2 and r["error"] == 0.0
+    for bad in (dict(skip=9), dict(skip=-1)):
+        with pytest.raises(capi.McubesError):
+            capi.combine(it, **bad)
+    it3 = it.copy()
+    it3[2, 1] = np.nan
+    with pytest.raises(capi.McubesError):
+        capi.combine(it3)
+
+
+def test_integrate_range_argument_checks(capi):
+    par = W.genz_params(W.GAUSSIAN, 3)
+    assert _status(lambda: capi.integrate_range(W.GAUSSIAN, par, 3, 1000, 6, 3, 2, 4, 0)) == 1   # no grid_in
+    assert _status(lambda: capi.integrate_range(W.GAUSSIAN, par, 3, 1000, 6, 3, 4, 4, 0)) == 1   # empty range
+    assert _status(lambda: capi.integrate_range(W.GAUSSIAN, par, 3, 1000, 6, 3, 5, 7, 0,
+                                                grid_in=oracle.uniform_grid(3))) == 1          # past itmax

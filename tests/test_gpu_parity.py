@@ -293,3 +293,20 @@ def test_invalid_arguments(capi):
     bad[0, 10] = bad[0, 9]
     with pytest.raises(capi.McubesError):
         capi.vsample_once(0, par, 2, 100, 1, grid_in=bad)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_checkpoint_resume_repeats_the_run(capi, mode):
+    """[0, 3) then [3, 7) from the returned grid equals the uninterrupted 7-iteration run."""
+    d, n, fid = 4, 200000, W.GAUSSIAN
+    par = _params(fid, d, seed=2)
+    full = capi.integrate(fid, par, d, n, 7, 4, 9, precision=mode, return_iters=True, return_grid=True)
+    a = capi.integrate_range(fid, par, d, n, 7, 4, 0, 3, 9, precision=mode)
+    b = capi.integrate_range(fid, par, d, n, 7, 4, 3, 7, 9, precision=mode, grid_in=a["grid"],
+                             prev_estimate=a["iters"][-1, 0])
+    iters = np.concatenate([a["iters"], b["iters"]])
+    rel = 1e-12 if mode == 0 else 1e-6
+    assert np.allclose(iters[:, 0], full["iters"][:, 0], rtol=rel, atol=0)
+    assert np.allclose(b["grid"], full["grid"], rtol=0, atol=1e-12 if mode == 0 else 1e-7)
+    r = capi.combine(iters)
+    assert math.isclose(r["estimate"], full["estimate"], rel_tol=rel)
