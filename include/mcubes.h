@@ -24,7 +24,8 @@
  *     asynchronous on that stream; every other call synchronises before it returns.
  *   - Grids are row-major d x (MCUBES_NBINS + 1) doubles: B[i][0] = 0 < B[i][1] < ... <
  *     B[i][500] = 1. Bin contributions are d x MCUBES_NBINS doubles.
- *   - Integrand parameters are 2d doubles: a[0..d-1] then u[0..d-1] (constant: a[0] = c).
+ *   - Integrand parameters are 2d doubles: a[0..d-1] then u[0..d-1] (constant: a[0] = c); the
+ *     rotated Gaussian takes d^2 + d (see MCUBES_ROTATED_GAUSSIAN).
  *   - Calls from different host threads are safe. Each thread has its own cached workspace,
  *     released by mcubes_shutdown() on that thread.
  */
@@ -65,7 +66,13 @@ extern "C" {
                                                                          Eq. 6: a_i = i+4, u_i = (3+i)/10 */
 #define MCUBES_ADDITION 6       /* sum x_i                               Sec. 5.3 */
 #define MCUBES_CONSTANT 7       /* a_0 */
-#define MCUBES_N_INTEGRANDS 8
+/* Correlated and multi-modal cases for the learned proposal (the paper has none):
+ *   double Gaussian: exp(-sum a_i^2 (x_i - u_i)^2) + exp(-sum a_i^2 (x_i - 1 + u_i)^2);
+ *   rotated Gaussian: exp(-(x - c)^T M (x - c)), params = M (d x d, row-major) then c (d), so
+ *     d^2 + d doubles instead of 2d. */
+#define MCUBES_DOUBLE_GAUSSIAN 8
+#define MCUBES_ROTATED_GAUSSIAN 9
+#define MCUBES_N_INTEGRANDS 10
 
 /* Arithmetic of the sampling path.
  *   MCUBES_FP64: the paper's setting. Draws, map, integrand and statistics are all FP64.
@@ -284,6 +291,51 @@ int mcubes_integrate_batch(int n_jobs, const mcubes_job *jobs, int itmax, int it
  * allocates and frees its own device memory.
  * Errors: as mcubes_integrate_batch. */
 int mcubes_tune_batch(int n_jobs, const mcubes_job *jobs, int precision, mcubes_batch_tuning *out);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned proposal (the target's extension; the paper's m-Cubes uses the VEGAS grid only): a
+ * coupling flow on [0,1]^d (neural importance sampling: coupling layers whose transformed axes
+ * go through piecewise-quadratic CDFs computed by a ReLU MLP). The MLPs run on the tensor
+ * cores with bf16 operands and FP32 accumulation.
+ *   Axis split of layer l: l mod 4 = 0 -> kept axes A = the first floor(d/2); 1 -> the halves
+ *   swapped; 2 -> A = the even axes; 3 -> swapped.
+ *   Parameters (FP32, flat), per layer: W1 [H x |A|], b1 [H], W2 [H x H], b2 [H],
+ *   W3 [|B|(2K+1) x H], b3 [|B|(2K+1)]; output slot s holds K bin-width logits, then K+1
+ *   edge-value logits, for axis B[s].
+ * Supported: 2 <= d <= 16, 1 <= layers <= 32, hidden in {32, 64, 128}, bins in {4, 8, 16, 32}
+ * (large d x bins x hidden combinations may exceed shared memory: CUDA error).
+ * Device buffers are row-major n x d FP32 (points), n FP32 (log densities).
+ * --------------------------------------------------------------------------------------- */
+typedef struct mcubes_flow_shape {
+    int32_t d, layers, hidden, bins;
+} mcubes_flow_shape;
+
+/* Number of FP32 parameters, or 0 for an unsupported shape. */
+int64_t mcubes_flow_param_count(const mcubes_flow_shape *shape);
+
+/* Scratch bytes for n samples (256-byte aligned buffer expected), or 0 if unsupported. */
+size_t mcubes_flow_work_bytes(const mcubes_flow_shape *shape, int64_t n);
+
+/* Density direction: d_z = flow(d_x), d_logq = log q(x). Asynchronous on stream.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA. */
+int mcubes_flow_forward_dev(const mcubes_flow_shape *shape, const float *d_params, int64_t n, const float *d_x,
+                            float *d_z, float *d_logq, void *d_work, size_t work_bytes, void *stream);
+
+/* Sampling direction: d_x = flow^-1(d_z), d_logq = log q(x). Asynchronous on stream. */
+int mcubes_flow_inverse_dev(const mcubes_flow_shape *shape, const float *d_params, int64_t n, const float *d_z,
+                            float *d_x, float *d_logq, void *d_work, size_t work_bytes, void *stream);
+
+/* Loss and gradient on n samples x with weights w (normalised to sum 1 by the caller):
+ *   loss_kind 0 (variance, chi^2): L = sum w / q(x)   (w = f^2 J from the grid sampler);
+ *   loss_kind 1 (KL):              L = -sum w log q(x) (w = |f| J).
+ * d_grad (param_count FP32) and d_loss[0] accumulate; zero them first. Asynchronous. */
+int mcubes_flow_grad_dev(const mcubes_flow_shape *shape, const float *d_params, int64_t n, const float *d_x,
+                         const float *d_w, int loss_kind, float *d_grad, float *d_loss, void *d_work,
+                         size_t work_bytes, void *stream);
+
+/* Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step >= 1) on the FP32 parameters. */
+int mcubes_flow_adam_dev(int64_t n_params, float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
+                         float lr, void *stream);
 
 /* Philox4x32-10 on the device, for checking the generator. out[4j..4j+3] = Philox(ctr[4j..4j+3],
  * key = (seed mod 2^32, seed >> 32)) for j < n.

@@ -21,6 +21,7 @@ ND = 500
 DMAX = 16
 
 OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS, ADDITION, CONSTANT = range(8)
+DOUBLE_GAUSSIAN, ROTATED_GAUSSIAN = 8, 9
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mcubes_oracle.c")

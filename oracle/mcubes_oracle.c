@@ -48,7 +48,10 @@ enum {
                              ; Eq. 6 has a_i = i + 4, u_i = (3 + i)/10 */
     ORC_ADDITION = 6,     /* sum x_i                                ; Sec. 5.3 */
     ORC_CONSTANT = 7,     /* a_1                                    ; exactness check */
-    ORC_N_INTEGRANDS = 8
+    ORC_DOUBLE_GAUSSIAN = 8, /* exp(-sum a_i^2 (x_i-u_i)^2) + exp(-sum a_i^2 (x_i-1+u_i)^2): two peaks
+                                mirrored through the centre (the learned proposal's test case) */
+    ORC_ROTATED_GAUSSIAN = 9,/* exp(-(x-c)^T M (x-c)); params are M (d x d, row-major) then c (d) */
+    ORC_N_INTEGRANDS = 10
 };
 
 /* ------------------------------------------------------------------------------------ */
@@ -154,6 +157,21 @@ double orc_integrand(int id, int d, const double *par, const double *x, int fp32
         return s;
     case ORC_CONSTANT:
         return a[0];
+    case ORC_DOUBLE_GAUSSIAN: {
+        double s2 = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double t1 = x[i] - u[i], t2 = x[i] - (1.0 - u[i]);
+            s += a[i] * a[i] * t1 * t1;
+            s2 += a[i] * a[i] * t2 * t2;
+        }
+        return exp(-s) + exp(-s2);
+    }
+    case ORC_ROTATED_GAUSSIAN: {
+        const double *M = par, *c = par + (size_t)d * d;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) s += (x[i] - c[i]) * M[i * d + j] * (x[j] - c[j]);
+        return exp(-s);
+    }
     default:
         return NAN;
     }

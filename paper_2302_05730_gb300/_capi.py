@@ -64,6 +64,11 @@ class BatchTuning(ctypes.Structure):
                         hist_mode=self.hist_mode[d]) for d in range(1, DMAX + 1) if self.block_threads[d]}
 
 
+class FlowShape(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("layers", ctypes.c_int32), ("hidden", ctypes.c_int32),
+                ("bins", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libmcubes.so is not built ({LIB_PATH}); run "
@@ -91,6 +96,13 @@ def _load():
         "mcubes_integrate_batch": (i32, [i32, ctypes.POINTER(Job), i32, i32, i32, ctypes.POINTER(BatchTuning), vp,
                                          ctypes.POINTER(Result), dp]),
         "mcubes_tune_batch": (i32, [i32, ctypes.POINTER(Job), i32, ctypes.POINTER(BatchTuning)]),
+        "mcubes_flow_param_count": (i64, [ctypes.POINTER(FlowShape)]),
+        "mcubes_flow_work_bytes": (ctypes.c_size_t, [ctypes.POINTER(FlowShape), i64]),
+        "mcubes_flow_forward_dev": (i32, [ctypes.POINTER(FlowShape), vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+        "mcubes_flow_inverse_dev": (i32, [ctypes.POINTER(FlowShape), vp, i64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+        "mcubes_flow_grad_dev": (i32, [ctypes.POINTER(FlowShape), vp, i64, vp, vp, i32, vp, vp, vp, ctypes.c_size_t,
+                                       vp]),
+        "mcubes_flow_adam_dev": (i32, [i64, vp, vp, vp, vp, i32, ctypes.c_float, vp]),
         "mcubes_philox_dev": (i32, [vp, u64, u64, i32, vp, vp]),
         "mcubes_status_string": (ctypes.c_char_p, [i32]),
         "mcubes_last_cuda_error": (i32, []),
@@ -337,6 +349,39 @@ def tune_batch(jobs, precision=FP64) -> BatchTuning:
     t = BatchTuning()
     _check(_lib.mcubes_tune_batch(len(jobs), arr, precision, ctypes.byref(t)), "tune_batch")
     return t
+
+
+def flow_shape(d, layers, hidden, bins) -> FlowShape:
+    return FlowShape(int(d), int(layers), int(hidden), int(bins))
+
+
+def flow_param_count(shape: FlowShape) -> int:
+    return int(_lib.mcubes_flow_param_count(ctypes.byref(shape)))
+
+
+def flow_work_bytes(shape: FlowShape, n: int) -> int:
+    return int(_lib.mcubes_flow_work_bytes(ctypes.byref(shape), int(n)))
+
+
+def flow_forward_dev(shape, d_params, n, d_x, d_z, d_logq, d_work, work_bytes, stream=None):
+    _check(_lib.mcubes_flow_forward_dev(ctypes.byref(shape), _dptr(d_params), int(n), _dptr(d_x), _dptr(d_z),
+                                        _dptr(d_logq), _dptr(d_work), int(work_bytes), _stream(stream)), "flow_forward")
+
+
+def flow_inverse_dev(shape, d_params, n, d_z, d_x, d_logq, d_work, work_bytes, stream=None):
+    _check(_lib.mcubes_flow_inverse_dev(ctypes.byref(shape), _dptr(d_params), int(n), _dptr(d_z), _dptr(d_x),
+                                        _dptr(d_logq), _dptr(d_work), int(work_bytes), _stream(stream)), "flow_inverse")
+
+
+def flow_grad_dev(shape, d_params, n, d_x, d_w, loss_kind, d_grad, d_loss, d_work, work_bytes, stream=None):
+    _check(_lib.mcubes_flow_grad_dev(ctypes.byref(shape), _dptr(d_params), int(n), _dptr(d_x), _dptr(d_w),
+                                     int(loss_kind), _dptr(d_grad), _dptr(d_loss), _dptr(d_work), int(work_bytes),
+                                     _stream(stream)), "flow_grad")
+
+
+def flow_adam_dev(n_params, d_params, d_grad, d_m, d_v, step, lr, stream=None):
+    _check(_lib.mcubes_flow_adam_dev(int(n_params), _dptr(d_params), _dptr(d_grad), _dptr(d_m), _dptr(d_v),
+                                     int(step), float(lr), _stream(stream)), "flow_adam")
 
 
 def philox_dev(d_ctr, n, seed, impl, d_out, stream=None):

@@ -44,7 +44,7 @@ def _units():
         name = os.path.splitext(os.path.basename(src))[0]
         if name == "vsample_inst":
             for f32 in (0, 1):
-                for fid in range(8):
+                for fid in range(10):
                     for part in (0, 1):   # 0: single-job kernels, 1: batched kernels
                         units.append((f"vsample_{'f32' if f32 else 'f64'}_{fid}_{'batch' if part else 'one'}", src,
                                       [f"-DMCUBES_F32={f32}", f"-DMCUBES_FID={fid}", f"-DMCUBES_PART={part}"]))

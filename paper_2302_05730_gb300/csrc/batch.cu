@@ -25,14 +25,16 @@ using BatchLauncher = int (*)(int, const BatchJob *, const BatchTile *, int, int
 
 BatchLauncher batch_launcher_for(int prec, int fid)
 {
-    static const BatchLauncher f64[8] = {
+    static const BatchLauncher f64[10] = {
         launch_vsample_batch_f64_0, launch_vsample_batch_f64_1, launch_vsample_batch_f64_2,
         launch_vsample_batch_f64_3, launch_vsample_batch_f64_4, launch_vsample_batch_f64_5,
-        launch_vsample_batch_f64_6, launch_vsample_batch_f64_7};
-    static const BatchLauncher f32[8] = {
+        launch_vsample_batch_f64_6, launch_vsample_batch_f64_7, launch_vsample_batch_f64_8,
+        launch_vsample_batch_f64_9};
+    static const BatchLauncher f32[10] = {
         launch_vsample_batch_f32_0, launch_vsample_batch_f32_1, launch_vsample_batch_f32_2,
         launch_vsample_batch_f32_3, launch_vsample_batch_f32_4, launch_vsample_batch_f32_5,
-        launch_vsample_batch_f32_6, launch_vsample_batch_f32_7};
+        launch_vsample_batch_f32_6, launch_vsample_batch_f32_7, launch_vsample_batch_f32_8,
+        launch_vsample_batch_f32_9};
     return prec == MCUBES_FP32_EVAL ? f32[fid] : f64[fid];
 }
 

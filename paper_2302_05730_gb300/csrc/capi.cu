@@ -91,7 +91,7 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
     if (st) return st;
     if (pb.p > 0xFFFFFFFFll) return MCUBES_ERR_INVALID_ARG;
     if (prec == MCUBES_FP32_EVAL && pb.g > (1 << 24)) return MCUBES_ERR_INVALID_ARG;
-    for (int i = 0; i < 2 * d; ++i)
+    for (int i = 0; i < param_len(fid, d); ++i)
         if (!std::isfinite(params[i])) return MCUBES_ERR_INVALID_ARG;
 
     pb.fid = fid;
@@ -118,10 +118,24 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
     IntegrandParams &ip = P.ip;
     ip.d = d;
     const double *a = params, *u = params + d;
-    for (int i = 0; i < d; ++i) {
-        ip.a[i] = a[i];
-        ip.u[i] = u[i];
+    if (fid == MCUBES_ROTATED_GAUSSIAN) {   // params: M (d x d), then the centre c
+        u = params + (size_t)d * d;
+        for (int i = 0; i < d * d; ++i) {
+            ip.m[i] = params[i];
+            ip.fm[i] = (float)(params[i] * kLog2e);
+        }
+        for (int i = 0; i < d; ++i) {
+            ip.u[i] = u[i];
+            ip.fu[i] = (float)u[i];
+        }
+    } else {
+        for (int i = 0; i < d; ++i) {
+            ip.a[i] = a[i];
+            ip.u[i] = u[i];
+        }
     }
+    if (fid == MCUBES_DOUBLE_GAUSSIAN)
+        for (int i = 0; i < d; ++i) ip.b[i] = 1.0 - u[i];
     if (prec == MCUBES_FP64) {
         double s = 1.0;
         for (int i = 0; i < d; ++i) s *= (double)kNB;
@@ -174,6 +188,15 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
         case MCUBES_CONSTANT:
             F = a[0];
             break;
+        case MCUBES_DOUBLE_GAUSSIAN:
+            for (int i = 0; i < d; ++i) {
+                ip.fa[i] = (float)(a[i] * kSqrtLog2e);
+                ip.fu[i] = (float)u[i];
+                ip.fb[i] = (float)(1.0 - u[i]);
+            }
+            break;
+        case MCUBES_ROTATED_GAUSSIAN:
+            break;   // fm, fu set above
         }
         if (!std::isfinite(F)) return MCUBES_ERR_INVALID_ARG;
         P.fscale = F;
@@ -185,12 +208,14 @@ using Launcher = int (*)(int, const VsampleParams &, const LaunchReq &, cudaStre
 
 static Launcher launcher_for(int prec, int fid)
 {
-    static const Launcher f64[8] = {launch_vsample_f64_0, launch_vsample_f64_1, launch_vsample_f64_2,
-                                    launch_vsample_f64_3, launch_vsample_f64_4, launch_vsample_f64_5,
-                                    launch_vsample_f64_6, launch_vsample_f64_7};
-    static const Launcher f32[8] = {launch_vsample_f32_0, launch_vsample_f32_1, launch_vsample_f32_2,
-                                    launch_vsample_f32_3, launch_vsample_f32_4, launch_vsample_f32_5,
-                                    launch_vsample_f32_6, launch_vsample_f32_7};
+    static const Launcher f64[10] = {launch_vsample_f64_0, launch_vsample_f64_1, launch_vsample_f64_2,
+                                     launch_vsample_f64_3, launch_vsample_f64_4, launch_vsample_f64_5,
+                                     launch_vsample_f64_6, launch_vsample_f64_7, launch_vsample_f64_8,
+                                     launch_vsample_f64_9};
+    static const Launcher f32[10] = {launch_vsample_f32_0, launch_vsample_f32_1, launch_vsample_f32_2,
+                                     launch_vsample_f32_3, launch_vsample_f32_4, launch_vsample_f32_5,
+                                     launch_vsample_f32_6, launch_vsample_f32_7, launch_vsample_f32_8,
+                                     launch_vsample_f32_9};
     return prec == MCUBES_FP32_EVAL ? f32[fid] : f64[fid];
 }
 

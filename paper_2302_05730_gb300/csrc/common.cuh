@@ -54,6 +54,8 @@ struct IntegrandParams {
     float fb[kDMax];   // FP32 auxiliary per axis (discontinuous: min(u, 1))
     float fc;          // FP32 scalar (oscillatory: u_0 mod 1)
     int d;
+    double m[kDMax * kDMax];   // rotated Gaussian: the quadratic form M (row-major)
+    float fm[kDMax * kDMax];   // ... as log2(e) M in single precision
 };
 
 // Everything one V-Sample launch needs, passed by value.

@@ -17,6 +17,8 @@
 //                  f/F = 2^(sum fa (x - fb)) inside the cut, else 0; F = exp(sum a min(u,1))
 //   addition       f/F = sum x; F = 1
 //   constant       f/F = 1; F = a_0
+//   double Gaussian fa = a sqrt(log2 e), fu = u, fb = 1 - u; f/F = 2^-s1 + 2^-s2; F = 1
+//   rotated Gaussian fm = log2(e) M, fu = c; f/F = 2^-((x-c)^T fm (x-c)); F = 1
 #pragma once
 
 #include "common.cuh"
@@ -32,7 +34,9 @@ enum : int {
     kDiscontinuous = 5,
     kAddition = 6,
     kConstant = 7,
-    kNumIntegrands = 8
+    kDoubleGaussian = 8,
+    kRotatedGaussian = 9,
+    kNumIntegrands = 10
 };
 
 // 2^x, hardware approximation (relative error about 2^-22), subnormal results kept.
@@ -63,8 +67,10 @@ __device__ __forceinline__ T inv_pow(T base)
 template <int FID, int D>
 struct Integrand64 {
     double s = 0.0;
+    double s2 = 0.0;
     double prod = 1.0;
     bool inside = true;
+    double xs[FID == kRotatedGaussian ? D : 1];
 
     __device__ __forceinline__ void add(int i, double x, const IntegrandParams &ip)
     {
@@ -83,6 +89,13 @@ struct Integrand64 {
             s = fma(ip.a[i], x, s);
         } else if constexpr (FID == kAddition) {
             s += x;
+        } else if constexpr (FID == kDoubleGaussian) {
+            const double v1 = ip.a[i] * (x - ip.u[i]);
+            const double v2 = ip.a[i] * (x - ip.b[i]);   // b = 1 - u
+            s = fma(v1, v1, s);
+            s2 = fma(v2, v2, s2);
+        } else if constexpr (FID == kRotatedGaussian) {
+            xs[i] = x - ip.u[i];
         }
     }
 
@@ -100,6 +113,18 @@ struct Integrand64 {
             return inside ? exp(s) : 0.0;
         } else if constexpr (FID == kAddition) {
             return s;
+        } else if constexpr (FID == kDoubleGaussian) {
+            return exp(-s) + exp(-s2);
+        } else if constexpr (FID == kRotatedGaussian) {
+            double q = 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                double r = 0.0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) r = fma(ip.m[i * D + j], xs[j], r);
+                q = fma(xs[i], r, q);
+            }
+            return exp(-q);
         } else {
             return ip.a[0];
         }
@@ -110,8 +135,10 @@ struct Integrand64 {
 template <int FID, int D>
 struct Integrand32 {
     float s = 0.0f;
+    float s2 = 0.0f;
     float prod = 1.0f;
     bool inside = true;
+    float xs[FID == kRotatedGaussian ? D : 1];
 
     __device__ __forceinline__ void add(int i, float x, const IntegrandParams &ip)
     {
@@ -130,6 +157,13 @@ struct Integrand32 {
             s = fmaf(ip.fa[i], x - ip.fb[i], s);
         } else if constexpr (FID == kAddition) {
             s += x;
+        } else if constexpr (FID == kDoubleGaussian) {
+            const float v1 = ip.fa[i] * (x - ip.fu[i]);
+            const float v2 = ip.fa[i] * (x - ip.fb[i]);
+            s = fmaf(v1, v1, s);
+            s2 = fmaf(v2, v2, s2);
+        } else if constexpr (FID == kRotatedGaussian) {
+            xs[i] = x - ip.fu[i];
         }
     }
 
@@ -149,6 +183,18 @@ struct Integrand32 {
             return inside ? ex2_approx(s) : 0.0f;
         } else if constexpr (FID == kAddition) {
             return s;
+        } else if constexpr (FID == kDoubleGaussian) {
+            return ex2_approx(-s) + ex2_approx(-s2);
+        } else if constexpr (FID == kRotatedGaussian) {
+            float q = 0.0f;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                float r = 0.0f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) r = fmaf(ip.fm[i * D + j], xs[j], r);
+                q = fmaf(xs[i], r, q);
+            }
+            return ex2_approx(-q);
         } else {
             return 1.0f;
         }

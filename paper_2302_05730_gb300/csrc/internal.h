@@ -17,6 +17,10 @@ struct Problem {
     VsampleParams P;
 };
 
+// Number of FP64 parameters integrand fid takes at dimension d (2d, or d^2 + d for the
+// rotated Gaussian).
+inline int param_len(int fid, int d) { return fid == 9 ? d * d + d : 2 * d; }
+
 // Host helpers of capi.cu, shared with the batched path.
 int cuda_status(cudaError_t e);   // MCUBES_* status of a CUDA error (records it per thread)
 int stratify(int d, int64_t n, int64_t *g, int64_t *m, int64_t *p);
@@ -48,6 +52,8 @@ MCUBES_DECLARE_LAUNCHER(f64, 4)
 MCUBES_DECLARE_LAUNCHER(f64, 5)
 MCUBES_DECLARE_LAUNCHER(f64, 6)
 MCUBES_DECLARE_LAUNCHER(f64, 7)
+MCUBES_DECLARE_LAUNCHER(f64, 8)
+MCUBES_DECLARE_LAUNCHER(f64, 9)
 MCUBES_DECLARE_LAUNCHER(f32, 0)
 MCUBES_DECLARE_LAUNCHER(f32, 1)
 MCUBES_DECLARE_LAUNCHER(f32, 2)
@@ -56,6 +62,8 @@ MCUBES_DECLARE_LAUNCHER(f32, 4)
 MCUBES_DECLARE_LAUNCHER(f32, 5)
 MCUBES_DECLARE_LAUNCHER(f32, 6)
 MCUBES_DECLARE_LAUNCHER(f32, 7)
+MCUBES_DECLARE_LAUNCHER(f32, 8)
+MCUBES_DECLARE_LAUNCHER(f32, 9)
 #undef MCUBES_DECLARE_LAUNCHER
 
 // Batched launchers: one (precision, integrand) slice, any d. hist_mode 0 = block-private
@@ -74,6 +82,8 @@ MCUBES_DECLARE_BATCH_LAUNCHER(f64, 4)
 MCUBES_DECLARE_BATCH_LAUNCHER(f64, 5)
 MCUBES_DECLARE_BATCH_LAUNCHER(f64, 6)
 MCUBES_DECLARE_BATCH_LAUNCHER(f64, 7)
+MCUBES_DECLARE_BATCH_LAUNCHER(f64, 8)
+MCUBES_DECLARE_BATCH_LAUNCHER(f64, 9)
 MCUBES_DECLARE_BATCH_LAUNCHER(f32, 0)
 MCUBES_DECLARE_BATCH_LAUNCHER(f32, 1)
 MCUBES_DECLARE_BATCH_LAUNCHER(f32, 2)
@@ -82,6 +92,8 @@ MCUBES_DECLARE_BATCH_LAUNCHER(f32, 4)
 MCUBES_DECLARE_BATCH_LAUNCHER(f32, 5)
 MCUBES_DECLARE_BATCH_LAUNCHER(f32, 6)
 MCUBES_DECLARE_BATCH_LAUNCHER(f32, 7)
+MCUBES_DECLARE_BATCH_LAUNCHER(f32, 8)
+MCUBES_DECLARE_BATCH_LAUNCHER(f32, 9)
 #undef MCUBES_DECLARE_BATCH_LAUNCHER
 
 int launch_rebin(int d, const double *d_grid_in, const double *d_C, double *d_grid_out,

@@ -14,6 +14,7 @@ from __future__ import annotations
 import numpy as np
 
 OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS, ADDITION, CONSTANT = range(8)
+DOUBLE_GAUSSIAN, ROTATED_GAUSSIAN = 8, 9
 
 NAMES = {
     OSCILLATORY: "oscillatory",
@@ -24,6 +25,8 @@ NAMES = {
     DISCONTINUOUS: "discontinuous",
     ADDITION: "addition",
     CONSTANT: "constant",
+    DOUBLE_GAUSSIAN: "double_gaussian",
+    ROTATED_GAUSSIAN: "rotated_gaussian",
 }
 BY_NAME = {v: k for k, v in NAMES.items()}
 
@@ -85,3 +88,21 @@ def batch_jobs(n_jobs: int = 4096, seed: int = 0, dmin: int = 2, dmax: int = 8,
         n = int(round(float(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))))
         jobs.append(dict(fid=GAUSSIAN, d=d, params=np.concatenate([a, u]), ncall=n))
     return jobs
+
+
+def double_gaussian_params(d: int, a: float = 10.0, u: float = 0.25):
+    """exp(-a^2 |x - u 1|^2) + exp(-a^2 |x - (1-u) 1|^2): centres u 1 and (1-u) 1."""
+    return np.concatenate([np.full(d, float(a)), np.full(d, float(u))])
+
+
+def rotated_gaussian_params(d: int, seed: int = 0, lam_min: float = 1.0, lam_max: float = 400.0, centre: float = 0.5):
+    """exp(-(x - c)^T Q diag(lam) Q^T (x - c)) with Q from the QR factorisation of a seeded Gaussian
+    matrix and lam = linspace(lam_min, lam_max, d). Parameters: M = Q diag(lam) Q^T (d x d,
+    row-major), then c (d)."""
+    rng = np.random.default_rng([0x507A7E, int(seed), int(d)])
+    Q, R = np.linalg.qr(rng.normal(size=(d, d)))
+    Q = Q * np.sign(np.diag(R))
+    lam = np.linspace(lam_min, lam_max, d)
+    M = (Q * lam) @ Q.T
+    M = (M + M.T) / 2.0
+    return np.concatenate([M.ravel(), np.full(d, float(centre))])

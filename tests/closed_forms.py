@@ -19,6 +19,7 @@ from math import atan, erf, exp, factorial, pi, sqrt
 import cmath
 
 OSCILLATORY, PRODUCT_PEAK, CORNER_PEAK, GAUSSIAN, C0, DISCONTINUOUS, ADDITION, CONSTANT = range(8)
+DOUBLE_GAUSSIAN, ROTATED_GAUSSIAN = 8, 9
 
 
 def _corner_exact(a):
@@ -69,7 +70,28 @@ def exact(fid, a, u):
         return d / 2.0
     if fid == CONSTANT:
         return a[0]
+    if fid == DOUBLE_GAUSSIAN:   # two Gaussians, centres u and 1 - u
+        return exact(GAUSSIAN, a, u) + exact(GAUSSIAN, a, [1.0 - v for v in u])
     raise ValueError(fid)
+
+
+def rotated_gaussian_exact(M, c):
+    """int_[0,1]^d exp(-(x-c)^T M (x-c)) dx = pi^{d/2} / sqrt(det M) * P(X in [0,1]^d) for
+    X ~ N(c, (2M)^-1); the box probability from scipy's multivariate normal CDF by
+    inclusion-exclusion over the 2^d corners."""
+    import itertools
+    import numpy as np
+    from scipy.stats import multivariate_normal
+    M = np.asarray(M, dtype=float)
+    c = np.asarray(c, dtype=float)
+    d = len(c)
+    cov = np.linalg.inv(2.0 * M)
+    mvn = multivariate_normal(mean=c, cov=cov, abseps=1e-12, releps=1e-10, maxpts=10 ** 7)
+    prob = 0.0
+    for corner in itertools.product([0, 1], repeat=d):
+        sign = (-1) ** (d - sum(corner))
+        prob += sign * mvn.cdf(np.array(corner, dtype=float))
+    return float(np.pi ** (d / 2) / np.sqrt(np.linalg.det(M)) * prob)
 
 
 def paper_params(fid, d):

@@ -64,7 +64,7 @@ def test_argument_checks_return_status_codes(capi):
     par = W.genz_params(W.GAUSSIAN, 3)
     assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 0, 1000, 3, 1, 0)) == 2
     assert _status(lambda: capi.integrate(W.GAUSSIAN, np.ones(34), 17, 1000, 3, 1, 0)) == 2
-    assert _status(lambda: capi.integrate(8, par, 3, 1000, 3, 1, 0)) == 3
+    assert _status(lambda: capi.integrate(10, par, 3, 1000, 3, 1, 0)) == 3
     assert _status(lambda: capi.integrate(-1, par, 3, 1000, 3, 1, 0)) == 3
     assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 3, 1, 3, 1, 0)) == 1       # ncall < 2
     assert _status(lambda: capi.integrate(W.GAUSSIAN, par, 3, 1000, 0, 0, 0)) == 1    # itmax < 1

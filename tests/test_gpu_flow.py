@@ -1,0 +1,174 @@
+"""GPU parity of the learned-proposal kernels (coupling flow) against the numpy oracle
+(oracle/flow.py).
+
+  - Density and sampling directions: against the oracle with bf16 rounding of the MLP operands
+    (the GPU's own precision), so only the order of FP32 sums and the FP32 coupling arithmetic
+    differ. A bf16 tie can still round the other way now and then (one activation off by one
+    bf16 step), which bounds the worst case. The typical (median) error is held much tighter.
+  - Gradients: against central finite differences of the oracle's FP64 loss. The GPU
+    differentiates through bf16 MLP operands, so the comparison is on the direction (cosine)
+    and size (relative norm) of the gradient, at a bf16-level tolerance. A wrong sign, index or
+    term shows up as an O(1) error.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import flow as F
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_05730_gb300 import capi as c
+    return c
+
+
+def _params(d, L, H, K, seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, scale, F.n_params(d, L, H, K)).astype(np.float32)
+
+
+def _work(capi, shape, n):
+    nb = capi.flow_work_bytes(shape, n)
+    buf = torch.empty(nb // 4 + 128, dtype=torch.float32, device="cuda")
+    return (buf.data_ptr() + 255) // 256 * 256, nb, buf
+
+
+SHAPES = [(2, 2, 32, 4), (4, 2, 32, 8), (5, 3, 64, 16), (8, 4, 64, 16), (7, 5, 32, 8), (10, 6, 128, 16)]
+
+
+@pytest.mark.parametrize("d,L,H,K", SHAPES)
+def test_flow_density_and_sampling_match_oracle(capi, d, L, H, K):
+    n = 777   # not a multiple of the 64-sample tile
+    p = _params(d, L, H, K, seed=d * 100 + L)
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0.0, 1.0, (n, d)).astype(np.float32)
+    shape = capi.flow_shape(d, L, H, K)
+    ws, nb, keep = _work(capi, shape, n)
+    dp = torch.from_numpy(p).cuda()
+    dx = torch.from_numpy(x).cuda()
+    dz = torch.empty_like(dx)
+    dl = torch.empty(n, dtype=torch.float32, device="cuda")
+    capi.flow_forward_dev(shape, dp, n, dx, dz, dl, ws, nb)
+    torch.cuda.synchronize()
+    z_ref, lq_ref = F.forward(p.astype(np.float64), x.astype(np.float64), d, L, H, K, use_bf16=True)
+    ez = np.abs(dz.cpu().numpy() - z_ref)
+    el = np.abs(dl.cpu().numpy() - lq_ref)
+    assert np.median(ez) < 2e-6 and ez.max() < 3e-3, (np.median(ez), ez.max())
+    assert np.median(el) < 2e-5 and el.max() < 3e-2, (np.median(el), el.max())
+    # sampling direction
+    zz = rng.uniform(0.0, 1.0, (n, d)).astype(np.float32)
+    dzz = torch.from_numpy(zz).cuda()
+    dxx = torch.empty_like(dzz)
+    dl2 = torch.empty_like(dl)
+    capi.flow_inverse_dev(shape, dp, n, dzz, dxx, dl2, ws, nb)
+    torch.cuda.synchronize()
+    x_ref, lq2_ref = F.inverse(p.astype(np.float64), zz.astype(np.float64), d, L, H, K, use_bf16=True)
+    ex = np.abs(dxx.cpu().numpy() - x_ref)
+    assert np.median(ex) < 2e-6 and ex.max() < 3e-3, (np.median(ex), ex.max())
+    el2 = np.abs(dl2.cpu().numpy() - lq2_ref)
+    assert np.median(el2) < 2e-5 and el2.max() < 3e-2
+    # round trip on the device: density(sample(z)) = z, with the same log-density
+    dz3 = torch.empty_like(dzz)
+    dl3 = torch.empty_like(dl)
+    capi.flow_forward_dev(shape, dp, n, dxx, dz3, dl3, ws, nb)
+    torch.cuda.synchronize()
+    assert np.median(np.abs(dz3.cpu().numpy() - zz)) < 1e-5
+    assert np.median(np.abs(dl3.cpu().numpy() - dl2.cpu().numpy())) < 1e-4
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d,L,H,K,sub", [(4, 2, 32, 4, None), (8, 4, 64, 16, 400)])
+def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, kind):
+    n = 300
+    p = _params(d, L, H, K, seed=7 + d, scale=0.2)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0.0, 1.0, (n, d))
+    f = np.exp(-np.sum((x - 0.35) ** 2, axis=1) * 8.0)
+    w = f ** 2 if kind == 0 else f
+    w = w / w.sum()
+    shape = capi.flow_shape(d, L, H, K)
+    ws, nb, keep = _work(capi, shape, n)
+    dp = torch.from_numpy(p).cuda()
+    dx = torch.from_numpy(x.astype(np.float32)).cuda()
+    dw = torch.from_numpy(w.astype(np.float32)).cuda()
+    grad = torch.zeros(p.size, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    capi.flow_grad_dev(shape, dp, n, dx, dw, kind, grad, loss, ws, nb)
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy().astype(np.float64)
+    kname = "variance" if kind == 0 else "kl"
+    l_ref = F.loss(p.astype(np.float64), x.astype(np.float32).astype(np.float64), w, d, L, H, K, kname)
+    assert abs(loss.item() - l_ref) <= 2e-2 * abs(l_ref)
+    idx = np.arange(p.size) if sub is None else np.random.default_rng(3).choice(p.size, sub, replace=False)
+    # bias the sample towards parameters that matter: include the output layer of the last layer
+    g_ref = F.grad_fd(p.astype(np.float64), x.astype(np.float32).astype(np.float64), w, d, L, H, K, kname,
+                      eps=1e-4, idx=idx)
+    a, b = g[idx], g_ref
+    cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+    rel = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert cos > 0.995 and rel < 0.08, (cos, rel)
+
+
+def test_adam_step(capi):
+    n = 1000
+    rng = np.random.default_rng(0)
+    p = rng.normal(size=n).astype(np.float32)
+    g = rng.normal(size=n).astype(np.float32)
+    m = np.zeros(n, np.float32)
+    v = np.zeros(n, np.float32)
+    dp, dg, dm, dv = (torch.from_numpy(a.copy()).cuda() for a in (p, g, m, v))
+    for step in (1, 2, 3):
+        capi.flow_adam_dev(n, dp, dg, dm, dv, step, 1e-2)
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        p = p - 1e-2 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
+    torch.cuda.synchronize()
+    assert np.allclose(dp.cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+
+
+def test_training_lowers_the_variance(capi):
+    """A few hundred Adam steps on samples of a correlated 2-d peak: the variance loss falls."""
+    d, L, H, K = 2, 4, 32, 8
+    shape = capi.flow_shape(d, L, H, K)
+    npar = capi.flow_param_count(shape)
+    rng = np.random.default_rng(4)
+    p = rng.normal(0.0, 0.05, npar).astype(np.float32)
+    for lay in F.unpack(p, d, L, H, K):
+        lay["W3"][...] = 0.0
+        lay["b3"][...] = 0.0
+    n = 1 << 14
+    x = rng.uniform(0, 1, (n, d))
+    u = x - 0.5
+    f = np.exp(-200.0 * (u[:, 0] - u[:, 1]) ** 2 - 10.0 * (u[:, 0] + u[:, 1]) ** 2)   # rotated, correlated
+    w = f ** 2
+    w = w / w.sum()
+    ws, nb, keep = _work(capi, shape, n)
+    dp = torch.from_numpy(p).cuda()
+    dx = torch.from_numpy(x.astype(np.float32)).cuda()
+    dw = torch.from_numpy(w.astype(np.float32)).cuda()
+    grad = torch.zeros(npar, dtype=torch.float32, device="cuda")
+    m = torch.zeros_like(grad)
+    v = torch.zeros_like(grad)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(1, 301):
+        grad.zero_()
+        loss.zero_()
+        capi.flow_grad_dev(shape, dp, n, dx, dw, 0, grad, loss, ws, nb)
+        capi.flow_adam_dev(npar, dp, grad, m, v, step, 5e-3)
+        losses.append(loss.item())
+    assert losses[-1] < 0.3 * losses[0], (losses[0], losses[-1])
+    # the loss of the trained parameters agrees with the oracle's (bf16 MLP operands)
+    loss.zero_()
+    grad.zero_()
+    capi.flow_grad_dev(shape, dp, n, dx, dw, 0, grad, loss, ws, nb)
+    torch.cuda.synchronize()
+    x_ref = x.astype(np.float32).astype(np.float64)
+    l_ref = F.loss(dp.cpu().numpy().astype(np.float64), x_ref, w, d, L, H, K, "variance", use_bf16=True)
+    assert abs(loss.item() - l_ref) < 2e-2 * l_ref, (loss.item(), l_ref)

@@ -38,7 +38,7 @@ from paper_2302_05730_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 EPS = np.finfo(np.float64).eps
-ALL = list(range(8))
+ALL = list(range(10))
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +50,10 @@ def capi():
 
 
 def _params(fid, d, seed=0):
+    if fid == W.DOUBLE_GAUSSIAN:
+        return W.double_gaussian_params(d, a=6.0, u=0.3)
+    if fid == W.ROTATED_GAUSSIAN:
+        return W.rotated_gaussian_params(d, seed=seed, lam_min=1.0, lam_max=40.0)
     if fid == W.CONSTANT:
         return W.constant_params(d, 2.5)
     if fid == W.ADDITION:
@@ -127,6 +131,8 @@ CASES = []
 for fid in ALL:
     for d, n in [(1, 1000), (2, 5000), (3, 30000), (5, 20000), (8, 40000)]:
         CASES.append((fid, d, n))
+CASES += [(W.DOUBLE_GAUSSIAN, 3, 30000), (W.DOUBLE_GAUSSIAN, 8, 40000), (W.ROTATED_GAUSSIAN, 2, 5000),
+          (W.ROTATED_GAUSSIAN, 5, 20000), (W.ROTATED_GAUSSIAN, 8, 40000)]
 CASES += [(W.GAUSSIAN, 12, 2 * 3 ** 12), (W.C0, 16, 2 ** 17 + 7), (W.PRODUCT_PEAK, 10, 2 * 3 ** 10 + 5),
           (W.DISCONTINUOUS, 6, 123457), (W.OSCILLATORY, 4, 31), (W.CORNER_PEAK, 2, 2),
           (W.ADDITION, 7, 2 * 5 ** 7 + 99)]

@@ -172,3 +172,34 @@ def test_config1_gaussian_reference_value():
     assert math.isclose(ref, (math.sqrt(math.pi) / 10 * math.erf(5.0)) ** 3, rel_tol=1e-15)
     est, sig, chi2, *_ = oracle.integrate(W.GAUSSIAN, d, par, 10 ** 6, itmax=10, iter_adjust=5, seed=0)
     assert abs(est - ref) < 4 * sig and sig / ref < 1e-4
+
+
+def test_double_gaussian_closed_form_and_mc():
+    """Two mirrored Gaussian peaks: Gauss-Legendre of the oracle integrand at d = 2 equals the sum
+    of two Gaussian closed forms; the oracle's m-Cubes run at d = 4 finds it within error."""
+    d = 2
+    par = W.double_gaussian_params(d, a=6.0, u=0.3)
+    q = _gauss_legendre_2d(lambda X: oracle.integrand(W.DOUBLE_GAUSSIAN, d, par, X), d, panels=200)
+    ref = exact(W.DOUBLE_GAUSSIAN, par[:d], par[d:])
+    assert abs(q - ref) <= 1e-11 * ref
+    d = 4
+    par = W.double_gaussian_params(d, a=6.0, u=0.3)
+    est, sig, *_ = oracle.integrate(W.DOUBLE_GAUSSIAN, d, par, 2 * 10 ** 5, itmax=6, iter_adjust=3, seed=3)
+    assert abs(est - exact(W.DOUBLE_GAUSSIAN, par[:d], par[d:])) < 5 * sig
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rotated_gaussian_against_multivariate_normal_box_probability(d):
+    """exp(-(x-c)^T M (x-c)) over the unit cube: scipy's multivariate normal CDF (box probability
+    by inclusion-exclusion) against quadrature of the oracle integrand (d = 2) and the oracle's
+    m-Cubes run (d = 3)."""
+    from closed_forms import rotated_gaussian_exact
+    par = W.rotated_gaussian_params(d, seed=1, lam_min=1.0, lam_max=60.0)
+    M = par[:d * d].reshape(d, d)
+    c = par[d * d:]
+    ref = rotated_gaussian_exact(M, c)
+    if d == 2:
+        q = _gauss_legendre_2d(lambda X: oracle.integrand(W.ROTATED_GAUSSIAN, d, par, X), d, panels=100)
+        assert abs(q - ref) <= 1e-9 * ref
+    est, sig, *_ = oracle.integrate(W.ROTATED_GAUSSIAN, d, par, 2 * 10 ** 5, itmax=6, iter_adjust=3, seed=5)
+    assert abs(est - ref) < 5 * sig and sig < 1e-2 * ref
