@@ -337,6 +337,43 @@ int mcubes_flow_grad_dev(const mcubes_flow_shape *shape, const float *d_params, 
 int mcubes_flow_adam_dev(int64_t n_params, float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
                          float lr, void *stream);
 
+/* Whole learned-proposal run:
+ *   1. vegas_iters grid-adjusting m-Cubes iterations (FP32-eval), then flow_iters frozen-grid
+ *      iterations as the reference;
+ *   2. train_samples drawn through the adapted grid with their weights (f^2 J for the variance
+ *      loss, |f| J for KL) train the flow (train_steps Adam steps of `batch` samples, rate lr,
+ *      starting from the identity flow);
+ *   3. flow_iters m-Cubes iterations sample with the flow: strata in latent space,
+ *      x = flow^-1(z), weight f(x)/q(x).
+ * All at ncall samples per iteration. params_out: NULL or mcubes_flow_param_count floats.
+ * Synchronous; allocates and frees its own device memory.
+ * Errors: INVALID_ARG (shape.d != d, unsupported shape, bad counts), as mcubes_integrate_ex,
+ * NONFINITE. */
+typedef struct mcubes_flow_config {
+    mcubes_flow_shape shape;
+    int32_t loss_kind;          /* 0: variance (chi^2), 1: KL */
+    int32_t vegas_iters;        /* >= 1 */
+    int32_t flow_iters;         /* >= 1 */
+    int32_t train_steps;        /* >= 0 */
+    int32_t batch;              /* >= 64 */
+    float lr;
+    int64_t ncall;              /* samples per iteration */
+    int64_t train_samples;      /* >= batch */
+    uint64_t seed;
+} mcubes_flow_config;
+
+typedef struct mcubes_flow_report {
+    mcubes_result vegas;        /* frozen adapted-grid iterations */
+    mcubes_result flow;         /* flow-proposal iterations */
+    double vegas_var_per_sample;   /* mean per-iteration variance x samples per iteration */
+    double flow_var_per_sample;
+    double train_loss_first, train_loss_last;
+    double seconds_vegas, seconds_train, seconds_flow;
+} mcubes_flow_report;
+
+int mcubes_flow_integrate(int integrand_id, const double *params, int d, const mcubes_flow_config *cfg,
+                          float *params_out, mcubes_flow_report *out);
+
 /* Philox4x32-10 on the device, for checking the generator. out[4j..4j+3] = Philox(ctr[4j..4j+3],
  * key = (seed mod 2^32, seed >> 32)) for j < n.
  *   impl 0: the library's own generator (the one the sampler uses).

@@ -49,6 +49,11 @@ class Tuning(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class FlowShape(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("layers", ctypes.c_int32), ("hidden", ctypes.c_int32),
+                ("bins", ctypes.c_int32)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("integrand_id", ctypes.c_int32), ("d", ctypes.c_int32), ("ncall", ctypes.c_int64),
                 ("params", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64)]
@@ -64,9 +69,18 @@ class BatchTuning(ctypes.Structure):
                         hist_mode=self.hist_mode[d]) for d in range(1, DMAX + 1) if self.block_threads[d]}
 
 
-class FlowShape(ctypes.Structure):
-    _fields_ = [("d", ctypes.c_int32), ("layers", ctypes.c_int32), ("hidden", ctypes.c_int32),
-                ("bins", ctypes.c_int32)]
+class FlowConfig(ctypes.Structure):
+    _fields_ = [("shape", FlowShape), ("loss_kind", ctypes.c_int32), ("vegas_iters", ctypes.c_int32),
+                ("flow_iters", ctypes.c_int32), ("train_steps", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("ncall", ctypes.c_int64), ("train_samples", ctypes.c_int64),
+                ("seed", ctypes.c_uint64)]
+
+
+class FlowReport(ctypes.Structure):
+    _fields_ = [("vegas", Result), ("flow", Result), ("vegas_var_per_sample", ctypes.c_double),
+                ("flow_var_per_sample", ctypes.c_double), ("train_loss_first", ctypes.c_double),
+                ("train_loss_last", ctypes.c_double), ("seconds_vegas", ctypes.c_double),
+                ("seconds_train", ctypes.c_double), ("seconds_flow", ctypes.c_double)]
 
 
 def _load():
@@ -103,6 +117,7 @@ def _load():
         "mcubes_flow_grad_dev": (i32, [ctypes.POINTER(FlowShape), vp, i64, vp, vp, i32, vp, vp, vp, ctypes.c_size_t,
                                        vp]),
         "mcubes_flow_adam_dev": (i32, [i64, vp, vp, vp, vp, i32, ctypes.c_float, vp]),
+        "mcubes_flow_integrate": (i32, [i32, dp, i32, ctypes.POINTER(FlowConfig), vp, ctypes.POINTER(FlowReport)]),
         "mcubes_philox_dev": (i32, [vp, u64, u64, i32, vp, vp]),
         "mcubes_status_string": (ctypes.c_char_p, [i32]),
         "mcubes_last_cuda_error": (i32, []),
@@ -165,6 +180,20 @@ def _hd(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def param_len(fid: int, d: int) -> int:
+    """FP64 parameters integrand fid takes at dimension d."""
+    return d * d + d if int(fid) == 9 else 2 * d
+
+
+def _par(fid, d, params):
+    """Integrand parameters as contiguous float64, checked for length (the C side reads
+    param_len(fid, d) values)."""
+    a, p = _hd(params)
+    if 0 <= int(fid) <= 9 and 1 <= int(d) <= DMAX and a.size < param_len(fid, d):
+        raise ValueError(f"integrand {fid} at d={d} takes {param_len(fid, d)} parameters, got {a.size}")
+    return a, p
+
+
 def _hptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
@@ -196,7 +225,7 @@ def integrate(fid, params, d, ncall, itmax, iter_adjust, seed, precision=FP64, t
               grid_in=None, return_iters=False, return_grid=False):
     """Whole m-Cubes integration. Returns dict(estimate, error, chi2_dof, iters_done,
     samples_per_iter[, iters (itmax x 2: I, Var)][, grid (d x 501)])."""
-    par, pp = _hd(params)
+    par, pp = _par(fid, d, params)
     res = Result()
     iters = np.zeros((itmax, 2)) if return_iters else None
     grid = np.zeros((d, NBINS + 1)) if return_grid else None
@@ -220,7 +249,7 @@ def integrate_range(fid, params, d, ncall, itmax, iter_adjust, it_begin, it_end,
                     grid_in=None, prev_estimate=0.0, stream=None):
     """Iterations [it_begin, it_end) of an itmax-iteration run (checkpoint / resume). Returns
     dict(iters (n x 2), grid (d x 501))."""
-    par, pp = _hd(params)
+    par, pp = _par(fid, d, params)
     gin = gp = None
     if grid_in is not None:
         gin, gp = _hd(grid_in)
@@ -245,7 +274,7 @@ def combine(iters, skip=0):
 def vsample_once(fid, params, d, ncall, seed, iteration=0, job=0, adjust=1, precision=FP64,
                  grid_in=None, want_grid=True, want_C=True):
     """One V-Sample pass (+ Rebin when adjust) with host buffers. Returns dict(I, Var[, C][, grid])."""
-    par, pp = _hd(params)
+    par, pp = _par(fid, d, params)
     gin = gp = None
     if grid_in is not None:
         gin, gp = _hd(grid_in)
@@ -266,7 +295,7 @@ def vsample_once(fid, params, d, ncall, seed, iteration=0, job=0, adjust=1, prec
 
 def vsample_dev(fid, params, d, ncall, seed, iteration, job, adjust, precision, d_grid, d_C, d_sums,
                 d_prev=None, d_probe=None, probe_shift=0, tune=None, stream=None):
-    par, pp = _hd(params)
+    par, pp = _par(fid, d, params)
     st = _lib.mcubes_vsample_dev(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
                                  int(adjust), precision, _dptr(d_grid), _dptr(d_C), _dptr(d_sums), _dptr(d_prev),
                                  _dptr(d_probe), probe_shift, _tune(tune), _stream(stream))
@@ -283,7 +312,7 @@ def workspace_bytes(d: int) -> int:
 
 def iteration_dev(fid, params, d, ncall, seed, iteration, job, adjust, precision, d_grid_in, d_grid_out,
                   d_result, d_prev=None, d_workspace=None, workspace_bytes=0, tune=None, stream=None):
-    par, pp = _hd(params)
+    par, pp = _par(fid, d, params)
     st = _lib.mcubes_iteration_dev(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
                                    int(adjust), precision, _dptr(d_grid_in), _dptr(d_grid_out), _dptr(d_result),
                                    _dptr(d_prev), _dptr(d_workspace), int(workspace_bytes), _tune(tune),
@@ -296,7 +325,7 @@ def iteration_dev_static(fid, params, d, ncall, seed, iteration, job, adjust, pr
     """mcubes_iteration_dev with the library's fixed scratch array: the call allocates no device
     memory, for callers that cannot allocate at that point. Calls that overlap on the GPU share,
     and race on, that one array."""
-    par, pp = _hd(params)
+    par, pp = _par(fid, d, params)
     st = _lib.mcubes_iteration_dev_static(int(fid), pp, d, int(ncall), int(seed) & (2 ** 64 - 1), iteration, job,
                                           int(adjust), precision, _dptr(d_grid_in), _dptr(d_grid_out),
                                           _dptr(d_result), _dptr(d_prev), _tune(tune), _stream(stream))
@@ -312,7 +341,7 @@ def _jobs(jobs):
     keep = []
     arr = (Job * len(jobs))()
     for k, j in enumerate(jobs):
-        par = np.ascontiguousarray(j["params"], dtype=np.float64)
+        par, _ = _par(j["fid"], j["d"], j["params"])
         keep.append(par)
         arr[k].integrand_id = int(j["fid"])
         arr[k].d = int(j["d"])
@@ -382,6 +411,36 @@ def flow_grad_dev(shape, d_params, n, d_x, d_w, loss_kind, d_grad, d_loss, d_wor
 def flow_adam_dev(n_params, d_params, d_grad, d_m, d_v, step, lr, stream=None):
     _check(_lib.mcubes_flow_adam_dev(int(n_params), _dptr(d_params), _dptr(d_grad), _dptr(d_m), _dptr(d_v),
                                      int(step), float(lr), _stream(stream)), "flow_adam")
+
+
+def _res(r):
+    return dict(estimate=r.estimate, error=r.error, chi2_dof=r.chi2_dof, iters_done=r.iters_done,
+                samples_per_iter=r.samples_per_iter)
+
+
+def flow_integrate(fid, params, d, layers=4, hidden=64, bins=16, loss="variance", vegas_iters=5, flow_iters=5,
+                   train_steps=500, batch=1 << 14, lr=3e-3, ncall=10 ** 6, train_samples=1 << 20, seed=0,
+                   return_params=False):
+    """m-Cubes with the learned proposal (VEGAS warm-up, training, flow-sampled iterations).
+    Returns dict(vegas, flow (results), vegas_var_per_sample, flow_var_per_sample, train_loss_first,
+    train_loss_last, seconds_*[, params])."""
+    par, pp = _par(fid, d, params)
+    cfg = FlowConfig(FlowShape(d, layers, hidden, bins), 0 if loss == "variance" else 1, vegas_iters, flow_iters,
+                     train_steps, batch, lr, int(ncall), int(train_samples), int(seed) & (2 ** 64 - 1))
+    rep = FlowReport()
+    out_par = None
+    if return_params:
+        out_par = np.zeros(flow_param_count(cfg.shape), dtype=np.float32)
+    st = _lib.mcubes_flow_integrate(int(fid), pp, d, ctypes.byref(cfg),
+                                    None if out_par is None else out_par.ctypes.data, ctypes.byref(rep))
+    _check(st, "flow_integrate")
+    out = dict(vegas=_res(rep.vegas), flow=_res(rep.flow), vegas_var_per_sample=rep.vegas_var_per_sample,
+               flow_var_per_sample=rep.flow_var_per_sample, train_loss_first=rep.train_loss_first,
+               train_loss_last=rep.train_loss_last, seconds_vegas=rep.seconds_vegas,
+               seconds_train=rep.seconds_train, seconds_flow=rep.seconds_flow)
+    if out_par is not None:
+        out["params"] = out_par
+    return out
 
 
 def philox_dev(d_ctr, n, seed, impl, d_out, stream=None):

@@ -83,10 +83,13 @@ def test_flow_density_and_sampling_match_oracle(capi, d, L, H, K):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("d,L,H,K,sub", [(4, 2, 32, 4, None), (8, 4, 64, 16, 400)])
-def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, kind):
+@pytest.mark.parametrize("d,L,H,K,sub,scale", [(4, 2, 32, 4, None, 0.2), (8, 4, 64, 16, 400, 0.1)])
+def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, scale, kind):
+    """Weight scale 0.1 at d = 8 is the regime training works in (it starts at the identity);
+    with much larger random weights bf16 noise compounds through four layers of backprop and
+    the comparison measures that noise rather than the kernels."""
     n = 300
-    p = _params(d, L, H, K, seed=7 + d, scale=0.2)
+    p = _params(d, L, H, K, seed=7 + d, scale=scale)
     rng = np.random.default_rng(2)
     x = rng.uniform(0.0, 1.0, (n, d))
     f = np.exp(-np.sum((x - 0.35) ** 2, axis=1) * 8.0)
@@ -112,7 +115,7 @@ def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, kind):
     a, b = g[idx], g_ref
     cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
     rel = float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    assert cos > 0.995 and rel < 0.08, (cos, rel)
+    assert cos > 0.998 and rel < 0.05, (cos, rel)
 
 
 def test_adam_step(capi):
@@ -172,3 +175,41 @@ def test_training_lowers_the_variance(capi):
     x_ref = x.astype(np.float32).astype(np.float64)
     l_ref = F.loss(dp.cpu().numpy().astype(np.float64), x_ref, w, d, L, H, K, "variance", use_bf16=True)
     assert abs(loss.item() - l_ref) < 2e-2 * l_ref, (loss.item(), l_ref)
+
+
+def test_flow_integrate_identity_flow_is_unbiased(capi):
+    """No training: the flow is the identity and samples the latent strata directly; both that
+    estimate and the frozen-grid one agree with the closed form within their errors."""
+    import math
+    from paper_2302_05730_gb300 import workloads as W
+    d = 3
+    par = W.gaussian_params(d, 8.0)
+    exact = (math.sqrt(math.pi) / 8.0 * math.erf(4.0)) ** 3
+    r = capi.flow_integrate(W.GAUSSIAN, par, d, layers=2, hidden=32, bins=8, vegas_iters=2, flow_iters=3,
+                            train_steps=0, batch=1024, ncall=200000, train_samples=1 << 15, seed=3)
+    for key in ("flow", "vegas"):
+        est, err = r[key]["estimate"], r[key]["error"]
+        assert abs(est - exact) < 4.5 * err and err < 1e-2 * exact, (key, est, exact, err)
+
+
+def test_learned_proposal_beats_the_grid_on_a_rotated_gaussian(capi):
+    """A strongly correlated peak (exp(-(x-c)^T Q diag(1..400) Q^T (x-c)), d = 4): a separable grid
+    cannot follow it, the trained flow can. The flow's variance per sample falls well below the
+    adapted grid's at the same budget, and both estimates match the closed form
+    (multivariate-normal box probability)."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import rotated_gaussian_exact
+    from paper_2302_05730_gb300 import workloads as W
+    d = 4
+    par = W.rotated_gaussian_params(d, seed=2, lam_min=1.0, lam_max=400.0)
+    exact = rotated_gaussian_exact(par[:d * d].reshape(d, d), par[d * d:])
+    r = capi.flow_integrate(W.ROTATED_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, vegas_iters=5, flow_iters=4,
+                            train_steps=1500, batch=1 << 14, lr=3e-3, ncall=200000, train_samples=1 << 18, seed=5)
+    gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
+    info = (r["vegas"], r["flow"], exact, gain, r["train_loss_first"], r["train_loss_last"])
+    for key in ("flow", "vegas"):
+        assert abs(r[key]["estimate"] - exact) < 4.5 * r[key]["error"], info
+    assert r["train_loss_last"] < r["train_loss_first"], info
+    assert gain > 3.0, info

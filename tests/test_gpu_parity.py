@@ -290,6 +290,8 @@ def test_nonfinite_integrand_reported(capi):
 def test_invalid_arguments(capi):
     par = np.ones(4)
     with pytest.raises(capi.McubesError):
+        capi.vsample_once(10, par, 2, 100, 1)
+    with pytest.raises(ValueError):      # the rotated Gaussian needs d^2 + d parameters
         capi.vsample_once(9, par, 2, 100, 1)
     with pytest.raises(capi.McubesError):
         capi.vsample_once(0, par, 2, 1, 1)
