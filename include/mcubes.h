@@ -341,8 +341,8 @@ int mcubes_flow_adam_dev(int64_t n_params, float *d_params, const float *d_grad,
  *   1. vegas_iters grid-adjusting m-Cubes iterations (FP32-eval), then flow_iters frozen-grid
  *      iterations as the reference;
  *   2. train_samples drawn through the adapted grid with their weights (f^2 J for the variance
- *      loss, |f| J for KL) train the flow (train_steps Adam steps of `batch` samples, rate lr,
- *      starting from the identity flow);
+ *      loss, |f| J for KL) train the flow (train_steps Adam steps of `batch` samples, starting
+ *      from the identity flow; the rate follows a cosine decay from lr to lr/10);
  *   3. flow_iters m-Cubes iterations sample with the flow: strata in latent space,
  *      x = flow^-1(z), weight f(x)/q(x).
  * All at ncall samples per iteration. params_out: NULL or mcubes_flow_param_count floats.

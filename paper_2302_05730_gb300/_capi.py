@@ -418,8 +418,8 @@ def _res(r):
                 samples_per_iter=r.samples_per_iter)
 
 
-def flow_integrate(fid, params, d, layers=4, hidden=64, bins=16, loss="variance", vegas_iters=5, flow_iters=5,
-                   train_steps=500, batch=1 << 14, lr=3e-3, ncall=10 ** 6, train_samples=1 << 20, seed=0,
+def flow_integrate(fid, params, d, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5, flow_iters=5,
+                   train_steps=1000, batch=1 << 14, lr=1e-3, ncall=10 ** 6, train_samples=1 << 20, seed=0,
                    return_params=False):
     """m-Cubes with the learned proposal (VEGAS warm-up, training, flow-sampled iterations).
     Returns dict(vegas, flow (results), vegas_var_per_sample, flow_var_per_sample, train_loss_first,

@@ -377,7 +377,10 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
         if ((st = mcubes_flow_grad_dev(&sh, d_par, batch, d_x + b0 * d, d_w + b0, cfg->loss_kind, d_grad, d_loss, d_work,
                                        wbytes, s)))
             return finish(st);
-        if ((st = mcubes_flow_adam_dev(npar, d_par, d_grad, d_m, d_v, step, cfg->lr, s))) return finish(st);
+        // cosine decay of the rate to a tenth over the run keeps late steps from undoing the fit
+        const float frac = cfg->train_steps > 1 ? (float)(step - 1) / (float)(cfg->train_steps - 1) : 0.f;
+        const float lr = cfg->lr * (0.1f + 0.9f * 0.5f * (1.0f + std::cos(3.14159265f * frac)));
+        if ((st = mcubes_flow_adam_dev(npar, d_par, d_grad, d_m, d_v, step, lr, s))) return finish(st);
         if (step == 1 || step == cfg->train_steps) {
             float l = 0.f;
             if ((st = cuda_status(cudaMemcpyAsync(&l, d_loss, sizeof(float), cudaMemcpyDeviceToHost, s)))) return finish(st);

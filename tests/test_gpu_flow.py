@@ -205,11 +205,27 @@ def test_learned_proposal_beats_the_grid_on_a_rotated_gaussian(capi):
     d = 4
     par = W.rotated_gaussian_params(d, seed=2, lam_min=1.0, lam_max=400.0)
     exact = rotated_gaussian_exact(par[:d * d].reshape(d, d), par[d * d:])
-    r = capi.flow_integrate(W.ROTATED_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, vegas_iters=5, flow_iters=4,
-                            train_steps=1500, batch=1 << 14, lr=3e-3, ncall=200000, train_samples=1 << 18, seed=5)
+    r = capi.flow_integrate(W.ROTATED_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5,
+                            flow_iters=4, train_steps=1000, batch=1 << 14, lr=1e-3, ncall=200000,
+                            train_samples=1 << 20, seed=5)
     gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
     info = (r["vegas"], r["flow"], exact, gain, r["train_loss_first"], r["train_loss_last"])
     for key in ("flow", "vegas"):
         assert abs(r[key]["estimate"] - exact) < 4.5 * r[key]["error"], info
     assert r["train_loss_last"] < r["train_loss_first"], info
-    assert gain > 3.0, info
+    assert gain > 4.0, info
+
+
+def test_learned_proposal_double_gaussian_d8(capi):
+    """Two peaks on the diagonal of [0,1]^8: the separable grid spreads its resolution over all
+    2^8 combinations of the per-axis peaks, the flow learns the two real ones."""
+    from paper_2302_05730_gb300 import workloads as W
+    d = 8
+    par = W.double_gaussian_params(d)
+    exact = 1.9450128121400754e-06   # twice the Gaussian closed form (tests/closed_forms.py)
+    r = capi.flow_integrate(W.DOUBLE_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5,
+                            flow_iters=4, train_steps=1000, batch=1 << 14, lr=1e-3, ncall=1 << 20,
+                            train_samples=1 << 20, seed=5)
+    gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
+    assert abs(r["flow"]["estimate"] - exact) < 4.5 * r["flow"]["error"], (r["flow"], gain)
+    assert gain > 10.0, (r["flow"], r["vegas"], gain)
