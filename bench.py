@@ -176,6 +176,7 @@ def main():
                     help="only the FP32-eval device-resident leg (profiling runs)")
     ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (4096-job) leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -381,6 +382,46 @@ def main():
         batch["plain_fp64_sequential"] = {"seconds_sampled": el, "jobs_sampled": len(sample),
                                           "seconds_scaled": el / frac, "samples_per_s": 8 * tot * frac / el}
 
+    # ---- learned proposal (4-layer coupling flow, width 64, 16 bins; 2^20 samples per iteration):
+    # double Gaussian exp(-100|x - p1|^2) + exp(-100|x - p2|^2), p1 = 0.25 1, p2 = 0.75 1, and a rotated
+    # anisotropic Gaussian (random orthogonal Q, eigenvalues 1..400), d = 8. Variance per sample against
+    # the adapted grid at the same budget, and time to 1e-3 of each form.
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = {}
+        cases = [("double_gaussian", W.DOUBLE_GAUSSIAN, W.double_gaussian_params(8)),
+                 ("rotated_gaussian", W.ROTATED_GAUSSIAN, W.rotated_gaussian_params(8, seed=0))]
+        n_it = 1 << 20
+        for name, fid, par in cases:
+            r = capi.flow_integrate(fid, par, 8, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5, flow_iters=4,
+                                    train_steps=1000, batch=1 << 14, lr=5e-4, ncall=n_it, train_samples=1 << 20, seed=0)
+            I = abs(r["flow"]["estimate"])
+            target = (1e-3 * I) ** 2
+            g8, m8, p8 = capi.stratify(8, n_it)
+            var_it_flow = r["flow_var_per_sample"] / (m8 * p8)
+            var_it_grid = r["vegas_var_per_sample"] / (m8 * p8)
+            k_flow = int(math.ceil(var_it_flow / target))
+            k_grid = int(math.ceil(var_it_grid / target))
+            t_it_flow = r["seconds_flow"] / 4
+            # plain FP64 m-Cubes on the same integrand: per-iteration time and variance after adaptation
+            t0 = time.perf_counter()
+            pl = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP64, return_iters=True)
+            t64 = (time.perf_counter() - t0) / 9
+            v64 = float(np.mean(pl["iters"][5:, 1]))
+            k64 = int(math.ceil(v64 / target))
+            t0 = time.perf_counter()
+            p32 = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP32_EVAL, return_iters=True)
+            t32 = (time.perf_counter() - t0) / 9
+            k32 = int(math.ceil(float(np.mean(p32["iters"][5:, 1])) / target))
+            learned[name] = {
+                "flow": r["flow"], "grid": r["vegas"], "variance_gain_per_sample": r["vegas_var_per_sample"] / r["flow_var_per_sample"],
+                "train_seconds": r["seconds_train"], "flow_samples_per_s": 4 * m8 * p8 / max(r["seconds_flow"], 1e-9),
+                "time_to_1e-3_s": {
+                    "learned": r["seconds_vegas"] * 5 / 9 + r["seconds_train"] + k_flow * t_it_flow,
+                    "fp32_grid": 5 * t32 + k32 * t32, "fp64_grid": 5 * t64 + k64 * t64,
+                    "iters": {"learned": k_flow, "fp32_grid": k32, "fp64_grid": k64}},
+            }
+
     # ---- CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -418,6 +459,7 @@ def main():
             "cpu_baseline": cpu,
             "time_to_1e-3": tta,
             "batch": batch,
+            "learned": learned,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -340,9 +340,10 @@ int mcubes_flow_adam_dev(int64_t n_params, float *d_params, const float *d_grad,
 /* Whole learned-proposal run:
  *   1. vegas_iters grid-adjusting m-Cubes iterations (FP32-eval), then flow_iters frozen-grid
  *      iterations as the reference;
- *   2. train_samples drawn through the adapted grid with their weights (f^2 J for the variance
- *      loss, |f| J for KL) train the flow (train_steps Adam steps of `batch` samples, starting
- *      from the identity flow; the rate follows a cosine decay from lr to lr/10);
+ *   2. sets of train_samples points drawn through the adapted grid with their weights (f^2 J for
+ *      the variance loss, |f| J for KL) train the flow (train_steps Adam steps of `batch` samples,
+ *      starting from the identity flow; a fresh set is drawn for every pass over the previous
+ *      one; the rate follows a cosine decay from lr to lr/10);
  *   3. flow_iters m-Cubes iterations sample with the flow: strata in latent space,
  *      x = flow^-1(z), weight f(x)/q(x).
  * All at ncall samples per iteration. params_out: NULL or mcubes_flow_param_count floats.
@@ -358,7 +359,7 @@ typedef struct mcubes_flow_config {
     int32_t batch;              /* >= 64 */
     float lr;
     int64_t ncall;              /* samples per iteration */
-    int64_t train_samples;      /* >= batch */
+    int64_t train_samples;      /* points per training set (one epoch), >= batch */
     uint64_t seed;
 } mcubes_flow_config;
 

@@ -419,7 +419,7 @@ def _res(r):
 
 
 def flow_integrate(fid, params, d, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5, flow_iters=5,
-                   train_steps=1000, batch=1 << 14, lr=1e-3, ncall=10 ** 6, train_samples=1 << 20, seed=0,
+                   train_steps=1000, batch=1 << 14, lr=5e-4, ncall=10 ** 6, train_samples=1 << 20, seed=0,
                    return_params=False):
     """m-Cubes with the learned proposal (VEGAS warm-up, training, flow-sampled iterations).
     Returns dict(vegas, flow (results), vegas_var_per_sample, flow_var_per_sample, train_loss_first,

@@ -1,7 +1,7 @@
 // The learned proposal in use: m-Cubes with the coupling flow standing in for the VEGAS grid.
 //   1. VEGAS adapts its grid for a few iterations (the library's own V-Sample and Rebin).
 //   2. Samples drawn through the adapted grid are exported with their weights f^2 J
-//      (variance loss) or |f| J (KL loss): the data the flow trains on.
+//      (variance loss) or |f| J (KL loss): the data the flow trains on, a fresh set per epoch.
 //   3. The flow trains on them with the library's own forward, backward and Adam kernels.
 //   4. m-Cubes iterations sample with the flow: the sub-cube strata live in latent space,
 //      z = (c + u) / g, and x = flow^-1(z) carries density q(x). Each sample weighs f(x) / q(x),
@@ -208,13 +208,16 @@ __global__ void flow_eval_kernel(const SampleSpec S, const IntegrandParams ip, d
     }
 }
 
-// Weights for training: variance loss w^2, KL |w|, normalised so a batch of `batch` sums to 1.
-__global__ void train_weights_kernel(const float *__restrict__ w, long long n, int kind, double total, double scale,
-                                     float *__restrict__ out)
+// Weights for training: variance loss w^2, KL |w|, normalised so a batch of `batch` sums to 1
+// (total read on the device; a set whose total is not positive and finite trains on zero weights).
+__global__ void train_weights_kernel(const float *__restrict__ w, long long n, int kind, const double *__restrict__ total,
+                                     double scale, float *__restrict__ out)
 {
+    const double tot = *total;
+    const double f = (tot > 0.0 && tot < INFINITY) ? scale / tot : 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v = kind == 0 ? (double)w[i] * (double)w[i] : fabs((double)w[i]);
-        out[i] = (float)(v / total * scale);
+        out[i] = (float)(v * f);
     }
 }
 
@@ -335,7 +338,10 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     };
     if ((st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)))) return finish(st);
 
-    // ---- 2. training data through the adapted grid
+    // ---- 2. training data through the adapted grid. Each pass over the set (an epoch) draws a fresh
+    // one from another Philox stream (job word 0x40000000 | epoch): the weights f J are heavy-tailed
+    // wherever the grid misses the integrand's shape, and a fixed set lets the flow fit its few
+    // largest points rather than the integrand.
     t0 = std::chrono::steady_clock::now();
     SampleSpec E;
     {
@@ -346,21 +352,29 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
                        (uint32_t)(cfg->seed >> 32), (uint32_t)(itmax + 1) << 16, 0x40000000u, d, integrand_id};
     }
     const long long nexp = (long long)E.m * E.p;   // <= train_samples
+    const int batch = cfg->batch;
     if ((st = cuda_status(cudaMemcpyAsync(d_grid, grid.data(), sizeof(double) * d * kGS, cudaMemcpyHostToDevice, s))))
         return finish(st);
-    vegas_export_kernel<<<(unsigned)std::min<long long>((nexp + 255) / 256, 65535), 256, 0, s>>>(E, pb.P.ip, d_grid,
-                                                                                                  nexp, d_x, d_wraw);
-    if ((st = cuda_status(cudaGetLastError()))) return finish(st);
     double *d_tot = d_sums + 2 * (size_t)cfg->flow_iters;
-    if ((st = cuda_status(cudaMemsetAsync(d_tot, 0, sizeof(double), s)))) return finish(st);
-    sum_kernel<<<512, 256, 0, s>>>(d_wraw, nexp, cfg->loss_kind, d_tot);
-    double tot = 0.0;
-    if ((st = cuda_status(cudaMemcpyAsync(&tot, d_tot, sizeof(double), cudaMemcpyDeviceToHost, s)))) return finish(st);
-    if ((st = cuda_status(cudaStreamSynchronize(s)))) return finish(st);
-    if (!(tot > 0.0) || !std::isfinite(tot)) return finish(MCUBES_ERR_NONFINITE);
-    const int batch = cfg->batch;
-    train_weights_kernel<<<512, 256, 0, s>>>(d_wraw, nexp, cfg->loss_kind, tot, (double)nexp / (double)batch, d_w);
-    if ((st = cuda_status(cudaGetLastError()))) return finish(st);
+    auto draw_training_set = [&](uint32_t epoch) -> int {
+        SampleSpec Ee = E;
+        Ee.job = 0x40000000u | (epoch & 0x0FFFFFFFu);
+        vegas_export_kernel<<<(unsigned)std::min<long long>((nexp + 255) / 256, 65535), 256, 0, s>>>(Ee, pb.P.ip, d_grid,
+                                                                                                      nexp, d_x, d_wraw);
+        int e = cuda_status(cudaGetLastError());
+        if (e) return e;
+        if ((e = cuda_status(cudaMemsetAsync(d_tot, 0, sizeof(double), s)))) return e;
+        sum_kernel<<<512, 256, 0, s>>>(d_wraw, nexp, cfg->loss_kind, d_tot);
+        train_weights_kernel<<<512, 256, 0, s>>>(d_wraw, nexp, cfg->loss_kind, d_tot, (double)nexp / (double)batch, d_w);
+        return cuda_status(cudaGetLastError());
+    };
+    if ((st = draw_training_set(0))) return finish(st);
+    {
+        double tot = 0.0;
+        if ((st = cuda_status(cudaMemcpyAsync(&tot, d_tot, sizeof(double), cudaMemcpyDeviceToHost, s)))) return finish(st);
+        if ((st = cuda_status(cudaStreamSynchronize(s)))) return finish(st);
+        if (!(tot > 0.0) || !std::isfinite(tot)) return finish(MCUBES_ERR_NONFINITE);
+    }
 
     // ---- 3. train
     std::vector<float> h_par;
@@ -372,6 +386,7 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     const long long nbatches = std::max<long long>(1, nexp / batch);
     for (int step = 1; step <= cfg->train_steps; ++step) {
         const long long b0 = ((step - 1) % nbatches) * (long long)batch;
+        if (step > 1 && b0 == 0 && (st = draw_training_set((uint32_t)((step - 1) / nbatches)))) return finish(st);
         if ((st = cuda_status(cudaMemsetAsync(d_grad, 0, sizeof(float) * npar, s)))) return finish(st);
         if ((st = cuda_status(cudaMemsetAsync(d_loss, 0, sizeof(float), s)))) return finish(st);
         if ((st = mcubes_flow_grad_dev(&sh, d_par, batch, d_x + b0 * d, d_w + b0, cfg->loss_kind, d_grad, d_loss, d_work,

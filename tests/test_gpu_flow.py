@@ -205,15 +205,39 @@ def test_learned_proposal_beats_the_grid_on_a_rotated_gaussian(capi):
     d = 4
     par = W.rotated_gaussian_params(d, seed=2, lam_min=1.0, lam_max=400.0)
     exact = rotated_gaussian_exact(par[:d * d].reshape(d, d), par[d * d:])
-    r = capi.flow_integrate(W.ROTATED_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5,
-                            flow_iters=4, train_steps=1000, batch=1 << 14, lr=1e-3, ncall=200000,
-                            train_samples=1 << 20, seed=5)
+    # variance loss (weights f^2 J); gains of 8-44 were measured over seeds 8-11 at these settings
+    r = capi.flow_integrate(W.ROTATED_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, loss="variance", vegas_iters=5,
+                            flow_iters=4, train_steps=1000, batch=1 << 14, lr=5e-4, ncall=200000,
+                            train_samples=1 << 20, seed=9)
     gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
     info = (r["vegas"], r["flow"], exact, gain, r["train_loss_first"], r["train_loss_last"])
     for key in ("flow", "vegas"):
         assert abs(r[key]["estimate"] - exact) < 4.5 * r[key]["error"], info
     assert r["train_loss_last"] < r["train_loss_first"], info
     assert gain > 4.0, info
+
+
+def test_learned_proposal_rotated_gaussian_d8(capi):
+    """The same family at d = 8 (eigenvalues 1..400, 2^20 samples per iteration): the adapted grid
+    misses mass off its axes and its error estimate undercounts (its estimate sits several sigma
+    low); the trained flow's estimate agrees with the closed form and its variance per sample is
+    far below the grid's."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from closed_forms import rotated_gaussian_exact
+    from paper_2302_05730_gb300 import workloads as W
+    d = 8
+    par = W.rotated_gaussian_params(d, seed=0)
+    exact = rotated_gaussian_exact(par[:d * d].reshape(d, d), par[d * d:])
+    r = capi.flow_integrate(W.ROTATED_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, loss="variance", vegas_iters=5,
+                            flow_iters=4, train_steps=2000, batch=1 << 14, lr=1e-3, ncall=1 << 20,
+                            train_samples=1 << 20, seed=6)
+    gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
+    info = (r["vegas"], r["flow"], exact, gain, r["train_loss_first"], r["train_loss_last"])
+    assert abs(r["flow"]["estimate"] - exact) < 4.5 * r["flow"]["error"], info
+    assert r["train_loss_last"] < r["train_loss_first"], info
+    assert gain > 10.0, info
 
 
 def test_learned_proposal_double_gaussian_d8(capi):
@@ -224,7 +248,7 @@ def test_learned_proposal_double_gaussian_d8(capi):
     par = W.double_gaussian_params(d)
     exact = 1.9450128121400754e-06   # twice the Gaussian closed form (tests/closed_forms.py)
     r = capi.flow_integrate(W.DOUBLE_GAUSSIAN, par, d, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5,
-                            flow_iters=4, train_steps=1000, batch=1 << 14, lr=1e-3, ncall=1 << 20,
+                            flow_iters=4, train_steps=1000, batch=1 << 14, lr=5e-4, ncall=1 << 20,
                             train_samples=1 << 20, seed=5)
     gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
     assert abs(r["flow"]["estimate"] - exact) < 4.5 * r["flow"]["error"], (r["flow"], gain)
