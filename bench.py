@@ -121,6 +121,39 @@ def replica_job(rank: int) -> int:
     return rank
 
 
+# ------------------------------------------------------------------------------ oracle timing
+def host_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def oracle_vsample_ranges(fams, pars, grids, ncall, starts, cubes, threads, it=1):
+    """The oracle's V-Sample over [t0, t0 + cubes) of each family, split into `threads` equal
+    sub-ranges run side by side (the oracle holds no global state and ctypes releases the
+    interpreter lock during the call). Returns the samples processed."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    g, m, p = oracle.stratify(D, ncall)
+    jobs = []
+    for fid in fams:
+        t0 = starts[fid]
+        step = -(-cubes // threads)
+        for a in range(t0, t0 + cubes, step):
+            jobs.append((fid, a, min(a + step, t0 + cubes)))
+
+    def one(job):
+        fid, a, b = job
+        oracle.vsample(fid, D, pars[fid], ncall, 0, it=it, mode=1, adjust=1, B=grids[fid], t0=a, t1=b)
+        return (b - a) * p
+
+    if threads == 1:
+        return sum(one(j) for j in jobs)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return sum(ex.map(one, jobs))
+
+
 # ------------------------------------------------------------------------------ reference arm
 def run_reference(args, rank):
     """The CPU oracle on a bounded sample of the workload (sub-cube ranges of each family)."""
@@ -130,17 +163,15 @@ def run_reference(args, rank):
     from paper_2302_05730_gb300 import workloads as W
 
     g, m, p = oracle.stratify(D, NCALL)
-    cubes = 1 << 15
+    threads = host_threads()
+    cubes = (1 << 15) * threads
     B = oracle.uniform_grid(D)
+    grids = {fid: B for fid in W.GENZ6}
     pars = {fid: W.genz_params(fid, D, seed=0) for fid in W.GENZ6}
 
     def step(k):
-        n = 0
-        for fid in W.GENZ6:
-            t0 = (k * 7919 * cubes) % (m - cubes)
-            oracle.vsample(fid, D, pars[fid], NCALL, 0, it=k % 65536, mode=1, adjust=1, B=B, t0=t0, t1=t0 + cubes)
-            n += cubes * p
-        return n
+        starts = {fid: (k * 7919 * cubes) % (m - cubes) for fid in W.GENZ6}
+        return oracle_vsample_ranges(W.GENZ6, pars, grids, NCALL, starts, cubes, threads, it=k % 65536)
 
     for k in range(args.warmup):
         step(k)
@@ -156,11 +187,61 @@ def run_reference(args, rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "genz6-d8-n1e8 (oracle sample)", "d": D, "ncall": NCALL,
                        "families": [W.NAMES[f] for f in W.GENZ6], "sample_cubes_per_family_step": cubes},
-            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": threads, "kind": "oracle",
                              "sample": f"{cubes} sub-cubes ({cubes * p} samples) of each of the 6 families per step, "
-                                       "FP32-eval point layout, single thread"},
+                                       f"FP32-eval point layout, {threads} threads over equal sub-cube ranges"},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ learned proposal
+def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20):
+    """Learned proposal (4-layer coupling flow, width 64, 16 bins; 2^20 samples per iteration) on
+    the double Gaussian exp(-100|x - p1|^2) + exp(-100|x - p2|^2), p1 = 0.25 1, p2 = 0.75 1, and on
+    a rotated anisotropic Gaussian (random orthogonal Q, eigenvalues 1..400), d = 8. Reports the
+    variance per sample against the adapted grid at the same budget, and the time to a relative
+    error of 1e-3 for the learned proposal, the FP32-eval grid and the plain FP64 grid: warm-up
+    iterations plus the iterations the measured per-iteration variance needs."""
+    a, u = 10.0, 0.25
+    one = math.sqrt(math.pi) / (2 * a) * (math.erf(a * (1 - u)) + math.erf(a * u))
+    exact = {"double_gaussian": 2.0 * one ** 8}
+    out = {}
+    cases = [("double_gaussian", W.DOUBLE_GAUSSIAN, W.double_gaussian_params(8)),
+             ("rotated_gaussian", W.ROTATED_GAUSSIAN, W.rotated_gaussian_params(8, seed=0))]
+    g8, m8, p8 = capi.stratify(8, n_it)
+    for name, fid, par in cases:
+        r = capi.flow_integrate(fid, par, 8, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5, flow_iters=4,
+                                train_steps=train_steps, batch=1 << 14, lr=5e-4, ncall=n_it, train_samples=1 << 20,
+                                seed=0)
+        I = abs(r["flow"]["estimate"])
+        target = (1e-3 * I) ** 2
+        k_flow = int(math.ceil(r["flow_var_per_sample"] / (m8 * p8) / target))
+        t_it_flow = r["seconds_flow"] / 4
+        # plain m-Cubes on the same integrand: per-iteration time and variance after adaptation
+        t0 = time.perf_counter()
+        pl = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP64, return_iters=True)
+        t64 = (time.perf_counter() - t0) / 9
+        k64 = int(math.ceil(float(np.mean(pl["iters"][5:, 1])) / target))
+        t0 = time.perf_counter()
+        p32 = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP32_EVAL, return_iters=True)
+        t32 = (time.perf_counter() - t0) / 9
+        k32 = int(math.ceil(float(np.mean(p32["iters"][5:, 1])) / target))
+        rec = {
+            "flow": r["flow"], "grid": r["vegas"],
+            "variance_gain_per_sample": r["vegas_var_per_sample"] / r["flow_var_per_sample"],
+            "train_seconds": r["seconds_train"], "train_steps": train_steps,
+            "flow_samples_per_s": 4 * m8 * p8 / max(r["seconds_flow"], 1e-9),
+            "time_to_1e-3_s": {
+                "learned": r["seconds_vegas"] * 5 / 9 + r["seconds_train"] + k_flow * t_it_flow,
+                "fp32_grid": (5 + k32) * t32, "fp64_grid": (5 + k64) * t64,
+                "iters": {"learned": k_flow, "fp32_grid": k32, "fp64_grid": k64}},
+        }
+        if name in exact:
+            rec["exact"] = exact[name]
+            rec["flow_z"] = (r["flow"]["estimate"] - exact[name]) / max(r["flow"]["error"], 1e-300)
+            rec["grid_z"] = (r["vegas"]["estimate"] - exact[name]) / max(r["vegas"]["error"], 1e-300)
+        out[name] = rec
+    return out
 
 
 # ------------------------------------------------------------------------------ our arm
@@ -177,6 +258,8 @@ def main():
     ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (4096-job) leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling runs)")
+    ap.add_argument("--train-steps", type=int, default=1000, help="flow training steps in the learned leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -197,6 +280,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.learned_only:
+        if rank == 0:
+            print(json.dumps({"learned": learned_leg(capi, W, args.train_steps)}), flush=True)
+        return
 
     stream = torch.cuda.Stream(device=dev)
     job = replica_job(rank)
@@ -382,61 +470,28 @@ def main():
         batch["plain_fp64_sequential"] = {"seconds_sampled": el, "jobs_sampled": len(sample),
                                           "seconds_scaled": el / frac, "samples_per_s": 8 * tot * frac / el}
 
-    # ---- learned proposal (4-layer coupling flow, width 64, 16 bins; 2^20 samples per iteration):
-    # double Gaussian exp(-100|x - p1|^2) + exp(-100|x - p2|^2), p1 = 0.25 1, p2 = 0.75 1, and a rotated
-    # anisotropic Gaussian (random orthogonal Q, eigenvalues 1..400), d = 8. Variance per sample against
-    # the adapted grid at the same budget, and time to 1e-3 of each form.
     learned = None
     if not args.no_learned and rank == 0:
-        learned = {}
-        cases = [("double_gaussian", W.DOUBLE_GAUSSIAN, W.double_gaussian_params(8)),
-                 ("rotated_gaussian", W.ROTATED_GAUSSIAN, W.rotated_gaussian_params(8, seed=0))]
-        n_it = 1 << 20
-        for name, fid, par in cases:
-            r = capi.flow_integrate(fid, par, 8, layers=4, hidden=64, bins=16, loss="kl", vegas_iters=5, flow_iters=4,
-                                    train_steps=1000, batch=1 << 14, lr=5e-4, ncall=n_it, train_samples=1 << 20, seed=0)
-            I = abs(r["flow"]["estimate"])
-            target = (1e-3 * I) ** 2
-            g8, m8, p8 = capi.stratify(8, n_it)
-            var_it_flow = r["flow_var_per_sample"] / (m8 * p8)
-            var_it_grid = r["vegas_var_per_sample"] / (m8 * p8)
-            k_flow = int(math.ceil(var_it_flow / target))
-            k_grid = int(math.ceil(var_it_grid / target))
-            t_it_flow = r["seconds_flow"] / 4
-            # plain FP64 m-Cubes on the same integrand: per-iteration time and variance after adaptation
-            t0 = time.perf_counter()
-            pl = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP64, return_iters=True)
-            t64 = (time.perf_counter() - t0) / 9
-            v64 = float(np.mean(pl["iters"][5:, 1]))
-            k64 = int(math.ceil(v64 / target))
-            t0 = time.perf_counter()
-            p32 = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP32_EVAL, return_iters=True)
-            t32 = (time.perf_counter() - t0) / 9
-            k32 = int(math.ceil(float(np.mean(p32["iters"][5:, 1])) / target))
-            learned[name] = {
-                "flow": r["flow"], "grid": r["vegas"], "variance_gain_per_sample": r["vegas_var_per_sample"] / r["flow_var_per_sample"],
-                "train_seconds": r["seconds_train"], "flow_samples_per_s": 4 * m8 * p8 / max(r["seconds_flow"], 1e-9),
-                "time_to_1e-3_s": {
-                    "learned": r["seconds_vegas"] * 5 / 9 + r["seconds_train"] + k_flow * t_it_flow,
-                    "fp32_grid": 5 * t32 + k32 * t32, "fp64_grid": 5 * t64 + k64 * t64,
-                    "iters": {"learned": k_flow, "fp32_grid": k32, "fp64_grid": k64}},
-            }
+        learned = learned_leg(capi, W, args.train_steps)
 
     # ---- CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        cubes = 1 << 21
+        threads = host_threads()
+        grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}
+        starts = {fid: 0 for fid in fams}
+        c1 = min(1 << 20, m)
         t0 = time.perf_counter()
-        n = 0
-        for fid in fams:
-            B = state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy()
-            oracle.vsample(fid, D, pars[fid], ncall, 0, it=1, mode=1, adjust=1, B=B, t0=0, t1=min(cubes, m))
-            n += cubes * p
+        n1 = oracle_vsample_ranges(fams, pars, grids, ncall, starts, c1, 1)
+        el1 = time.perf_counter() - t0
+        cn = min((1 << 19) * threads, m)
+        t0 = time.perf_counter()
+        nn = oracle_vsample_ranges(fams, pars, grids, ncall, starts, cn, threads)
         el = time.perf_counter() - t0
-        cpu = {"value": n / el, "unit": "samples/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {cubes} sub-cubes ({cubes * p} samples) of each of the 6 families on "
-                         f"the adapted grids, FP32-eval point layout, single thread ({el:.1f} s)"}
+        cpu = {"value": nn / el, "unit": "samples/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {cn} sub-cubes ({cn * p} samples) of each of the 6 families on the adapted "
+                         f"grids, FP32-eval point layout, {threads} threads over equal sub-cube ranges ({el:.1f} s)",
+               "single_thread": {"value": n1 / el1, "sample": f"first {c1} sub-cubes of each family ({el1:.1f} s)"}}
 
     if rank == 0:
         line = {

@@ -337,6 +337,26 @@ int mcubes_flow_grad_dev(const mcubes_flow_shape *shape, const float *d_params, 
 int mcubes_flow_adam_dev(int64_t n_params, float *d_params, const float *d_grad, float *d_m, float *d_v, int step,
                          float lr, void *stream);
 
+/* Scratch bytes of mcubes_flow_sample_dev (the bf16 copy of the weights in the fused kernel's
+ * layout), or 0 when the shape is unsupported or has more than 16 layers. */
+size_t mcubes_flow_sample_work_bytes(const mcubes_flow_shape *shape);
+
+/* Fused flow-proposal sampling of samples [i0, i0 + n) of one m-Cubes iteration, in one kernel:
+ * sample i = t p + q of sub-cube t (stratification of ncall as mcubes_stratify) draws the
+ * FP32-layout Philox uniforms u (counter (t, q, iteration << 16 | j, job), key = seed), takes the
+ * latent point z = (c + u) / g (the sub-cube's strata in latent space, Sec. 3.2 stratification
+ * carried over), then x = flow^-1(z) and q(x), and the weight
+ *   d_w[i - i0] = (f(x) / F) / q(x),
+ * f evaluated in the FP32-eval form and scaled by the integrand's FP32 factor F (*fscale_out).
+ * d_x (n x d) and d_logq (n) are optional (NULL: not written). params: as mcubes_integrate.
+ * d_work: mcubes_flow_sample_work_bytes bytes, 256-byte aligned. Asynchronous on stream.
+ * Errors: INVALID_ARG (also when the shape needs more shared memory than the device offers),
+ * UNSUPPORTED_DIM, UNKNOWN_INTEGRAND, WORKSPACE, CUDA. */
+int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const float *d_params, int integrand_id,
+                           const double *params, int64_t ncall, uint64_t seed, int iteration, uint32_t job,
+                           int64_t i0, int64_t n, float *d_x, float *d_logq, float *d_w, double *fscale_out,
+                           void *d_work, size_t work_bytes, void *stream);
+
 /* Whole learned-proposal run:
  *   1. vegas_iters grid-adjusting m-Cubes iterations (FP32-eval), then flow_iters frozen-grid
  *      iterations as the reference;

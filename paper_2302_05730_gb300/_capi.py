@@ -118,6 +118,9 @@ def _load():
                                        vp]),
         "mcubes_flow_adam_dev": (i32, [i64, vp, vp, vp, vp, i32, ctypes.c_float, vp]),
         "mcubes_flow_integrate": (i32, [i32, dp, i32, ctypes.POINTER(FlowConfig), vp, ctypes.POINTER(FlowReport)]),
+        "mcubes_flow_sample_work_bytes": (ctypes.c_size_t, [ctypes.POINTER(FlowShape)]),
+        "mcubes_flow_sample_dev": (i32, [ctypes.POINTER(FlowShape), vp, i32, dp, i64, u64, i32, u32, i64, i64, vp, vp,
+                                         vp, dp, vp, ctypes.c_size_t, vp]),
         "mcubes_philox_dev": (i32, [vp, u64, u64, i32, vp, vp]),
         "mcubes_status_string": (ctypes.c_char_p, [i32]),
         "mcubes_last_cuda_error": (i32, []),
@@ -400,6 +403,23 @@ def flow_forward_dev(shape, d_params, n, d_x, d_z, d_logq, d_work, work_bytes, s
 def flow_inverse_dev(shape, d_params, n, d_z, d_x, d_logq, d_work, work_bytes, stream=None):
     _check(_lib.mcubes_flow_inverse_dev(ctypes.byref(shape), _dptr(d_params), int(n), _dptr(d_z), _dptr(d_x),
                                         _dptr(d_logq), _dptr(d_work), int(work_bytes), _stream(stream)), "flow_inverse")
+
+
+def flow_sample_work_bytes(shape: FlowShape) -> int:
+    return int(_lib.mcubes_flow_sample_work_bytes(ctypes.byref(shape)))
+
+
+def flow_sample_dev(shape, d_params, fid, params, ncall, seed, iteration, job, i0, n, d_w, d_work, work_bytes,
+                    d_x=None, d_logq=None, stream=None) -> float:
+    """Fused flow-proposal sampling of samples [i0, i0 + n) of one iteration; returns the
+    integrand's FP32 scale F (d_w holds (f / F) / q)."""
+    par, pp = _par(fid, shape.d, params)
+    F = ctypes.c_double(0.0)
+    _check(_lib.mcubes_flow_sample_dev(ctypes.byref(shape), _dptr(d_params), int(fid), pp, int(ncall),
+                                       int(seed) & (2 ** 64 - 1), int(iteration), int(job) & 0xFFFFFFFF, int(i0),
+                                       int(n), _dptr(d_x), _dptr(d_logq), _dptr(d_w), ctypes.byref(F),
+                                       _dptr(d_work), int(work_bytes), _stream(stream)), "flow_sample")
+    return F.value
 
 
 def flow_grad_dev(shape, d_params, n, d_x, d_w, loss_kind, d_grad, d_loss, d_work, work_bytes, stream=None):

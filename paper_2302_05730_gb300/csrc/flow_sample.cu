@@ -15,8 +15,9 @@
 #include <vector>
 
 #include "../../include/mcubes.h"
-#include "internal.h"
+#include "flow_common.cuh"
 #include "integrands.cuh"
+#include "internal.h"
 
 using namespace mcubes;
 
@@ -208,6 +209,405 @@ __global__ void flow_eval_kernel(const SampleSpec S, const IntegrandParams ip, d
     }
 }
 
+// ------------------------------------------------------------------------------ fused sampling
+// One launch takes a range of samples from their Philox draws to their weights:
+//   z = (c + u) / g  ->  x = flow^-1(z), log q(x)  ->  w = (f(x) / F) exp(-log q(x)).
+// A block holds 512 samples in shared memory and runs them through the layers one after the
+// other. Each layer's weights are copied once per block and tile from a bf16 mirror that
+// already has the padded shared-memory layout (16-byte copies). The MLP of a layer runs on the
+// tensor cores (mma.sync m16n8k16, bf16 operands, FP32 accumulation); the hidden activations
+// stay in registers between its three GEMMs, since the accumulator layout of one GEMM is the
+// operand layout of the next. The output of the last GEMM goes to a per-warp shared buffer, two
+// axes at a time, and each lane then transforms one (sample, axis) pair with the same
+// pq_transform as the per-layer kernels.
+constexpr int kFWarps = 8, kFThreads = kFWarps * 32, kFSub = 4, kFRows = kFWarps * 16 * kFSub;
+constexpr int kFMaxLayers = 16;
+constexpr int kFusedUnsupported = -1;   // internal: the shape does not fit the fused kernel
+
+struct FusedLayer {
+    int nA, nB;
+    int A[flow::kMaxAB], B[flow::kMaxAB];
+    uint32_t off, bytes;                 // the layer's block in the mirror (bytes, multiples of 16)
+    uint32_t oW2, oW3, ob1, ob2, ob3;    // byte offsets inside the block (W1 at 0)
+    uint32_t pW1, pb1, pW2, pb2, pW3, pb3;   // offsets of the FP32 master parameters (floats)
+};
+
+struct FusedFlow {
+    int L, H, K, SW;                     // SW: output slot width 2K+1 rounded up to 8
+    uint32_t max_bytes, total_bytes;
+    FusedLayer lay[kFMaxLayers];
+};
+
+inline uint32_t al16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// Host: the mirror layout of a flow shape. Returns false when the shape needs more layers than
+// the fused path takes.
+bool fused_layout(const flow::Shape &S, FusedFlow &F)
+{
+    if (S.L > kFMaxLayers) return false;
+    std::memset(&F, 0, sizeof(F));
+    F.L = S.L;
+    F.H = S.H;
+    F.K = S.K;
+    F.SW = (2 * S.K + 1 + 7) & ~7;
+    const uint32_t LD0 = flow::kK0 + 8, LDH = (uint32_t)S.H + 8;
+    long long pos = 0;
+    uint32_t off = 0;
+    for (int l = 0; l < S.L; ++l) {
+        const flow::LayerDesc D = flow::describe(S, l, pos);
+        FusedLayer &Y = F.lay[l];
+        Y.nA = D.nA;
+        Y.nB = D.nB;
+        for (int i = 0; i < flow::kMaxAB; ++i) {
+            Y.A[i] = D.A[i];
+            Y.B[i] = D.B[i];
+        }
+        Y.pW1 = (uint32_t)D.offW1;
+        Y.pb1 = (uint32_t)D.offb1;
+        Y.pW2 = (uint32_t)D.offW2;
+        Y.pb2 = (uint32_t)D.offb2;
+        Y.pW3 = (uint32_t)D.offW3;
+        Y.pb3 = (uint32_t)D.offb3;
+        uint32_t b = al16(2u * S.H * LD0);
+        Y.oW2 = b;
+        b = al16(b + 2u * S.H * LDH);
+        Y.oW3 = b;
+        b = al16(b + 2u * (uint32_t)(D.nB * F.SW) * LDH);
+        Y.ob1 = b;
+        b = al16(b + 4u * S.H);
+        Y.ob2 = b;
+        b = al16(b + 4u * S.H);
+        Y.ob3 = b;
+        b = al16(b + 4u * (uint32_t)(D.nB * F.SW));
+        Y.bytes = b;
+        Y.off = off;
+        off += b;
+        F.max_bytes = std::max(F.max_bytes, b);
+    }
+    F.total_bytes = off;
+    return true;
+}
+
+// The bf16 mirror of the FP32 parameters in the fused kernel's shared layout: W1 [H][kK0 + 8],
+// W2 [H][H + 8], W3 [|B| SW][H + 8] (slot j at rows j SW .. j SW + 2K), zero padding; biases FP32.
+// blockIdx.y is the layer.
+__global__ void mirror_kernel(const FusedFlow F, const float *__restrict__ p, unsigned char *__restrict__ mirror)
+{
+    const FusedLayer &Y = F.lay[blockIdx.y];
+    const int H = F.H, LD0 = flow::kK0 + 8, LDH = H + 8, no = 2 * F.K + 1;
+    unsigned char *base = mirror + Y.off;
+    __nv_bfloat16 *W1 = reinterpret_cast<__nv_bfloat16 *>(base);
+    __nv_bfloat16 *W2 = reinterpret_cast<__nv_bfloat16 *>(base + Y.oW2);
+    __nv_bfloat16 *W3 = reinterpret_cast<__nv_bfloat16 *>(base + Y.oW3);
+    float *b1 = reinterpret_cast<float *>(base + Y.ob1);
+    float *b2 = reinterpret_cast<float *>(base + Y.ob2);
+    float *b3 = reinterpret_cast<float *>(base + Y.ob3);
+    const int n1 = H * LD0, n2 = H * LDH, n3 = Y.nB * F.SW * LDH;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 + n2 + n3 + 2 * H + Y.nB * F.SW;
+         e += gridDim.x * blockDim.x) {
+        if (e < n1) {
+            const int r = e / LD0, c = e - r * LD0;
+            W1[e] = __float2bfloat16_rn(c < Y.nA ? p[Y.pW1 + r * Y.nA + c] : 0.f);
+        } else if (e < n1 + n2) {
+            const int f = e - n1, r = f / LDH, c = f - r * LDH;
+            W2[f] = __float2bfloat16_rn(c < H ? p[Y.pW2 + r * H + c] : 0.f);
+        } else if (e < n1 + n2 + n3) {
+            const int f = e - n1 - n2, r = f / LDH, c = f - r * LDH, j = r / F.SW, k = r - j * F.SW;
+            W3[f] = __float2bfloat16_rn((c < H && k < no) ? p[Y.pW3 + (j * no + k) * H + c] : 0.f);
+        } else if (e < n1 + n2 + n3 + H) {
+            b1[e - n1 - n2 - n3] = p[Y.pb1 + e - n1 - n2 - n3];
+        } else if (e < n1 + n2 + n3 + 2 * H) {
+            b2[e - n1 - n2 - n3 - H] = p[Y.pb2 + e - n1 - n2 - n3 - H];
+        } else {
+            const int f = e - n1 - n2 - n3 - 2 * H, j = f / F.SW, k = f - j * F.SW;
+            b3[f] = k < no ? p[Y.pb3 + j * no + k] : 0.f;
+        }
+    }
+}
+
+template <int H, int K>
+constexpr int fused_min_blocks()
+{
+    return H <= 64 ? 2 : 1;
+}
+
+template <int H, int K>
+size_t fused_smem(const FusedFlow &F, int d)
+{
+    constexpr int SW = (2 * K + 1 + 7) & ~7;
+    const int HS = d | 1;
+    return (size_t)F.max_bytes + sizeof(float) * ((size_t)kFRows * HS + kFRows + (size_t)kFWarps * 2 * 16 * (SW + 1));
+}
+
+// Samples [i0, i0 + n) of one iteration (sample i = t p + q, t the sub-cube): x (optional,
+// n x d), log q (optional) and the weight w = (f / F) / q, all indexed from i0.
+template <int H, int K>
+__global__ void __launch_bounds__(kFThreads, fused_min_blocks<H, K>())
+    flow_sample_kernel(const FusedFlow F, const unsigned char *__restrict__ mirror, const SampleSpec S,
+                       const IntegrandParams ip, long long i0, long long n, float *__restrict__ x_out,
+                       float *__restrict__ lq_out, float *__restrict__ w_out)
+{
+    constexpr int SW = (2 * K + 1 + 7) & ~7, NT3 = SW / 8, OS = SW + 1, LD0 = flow::kK0 + 8, LDH = H + 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int d = S.d, HS = d | 1;
+    unsigned char *wbuf = smem;
+    float *hs = reinterpret_cast<float *>(smem + F.max_bytes);
+    float *lqs = hs + kFRows * HS;
+    float *obuf = lqs + kFRows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int row = lane & 15, half = lane >> 4;
+    float *ob = obuf + warp * 2 * 16 * OS;
+    const float ig = 1.0f / (float)S.g;
+    const long long ntiles = (n + kFRows - 1) / kFRows;
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long j0 = tile * kFRows;      // first sample of the tile, relative to i0
+        for (int r = threadIdx.x; r < kFRows; r += kFThreads) {
+            float *hr = hs + r * HS;
+            if (j0 + r < n) {
+                const long long i = i0 + j0 + r;
+                const uint32_t tc = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
+                uint32_t c[kDMax];
+                digits(tc, S.g, d, c);
+                for (int a = 0; a < d; ++a) {
+                    const float u = uniform32(tc, q, S.ctr2_hi, S.job, S.key0, S.key1, a);
+                    hr[a] = fminf(((float)c[a] + u) * ig, 0.99999994f);
+                }
+            } else {
+                for (int a = 0; a < d; ++a) hr[a] = 0.5f;
+            }
+            lqs[r] = 0.f;
+        }
+        for (int l = F.L - 1; l >= 0; --l) {
+            const FusedLayer &Y = F.lay[l];
+            __syncthreads();   // the previous layer is done with the weight buffer; hs is complete
+            {
+                const uint4 *src = reinterpret_cast<const uint4 *>(mirror + Y.off);
+                uint4 *dst = reinterpret_cast<uint4 *>(wbuf);
+                for (uint32_t e = threadIdx.x; e < Y.bytes / 16u; e += kFThreads) dst[e] = src[e];
+            }
+            __syncthreads();
+            const __nv_bfloat16 *W1 = reinterpret_cast<const __nv_bfloat16 *>(wbuf);
+            const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(wbuf + Y.oW2);
+            const __nv_bfloat16 *W3 = reinterpret_cast<const __nv_bfloat16 *>(wbuf + Y.oW3);
+            const float *b1 = reinterpret_cast<const float *>(wbuf + Y.ob1);
+            const float *b2 = reinterpret_cast<const float *>(wbuf + Y.ob2);
+            const float *b3 = reinterpret_cast<const float *>(wbuf + Y.ob3);
+            const int cA0 = 2 * t, cA1 = 2 * t + 1;
+            const int xA0 = cA0 < Y.nA ? Y.A[cA0] : -1, xA1 = cA1 < Y.nA ? Y.A[cA1] : -1;
+            for (int sub = 0; sub < kFSub; ++sub) {
+                const int R0 = (warp * kFSub + sub) * 16;
+                // GEMM 1 operand: the A axes of rows R0 + g and R0 + g + 8, columns >= |A| zero
+                uint32_t a1[4];
+                {
+                    const float *hA = hs + (R0 + g) * HS, *hB = hs + (R0 + g + 8) * HS;
+                    a1[0] = flow::pack_bf16(xA0 >= 0 ? hA[xA0] : 0.f, xA1 >= 0 ? hA[xA1] : 0.f);
+                    a1[1] = flow::pack_bf16(xA0 >= 0 ? hB[xA0] : 0.f, xA1 >= 0 ? hB[xA1] : 0.f);
+                    a1[2] = 0u;
+                    a1[3] = 0u;
+                }
+                uint32_t a2[H / 16][4];
+                {
+                    float acc[H / 8][4] = {};
+#pragma unroll
+                    for (int nt = 0; nt < H / 8; ++nt) {
+                        const __nv_bfloat16 *bp = W1 + (nt * 8 + g) * LD0 + 2 * t;
+                        flow::mma16816(acc[nt], a1, flow::ld32(bp), flow::ld32(bp + 8));
+                    }
+#pragma unroll
+                    for (int kt = 0; kt < H / 16; ++kt) {
+                        const int c = 16 * kt + 2 * t;
+                        a2[kt][0] = flow::pack_bf16(fmaxf(acc[2 * kt][0] + b1[c], 0.f), fmaxf(acc[2 * kt][1] + b1[c + 1], 0.f));
+                        a2[kt][1] = flow::pack_bf16(fmaxf(acc[2 * kt][2] + b1[c], 0.f), fmaxf(acc[2 * kt][3] + b1[c + 1], 0.f));
+                        a2[kt][2] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][0] + b1[c + 8], 0.f),
+                                                    fmaxf(acc[2 * kt + 1][1] + b1[c + 9], 0.f));
+                        a2[kt][3] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][2] + b1[c + 8], 0.f),
+                                                    fmaxf(acc[2 * kt + 1][3] + b1[c + 9], 0.f));
+                    }
+                }
+                uint32_t a3[H / 16][4];
+                {
+                    float acc[H / 8][4] = {};
+#pragma unroll
+                    for (int kt = 0; kt < H / 16; ++kt)
+#pragma unroll
+                        for (int nt = 0; nt < H / 8; ++nt) {
+                            const __nv_bfloat16 *bp = W2 + (nt * 8 + g) * LDH + kt * 16 + 2 * t;
+                            flow::mma16816(acc[nt], a2[kt], flow::ld32(bp), flow::ld32(bp + 8));
+                        }
+#pragma unroll
+                    for (int kt = 0; kt < H / 16; ++kt) {
+                        const int c = 16 * kt + 2 * t;
+                        a3[kt][0] = flow::pack_bf16(fmaxf(acc[2 * kt][0] + b2[c], 0.f), fmaxf(acc[2 * kt][1] + b2[c + 1], 0.f));
+                        a3[kt][1] = flow::pack_bf16(fmaxf(acc[2 * kt][2] + b2[c], 0.f), fmaxf(acc[2 * kt][3] + b2[c + 1], 0.f));
+                        a3[kt][2] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][0] + b2[c + 8], 0.f),
+                                                    fmaxf(acc[2 * kt + 1][1] + b2[c + 9], 0.f));
+                        a3[kt][3] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][2] + b2[c + 8], 0.f),
+                                                    fmaxf(acc[2 * kt + 1][3] + b2[c + 9], 0.f));
+                    }
+                }
+                float lq = 0.f;
+                for (int jp = 0; jp < Y.nB; jp += 2) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int j = jp + hh;
+                        if (j < Y.nB) {   // warp-uniform
+                            float acc[NT3][4] = {};
+#pragma unroll
+                            for (int kt = 0; kt < H / 16; ++kt)
+#pragma unroll
+                                for (int nt = 0; nt < NT3; ++nt) {
+                                    const __nv_bfloat16 *bp = W3 + (j * SW + nt * 8 + g) * LDH + kt * 16 + 2 * t;
+                                    flow::mma16816(acc[nt], a3[kt], flow::ld32(bp), flow::ld32(bp + 8));
+                                }
+                            float *o = ob + hh * 16 * OS;
+#pragma unroll
+                            for (int nt = 0; nt < NT3; ++nt) {
+                                const int c = nt * 8 + 2 * t;
+                                o[g * OS + c] = acc[nt][0] + b3[j * SW + c];
+                                o[g * OS + c + 1] = acc[nt][1] + b3[j * SW + c + 1];
+                                o[(g + 8) * OS + c] = acc[nt][2] + b3[j * SW + c];
+                                o[(g + 8) * OS + c + 1] = acc[nt][3] + b3[j * SW + c + 1];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    const int j = jp + half;
+                    if (j < Y.nB) {
+                        float *hv = hs + (R0 + row) * HS + Y.B[j];
+                        float out, q;
+                        flow::pq_transform<K>(ob + half * 16 * OS + row * OS, *hv, 1, out, q);
+                        *hv = out;
+                        lq += __logf(q);
+                    }
+                    __syncwarp();
+                }
+                lq += __shfl_xor_sync(0xffffffffu, lq, 16);
+                if (half == 0) lqs[R0 + row] += lq;
+            }
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < kFRows; r += kFThreads) {
+            const long long jr = j0 + r;
+            if (jr >= n) continue;
+            float x[kDMax];
+            for (int a = 0; a < d; ++a) x[a] = hs[r * HS + a];
+            const float lq = lqs[r];
+            w_out[jr] = eval32(S.fid, d, ip, x) * __expf(-lq);
+            if (x_out)
+                for (int a = 0; a < d; ++a) x_out[jr * d + a] = x[a];
+            if (lq_out) lq_out[jr] = lq;
+        }
+        __syncthreads();   // the next tile overwrites hs and lqs
+    }
+}
+
+// Per-cube mean and variance of the weights w of ncubes whole sub-cubes (p samples each, from
+// the first), compensated per-thread sums, block reduction, two FP64 atomics (scaled by F).
+__global__ void cube_stats_kernel(const SampleSpec S, double fscale, long long ncubes, const float *__restrict__ wv,
+                                  double *__restrict__ sums)
+{
+    float cI = 0.f, eI = 0.f, cV = 0.f, eV = 0.f;
+    const float inv_p = 1.0f / (float)S.p;
+    for (long long tc = blockIdx.x * (long long)blockDim.x + threadIdx.x; tc < ncubes;
+         tc += (long long)gridDim.x * blockDim.x) {
+        float w0 = 0.f, S1 = 0.f, S2 = 0.f;
+        for (uint32_t q = 0; q < S.p; ++q) {
+            const float w = wv[tc * S.p + q];
+            if (q == 0) {
+                w0 = w;
+            } else {
+                const float dv = w - w0;
+                S1 += dv;
+                S2 = fmaf(dv, dv, S2);
+            }
+        }
+        const float mean = fmaf(S1, inv_p, w0);
+        const float var = fmaxf(fmaf(-S1 * inv_p, S1, S2), 0.f);
+        const float tI = cI + mean;
+        eI += (fabsf(cI) >= fabsf(mean)) ? ((cI - tI) + mean) : ((mean - tI) + cI);
+        cI = tI;
+        const float tV = cV + var;
+        eV += (cV >= var) ? ((cV - tV) + var) : ((var - tV) + cV);
+        cV = tV;
+    }
+    double sI = (double)cI + (double)eI, sV = (double)cV + (double)eV;
+    for (int o = 16; o > 0; o >>= 1) {
+        sI += __shfl_xor_sync(0xffffffffu, sI, o);
+        sV += __shfl_xor_sync(0xffffffffu, sV, o);
+    }
+    __shared__ double red[2][32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wp] = sI;
+        red[1][wp] = sV;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) {
+            a += red[0][k];
+            b += red[1][k];
+        }
+        const double pp = (double)S.p;
+        atomicAdd(&sums[0], a * fscale);
+        atomicAdd(&sums[1], b * fscale * fscale / (pp * (pp - 1.0)));
+    }
+}
+
+template <int H, int K>
+int launch_fused_hk(const FusedFlow &F, const unsigned char *mirror, const SampleSpec &S, const IntegrandParams &ip,
+                    long long i0, long long n, float *x, float *lq, float *w, cudaStream_t s)
+{
+    const size_t smem = fused_smem<H, K>(F, S.d);
+    int dev = 0, optin = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (smem > (size_t)optin) return kFusedUnsupported;
+    e = cudaFuncSetAttribute(flow_sample_kernel<H, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flow_sample_kernel<H, K>, kFThreads, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (per_sm < 1) return kFusedUnsupported;
+    const long long tiles = (n + kFRows - 1) / kFRows;
+    const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
+    flow_sample_kernel<H, K><<<(unsigned)grid, kFThreads, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w);
+    return cuda_status(cudaGetLastError());
+}
+
+template <int H>
+int launch_fused_h(const FusedFlow &F, const unsigned char *mirror, const SampleSpec &S, const IntegrandParams &ip,
+                   long long i0, long long n, float *x, float *lq, float *w, cudaStream_t s)
+{
+    switch (F.K) {
+    case 4: return launch_fused_hk<H, 4>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    case 8: return launch_fused_hk<H, 8>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    case 16: return launch_fused_hk<H, 16>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    case 32: return launch_fused_hk<H, 32>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    default: return MCUBES_ERR_INVALID_ARG;
+    }
+}
+
+int launch_fused(const FusedFlow &F, const unsigned char *mirror, const SampleSpec &S, const IntegrandParams &ip,
+                 long long i0, long long n, float *x, float *lq, float *w, cudaStream_t s)
+{
+    if (n <= 0) return MCUBES_OK;
+    switch (F.H) {
+    case 32: return launch_fused_h<32>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    case 64: return launch_fused_h<64>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    case 128: return launch_fused_h<128>(F, mirror, S, ip, i0, n, x, lq, w, s);
+    default: return MCUBES_ERR_INVALID_ARG;
+    }
+}
+
+int build_mirror(const FusedFlow &F, const float *d_params, unsigned char *mirror, cudaStream_t s)
+{
+    mirror_kernel<<<dim3(64, (unsigned)F.L), 256, 0, s>>>(F, d_params, mirror);
+    return cuda_status(cudaGetLastError());
+}
+
 // Weights for training: variance loss w^2, KL |w|, normalised so a batch of `batch` sums to 1
 // (total read on the device; a set whose total is not positive and finite trains on zero weights).
 __global__ void train_weights_kernel(const float *__restrict__ w, long long n, int kind, const double *__restrict__ total,
@@ -266,6 +666,40 @@ double seconds_since(std::chrono::steady_clock::time_point t0)
 
 }  // namespace
 
+extern "C" size_t mcubes_flow_sample_work_bytes(const mcubes_flow_shape *shape)
+{
+    if (!shape || mcubes_flow_param_count(shape) <= 0) return 0;
+    FusedFlow F;
+    if (!fused_layout(flow::Shape{shape->d, shape->layers, shape->hidden, shape->bins}, F)) return 0;
+    return F.total_bytes;
+}
+
+extern "C" int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const float *d_params, int integrand_id,
+                                      const double *params, int64_t ncall, uint64_t seed, int iteration, uint32_t job,
+                                      int64_t i0, int64_t n, float *d_x, float *d_logq, float *d_w, double *fscale_out,
+                                      void *d_work, size_t work_bytes, void *stream)
+{
+    if (!shape || !d_params || !params || !d_w || n < 0 || i0 < 0 || iteration < 0 || iteration > 0xFFFF)
+        return MCUBES_ERR_INVALID_ARG;
+    if (mcubes_flow_param_count(shape) <= 0) return MCUBES_ERR_INVALID_ARG;
+    const flow::Shape S{shape->d, shape->layers, shape->hidden, shape->bins};
+    FusedFlow F;
+    if (!fused_layout(S, F)) return MCUBES_ERR_INVALID_ARG;
+    if (!d_work || work_bytes < F.total_bytes || ((uintptr_t)d_work & 255u)) return MCUBES_ERR_WORKSPACE;
+    Problem pb;
+    int st = prepare(integrand_id, params, S.d, ncall, seed, 0, 0, 0, MCUBES_FP32_EVAL, pb);
+    if (st) return st;
+    if (i0 + n > pb.m * pb.p) return MCUBES_ERR_INVALID_ARG;
+    if (fscale_out) *fscale_out = pb.P.fscale;
+    const SampleSpec SS{(uint32_t)pb.m, (uint32_t)pb.p, (uint32_t)pb.g, (uint32_t)seed, (uint32_t)(seed >> 32),
+                        (uint32_t)iteration << 16, job, S.d, integrand_id};
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *mirror = (unsigned char *)d_work;
+    if ((st = build_mirror(F, d_params, mirror, s))) return st;
+    st = launch_fused(F, mirror, SS, pb.P.ip, i0, n, d_x, d_logq, d_w, s);
+    return st == kFusedUnsupported ? MCUBES_ERR_INVALID_ARG : st;
+}
+
 extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int d, const mcubes_flow_config *cfg,
                                      float *params_out, mcubes_flow_report *out)
 {
@@ -307,11 +741,14 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     const long long chunk_cubes = std::max<long long>(1, (1LL << 20) / p);
     const long long nchunk = chunk_cubes * p;
     const long long nwork = std::max<long long>(cfg->batch, nchunk);
+    FusedFlow FF;
+    const bool fused_ok = fused_layout(flow::Shape{sh.d, sh.layers, sh.hidden, sh.bins}, FF);
     const size_t wbytes = mcubes_flow_work_bytes(&sh, nwork);
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t bytes = al(sizeof(double) * d * kGS) + 2 * al(sizeof(float) * ntr * d) + 3 * al(sizeof(float) * ntr) +
                          4 * al(sizeof(float) * npar) + al(sizeof(float) * 2) + al(sizeof(double) * (2 * (size_t)cfg->flow_iters + 2)) +
-                         2 * al(sizeof(float) * nchunk * d) + al(sizeof(float) * nchunk) + al(wbytes);
+                         2 * al(sizeof(float) * nchunk * d) + al(sizeof(float) * nchunk) + al(wbytes) +
+                         al(fused_ok ? FF.total_bytes : 16);
     char *mem = nullptr;
     if ((st = cuda_status(cudaMalloc(&mem, bytes)))) return st;
     char *q = mem;
@@ -330,6 +767,7 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     float *d_xs = (float *)take(sizeof(float) * nchunk * d);
     float *d_lq = (float *)take(sizeof(float) * nchunk);
     void *d_work = take(wbytes);
+    unsigned char *d_mirror = (unsigned char *)take(fused_ok ? FF.total_bytes : 16);
     cudaStream_t s = nullptr;
     auto finish = [&](int code) {
         if (s) cudaStreamDestroy(s);
@@ -407,15 +845,30 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     if ((st = cuda_status(cudaStreamSynchronize(s)))) return finish(st);
     out->seconds_train = seconds_since(t0);
 
-    // ---- 4. m-Cubes iterations with the flow as proposal
+    // ---- 4. m-Cubes iterations with the flow as proposal: the fused sampling kernel where the
+    // shape fits it (shared memory, at most 16 layers), else the per-layer kernels
     t0 = std::chrono::steady_clock::now();
     if ((st = cuda_status(cudaMemsetAsync(d_sums, 0, sizeof(double) * 2 * cfg->flow_iters, s)))) return finish(st);
+    bool fused = fused_ok;
+    if (fused && (st = build_mirror(FF, d_par, d_mirror, s))) return finish(st);
     for (int it = 0; it < cfg->flow_iters; ++it) {
         SampleSpec F{(uint32_t)m, (uint32_t)p, (uint32_t)g, (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32),
                      (uint32_t)(itmax + 2 + it) << 16, 0x20000000u, d, integrand_id};
         for (long long c0 = 0; c0 < m; c0 += chunk_cubes) {
             const long long nc = std::min<long long>(chunk_cubes, m - c0);
             const long long ns = nc * p;
+            if (fused) {
+                st = launch_fused(FF, d_mirror, F, pb.P.ip, c0 * p, ns, nullptr, nullptr, d_lq, s);
+                if (st == kFusedUnsupported) {
+                    fused = false;
+                } else {
+                    if (st) return finish(st);
+                    cube_stats_kernel<<<(unsigned)std::min<long long>((nc + 255) / 256, 65535), 256, 0, s>>>(
+                        F, pb.P.fscale, nc, d_lq, d_sums + 2 * it);
+                    if ((st = cuda_status(cudaGetLastError()))) return finish(st);
+                    continue;
+                }
+            }
             latent_kernel<<<(unsigned)std::min<long long>((ns + 255) / 256, 65535), 256, 0, s>>>(F, c0 * p, ns, d_z);
             if ((st = cuda_status(cudaGetLastError()))) return finish(st);
             if ((st = mcubes_flow_inverse_dev(&sh, d_par, ns, d_z, d_xs, d_lq, d_work, wbytes, s))) return finish(st);

@@ -152,3 +152,31 @@ def test_integrate_range_argument_checks(capi):
     assert _status(lambda: capi.integrate_range(W.GAUSSIAN, par, 3, 1000, 6, 3, 4, 4, 0)) == 1   # empty range
     assert _status(lambda: capi.integrate_range(W.GAUSSIAN, par, 3, 1000, 6, 3, 5, 7, 0,
                                                 grid_in=oracle.uniform_grid(3))) == 1          # past itmax
+
+
+def test_flow_sample_work_bytes_and_argument_checks(capi):
+    """The fused sampler's scratch is the bf16 weight mirror: per layer W1 [H][24], W2 [H][H+8],
+    W3 [|B| SW][H+8] (bf16) and the biases (FP32), each 16-byte aligned; SW = 2K+1 rounded up to 8.
+    Argument and workspace checks answer before any CUDA call."""
+    def layer_bytes(H, nB, K):
+        al = lambda b: (b + 15) // 16 * 16
+        SW = (2 * K + 1 + 7) // 8 * 8
+        return al(2 * H * 24) + al(2 * H * (H + 8)) + al(2 * nB * SW * (H + 8)) + 2 * al(4 * H) + al(4 * nB * SW)
+    assert capi.flow_sample_work_bytes(capi.flow_shape(8, 4, 64, 16)) == 4 * layer_bytes(64, 4, 16)
+    # d = 7: |B| = 4, 3, 3, 4 (upper half, lower half, odd axes, even axes)
+    n7 = capi.flow_sample_work_bytes(capi.flow_shape(7, 4, 32, 8))
+    assert n7 == sum(layer_bytes(32, nb, 8) for nb in (4, 3, 3, 4))
+    assert capi.flow_sample_work_bytes(capi.flow_shape(8, 17, 64, 16)) == 0    # more than 16 layers
+    assert capi.flow_sample_work_bytes(capi.flow_shape(8, 4, 48, 16)) == 0     # unsupported width
+    par = W.genz_params(W.GAUSSIAN, 8)
+    sh = capi.flow_shape(8, 4, 64, 16)
+    nb = capi.flow_sample_work_bytes(sh)
+    call = lambda **kw: capi.flow_sample_dev(sh, kw.get("p", 1 << 20), W.GAUSSIAN, par, kw.get("ncall", 1 << 20), 0,
+                                             0, 0, kw.get("i0", 0), kw.get("n", 100), 2 << 20, kw.get("ws", 3 << 20),
+                                             kw.get("nb", nb))
+    assert _status(lambda: call(n=-1)) == 1
+    assert _status(lambda: call(ws=None)) == 8
+    assert _status(lambda: call(ws=(3 << 20) + 64)) == 8
+    assert _status(lambda: call(nb=nb - 16)) == 8
+    assert _status(lambda: call(i0=781250 - 50)) == 1       # past the iteration's m p samples
+    assert _status(lambda: call(p=None)) == 1

@@ -82,6 +82,85 @@ def test_flow_density_and_sampling_match_oracle(capi, d, L, H, K):
     assert np.median(np.abs(dl3.cpu().numpy() - dl2.cpu().numpy())) < 1e-4
 
 
+def _latent_fp32(d, g, p, seed, iteration, job, i0, n):
+    """Latent points of samples [i0, i0 + n) as the fused kernel draws them (FP32 layout):
+    Philox call a // 4 of counter (t, q, iteration << 16 | a // 4, job), word a % 4, low 23 bits;
+    z = min((c_a + u) * (1 / g), 1 - 2^-24) in single precision."""
+    import oracle
+    z = np.empty((n, d), dtype=np.float32)
+    ig = np.float32(1.0) / np.float32(g)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for r in range(n):
+        i = i0 + r
+        t, q = i // p, i % p
+        c, tt = [], t
+        for _ in range(d):
+            c.append(tt % g)
+            tt //= g
+        words = []
+        for j in range((d + 3) // 4):
+            words += oracle.philox([t, q, (iteration << 16) | j, job], key)
+        for a in range(d):
+            u = np.float32(words[a] & 0x7FFFFF) * np.float32(2.0 ** -23)
+            z[r, a] = min(np.float32((np.float32(c[a]) + u) * ig), np.float32(0.99999994))
+    return z
+
+
+FUSED_CASES = [(8, 4, 64, 16, 3, 1 << 20, 12345, 3001), (5, 3, 32, 8, 3, 200000, 777, 1500),
+               (10, 6, 128, 16, 1, 10 ** 9, 10 ** 8 + 5, 1100), (7, 5, 64, 4, 9, 300000, 0, 1300),
+               (16, 4, 64, 16, 6, 10 ** 8, 4096, 700), (8, 4, 64, 32, 9, 1 << 20, 99, 900)]
+
+
+@pytest.mark.parametrize("d,L,H,K,fid,ncall,i0,n", FUSED_CASES)
+def test_fused_flow_sampling_matches_oracle(capi, d, L, H, K, fid, ncall, i0, n):
+    """The fused sampling kernel (Philox latent point -> flow^-1 -> integrand weight) against the
+    oracle: latent points from the oracle's Philox, x and log q from the oracle flow with bf16
+    MLP operands, the weight from the oracle integrand at the kernel's x. Ragged n (not a
+    multiple of the 512-sample tile), offset i0, shapes up to d = 16 and width 128."""
+    import oracle
+    from paper_2302_05730_gb300 import workloads as W
+    p = _params(d, L, H, K, seed=d * 31 + L)
+    par = (W.rotated_gaussian_params(d, seed=1) if fid == W.ROTATED_GAUSSIAN else W.genz_params(fid, d, seed=2))
+    shape = capi.flow_shape(d, L, H, K)
+    nb = capi.flow_sample_work_bytes(shape)
+    assert nb > 0
+    buf = torch.empty(nb // 4 + 128, dtype=torch.float32, device="cuda")
+    ws = (buf.data_ptr() + 255) // 256 * 256
+    dp = torch.from_numpy(p).cuda()
+    dx = torch.empty((n, d), dtype=torch.float32, device="cuda")
+    dl = torch.empty(n, dtype=torch.float32, device="cuda")
+    dw = torch.empty(n, dtype=torch.float32, device="cuda")
+    seed, it, job = 0x1234ABCD5678, 7, 3
+    Fs = capi.flow_sample_dev(shape, dp, fid, par, ncall, seed, it, job, i0, n, dw, ws, nb, d_x=dx, d_logq=dl)
+    torch.cuda.synchronize()
+    g, m, pp = capi.stratify(d, ncall)
+    z = _latent_fp32(d, g, pp, seed, it, job, i0, n)
+    x_ref, lq_ref = F.inverse(p.astype(np.float64), z.astype(np.float64), d, L, H, K, use_bf16=True)
+    xg, lg, wg = dx.cpu().numpy(), dl.cpu().numpy(), dw.cpu().numpy()
+    ex = np.abs(xg - x_ref).max(axis=1)
+    el = np.abs(lg - lq_ref)
+    # most samples agree to FP32 rounding; a bf16 tie that rounds the other way moves a few by
+    # up to a bf16 step, more often the more layers and units there are
+    assert np.median(ex) < 2e-6 and np.mean(ex > 1e-4) < 1e-2 and ex.max() < 2e-2, \
+        (np.median(ex), np.mean(ex > 1e-4), ex.max())
+    assert np.median(el) < 2e-5 and np.mean(el > 1e-3) < 1e-2 and el.max() < 2e-1, \
+        (np.median(el), np.mean(el > 1e-3), el.max())
+    # the weight against the oracle integrand at the kernel's own point (FP32-eval rounding)
+    f_ref = oracle.integrand(fid, d, par, xg.astype(np.float64))
+    w_ref = f_ref * np.exp(-lg.astype(np.float64)) / Fs
+    scale = np.abs(w_ref).max() + 1e-30
+    assert np.allclose(wg, w_ref, rtol=2e-4, atol=1e-6 * scale), np.abs(wg - w_ref).max() / scale
+    # the per-layer kernels on the same latent points give the same samples
+    wsz, nbz, keep = _work(capi, shape, n)
+    dz = torch.from_numpy(z).cuda()
+    dx2 = torch.empty_like(dx)
+    dl2 = torch.empty_like(dl)
+    capi.flow_inverse_dev(shape, dp, n, dz, dx2, dl2, wsz, nbz)
+    torch.cuda.synchronize()
+    assert np.median(np.abs(dx2.cpu().numpy() - xg)) < 1e-6
+    assert np.median(np.abs(dl2.cpu().numpy() - lg)) < 1e-5
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("d,L,H,K,sub,scale", [(4, 2, 32, 4, None, 0.2), (8, 4, 64, 16, 400, 0.1)])
 def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, scale, kind):
