@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 
 D = 8
 NCALL = 10 ** 8
+# DRAM bytes (read + write) per vsample_kernel<8, oscillatory, FP32-eval> launch at d = 8, 1e8 samples
+# per iteration, from one ncu capture of this kernel as it stands: the mean over the 5 adjusting and
+# 5 frozen launches of one integration, and each kind's own mean.
+VSAMPLE_DRAM_BYTES = 143386
+VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 160768, "frozen": 126003}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts: 152 SMs, 4 SM sub-partitions x 32 lanes issue one instruction per clock.
@@ -295,38 +300,63 @@ def main():
     pars = {fid: W.genz_params(fid, D, seed=0) for fid in fams}
     uni = torch.from_numpy(np.tile(np.arange(NB + 1, dtype=np.float64) / NB, (D, 1))).to(dev)
 
+    ITMAX, ADJ = 10, 5   # one m-Cubes integration: 10 iterations, the first 5 adjust the grid
+    n_fam = len(fams)
+    sums_all = torch.zeros((n_fam, ITMAX, 2), dtype=torch.float64, device=dev)
+    sums_host = torch.zeros((n_fam, ITMAX, 2), dtype=torch.float64).pin_memory()
+
     def fresh_state():
         st = {}
         for fid in fams:
             st[fid] = dict(grid=[uni.clone(), torch.empty_like(uni)], cur=0,
-                           C=torch.zeros(D * NB, dtype=torch.float64, device=dev),
-                           sums=torch.zeros(2, dtype=torch.float64, device=dev))
+                           C=torch.zeros(D * NB, dtype=torch.float64, device=dev))
         return st
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
-    it_counter = [0]
+    run_counter = [0]
     launches = [0]
 
     def step(state, prec, kernel_events=None):
-        it = it_counter[0] % 65536
-        it_counter[0] += 1
-        for fid in fams:
+        """One whole integration of each family (all hot-path rows): uniform grid, ITMAX
+        V-Sample passes (the first ADJ accumulate bin contributions and rebin), the sums of every
+        iteration to the host in one copy; the host combination follows the step."""
+        seed = run_counter[0]
+        run_counter[0] += 1
+        sums_all.zero_()
+        for f, fid in enumerate(fams):
             s = state[fid]
-            s["C"].zero_()
-            s["sums"].zero_()
-            gin, gout = s["grid"][s["cur"]], s["grid"][1 - s["cur"]]
-            if kernel_events is not None:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            capi.vsample_dev(fid, pars[fid], D, ncall, 0, it, job, 1, prec, gin, s["C"], s["sums"],
-                             stream=stream)
-            if kernel_events is not None:
-                e1.record(stream)
-                kernel_events.append((fid, e0, e1))
-            capi.rebin_dev(D, gin, s["C"], gout, stream=stream)
-            launches[0] += 2
-            s["cur"] = 1 - s["cur"]
+            s["grid"][0].copy_(uni)
+            s["cur"] = 0
+            for it in range(ITMAX):
+                adjust = it < ADJ
+                if adjust:
+                    s["C"].zero_()
+                gin, gout = s["grid"][s["cur"]], s["grid"][1 - s["cur"]]
+                if kernel_events is not None:
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                capi.vsample_dev(fid, pars[fid], D, ncall, seed, it, job, int(adjust), prec, gin,
+                                 s["C"] if adjust else None, sums_all[f, it], stream=stream)
+                if kernel_events is not None:
+                    e1.record(stream)
+                    kernel_events.append((fid, adjust, e0, e1))
+                launches[0] += 1
+                if adjust and it + 1 < ITMAX:
+                    capi.rebin_dev(D, gin, s["C"], gout, stream=stream)
+                    launches[0] += 1
+                    s["cur"] = 1 - s["cur"]
+        sums_host.copy_(sums_all, non_blocking=True)
+
+    def combine_all():
+        """The combination (mcubes_combine) of every family's iterations after a step."""
+        out = {}
+        for f, fid in enumerate(fams):
+            it = sums_host[f].numpy().copy()
+            it[:, 0] /= m
+            it[:, 1] /= float(m) * float(m)
+            out[fid] = capi.combine(it)
+        return out
 
     def barrier():
         if dist is not None:
@@ -341,6 +371,7 @@ def main():
         barrier()
         launches[0] = 0
         step_ms = []
+        res = None
         for _ in range(steps):
             flush.add_(1.0)   # evict L2 between timed steps (outside the timed events)
             torch.cuda.synchronize(dev)
@@ -352,28 +383,24 @@ def main():
             b.record(stream)
             b.synchronize()
             step_ms.append(a.elapsed_time(b))
+            res = combine_all()
         barrier()
         total_ms = max_over_ranks(sum(step_ms), dist, dev)
-        # sanity: estimates are finite
-        for fid in fams:
-            v = state[fid]["sums"].cpu().numpy()
-            assert np.all(np.isfinite(v)), (fid, v)
-        return total_ms, state
+        for fid in fams:   # sanity: the last step's estimates are finite
+            assert math.isfinite(res[fid]["estimate"]) and math.isfinite(res[fid]["error"]), (fid, res[fid])
+        return total_ms, state, res
 
     # ---- headline: FP32-eval
     clocks = ClockSampler(local)
     clocks.start()
     kern_ev = []
-    total_ms, state32 = timed(capi.FP32_EVAL, args.steps, args.warmup, kern_ev)
+    total_ms, state32, res32 = timed(capi.FP32_EVAL, args.steps, args.warmup, kern_ev)
     clk = clocks.stop()
     n_launch = launches[0]
     ms_step = total_ms / args.steps
-    value = samples * len(fams) * args.steps * world / (total_ms * 1e-3)
+    value = samples * n_fam * ITMAX * args.steps * world / (total_ms * 1e-3)
 
-    # dominant kernel: the V-Sample launches inside the timed region
-    kms = [e0.elapsed_time(e1) for (_, e0, e1) in kern_ev]
-    avg_kms = sum(kms) / len(kms)
-    ops = sum(algorithmic_ops_per_sample(fid, D, True, True) for fid in fams) / len(fams) * samples
+    # dominant kernel: the V-Sample launches inside the timed region (adjusting and frozen)
     sm_mhz = FALLBACK_SM_MHZ
     peak_src = "fallback (2070 MHz max SM clock)"
     if os.path.exists(PEAKS_FILE):
@@ -383,40 +410,53 @@ def main():
         except (ValueError, OSError):
             pass
     peak = sm_peak_ops(sm_mhz) / 1e12
-    achieved = ops / (avg_kms * 1e-3) / 1e12
+    kinds = {}
+    for adj in (True, False):
+        ev = [(fid, e0.elapsed_time(e1)) for (fid, a_, e0, e1) in kern_ev if a_ == adj]
+        ops_k = sum(algorithmic_ops_per_sample(fid, D, adj, True) * samples for fid, _ in ev)
+        ms_k = sum(t for _, t in ev)
+        name = "adjusting" if adj else "frozen"
+        kinds[name] = {
+            "launches": len(ev), "avg_launch_ms": ms_k / len(ev), "samples_per_s": samples * len(ev) / (ms_k * 1e-3),
+            "achieved": ops_k / (ms_k * 1e-3) / 1e12, "frac": ops_k / (ms_k * 1e-3) / 1e12 / peak,
+            "traffic": VSAMPLE_DRAM_BYTES_BY_KIND[name] if ncall == NCALL else None}
+    all_ms = sum(e0.elapsed_time(e1) for (_, _, e0, e1) in kern_ev)
+    ops = sum(algorithmic_ops_per_sample(fid, D, a_, True) * samples for (fid, a_, _, _) in kern_ev)
+    avg_kms = all_ms / len(kern_ev)
+    achieved = ops / (all_ms * 1e-3) / 1e12
+    ops_per_launch = ops / len(kern_ev)
 
     if args.headline_only:
         if rank == 0:
             print(json.dumps({"metric": "m-Cubes samples/s", "value": value, "unit": "samples/s",
                               "ms_per_step": ms_step, "ncall": ncall, "avg_launch_ms": avg_kms,
-                              "gpu_launches": n_launch, "clocks": clk}), flush=True)
+                              "by_kind": kinds, "gpu_launches": n_launch, "clocks": clk}), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
 
     # ---- plain FP64 arm (same steps)
-    f64_steps = max(3, args.steps // 4)
-    total64, _ = timed(capi.FP64, f64_steps, 3)
-    value64 = samples * len(fams) * f64_steps * world / (total64 * 1e-3)
+    f64_steps = 3
+    total64, _, res64 = timed(capi.FP64, f64_steps, 3)
+    value64 = samples * n_fam * ITMAX * f64_steps * world / (total64 * 1e-3)
 
-    # ---- end to end through the host-buffer C call (H2D of the grid, D2H of grid, C, estimate)
-    host_grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}
+    # ---- end to end through the public host call (mcubes_integrate_ex: parameters in, per-iteration
+    # results and the combined estimate out; the call uploads the previous-estimate slot and reads back
+    # every iteration's sums)
     for fid in fams:   # warm-up
-        capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=1, job=job, adjust=1,
-                          precision=capi.FP32_EVAL, grid_in=host_grids[fid])
+        capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 0, precision=capi.FP32_EVAL)
     barrier()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = 3
     t = time.perf_counter()
+    e2e_res = {}
     for k in range(e2e_steps):
         for fid in fams:
-            r = capi.vsample_once(fid, pars[fid], D, ncall, 0, iteration=2 + k, job=job, adjust=1,
-                                  precision=capi.FP32_EVAL, grid_in=host_grids[fid])
-            host_grids[fid] = r["grid"]
+            e2e_res[fid] = capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 1 + k, precision=capi.FP32_EVAL,
+                                          return_iters=True)
     e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
-    e2e_value = samples * len(fams) * e2e_steps * world / e2e_s
-    grid_bytes = D * (NB + 1) * 8
-    h2d = len(fams) * (grid_bytes + 2 * D * 8)
-    d2h = len(fams) * (grid_bytes + D * NB * 8 + 16)
+    e2e_value = samples * n_fam * ITMAX * e2e_steps * world / e2e_s
+    h2d = n_fam * 16                       # the previous-estimate slot
+    d2h = n_fam * 2 * (ITMAX + 1) * 8      # every iteration's (sum I_t, sum V_t)
 
     # ---- time to 1e-3 relative error (full mcubes_integrate runs, host buffers)
     tta = None
@@ -478,7 +518,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = host_threads()
-        grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}
+        grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}   # adapted
         starts = {fid: 0 for fid in fams}
         c1 = min(1 << 20, m)
         t0 = time.perf_counter()
@@ -500,16 +540,26 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "genz6-d8-n1e8-fp32eval", "d": D, "ncall": ncall, "g": g, "m": m, "p": p,
                        "families": [W.NAMES[f] for f in fams], "params": "a_i~U[5,15], u_i~U[0.2,0.8], seed 0",
-                       "step": "V-Sample (adjust) + Rebin for each family", "precision": "FP32-eval, FP64 sums/Rebin",
+                       "step": f"one whole m-Cubes integration of each family: {ITMAX} iterations, the first {ADJ} "
+                               "adjusting (V-Sample with bin contributions + Rebin), the rest frozen; sums to the "
+                               "host and the combination", "precision": "FP32-eval, FP64 sums/Rebin",
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-            "fp64": {"value": value64, "unit": "samples/s", "steps": f64_steps},
+            "estimates": {W.NAMES[f]: {"estimate": res32[f]["estimate"], "error": res32[f]["error"],
+                                       "chi2_dof": res32[f]["chi2_dof"]} for f in fams},
+            "fp64": {"value": value64, "unit": "samples/s", "steps": f64_steps,
+                     "estimates": {W.NAMES[f]: {"estimate": res64[f]["estimate"], "error": res64[f]["error"]}
+                                   for f in fams}},
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "call": "mcubes_vsample_once (host grid in, grid + C + estimate out)"},
+                    "call": f"mcubes_integrate_ex per family ({ITMAX} iterations, {ADJ} adjusting), host results"},
             "gpu_launches": n_launch,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "vsample_kernel<8, fid, FP32>",
-                         "ops_per_launch": ops, "avg_launch_ms": avg_kms,
+                         "frac": achieved / peak,
+                         "traffic": VSAMPLE_DRAM_BYTES if ncall == NCALL else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the 10 "
+                                           "launches of one full-size integration "
+                                           "(profiles/vsample_fp32_d8_genz6_n1e8_launches.md)",
+                         "kernel": "vsample_kernel<8, fid, FP32> (adjusting and frozen launches)",
+                         "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_kms, "by_kind": kinds,
                          "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})"},
             "cpu_baseline": cpu,
             "time_to_1e-3": tta,
