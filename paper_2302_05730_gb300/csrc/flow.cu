@@ -219,70 +219,8 @@ __global__ void coupling_bwd_kernel(const LayerDesc D, const float *__restrict__
         for (int j = 0; j < D.nB; ++j) {
             const float *raw = o + s * D.nout + j * (2 * K + 1);
             float *draw = dodraw + s * D.nout + j * (2 * K + 1);
-            float W[K], V[K + 1];
-            widths_values<K>(raw, W, V);
-            const float x = h_in[s * d + D.B[j]];
-            const float gy = gout[s * d + D.B[j]];
-            float X = 0.f, E = 0.f;
-            int b = 0;
-#pragma unroll
-            for (int k = 0; k < K - 1; ++k) {
-                E += W[k];
-                if (x >= E) {
-                    X = E;
-                    b = k + 1;
-                }
-            }
-            float Wb = W[0], Vb = V[0], Vb1 = V[1];
-#pragma unroll
-            for (int k = 1; k < K; ++k)
-                if (b == k) {
-                    Wb = W[k];
-                    Vb = V[k];
-                    Vb1 = V[k + 1];
-                }
-            const float delta = fminf(fmaxf(x - X, 0.f), Wb);
-            const float dV = Vb1 - Vb;
-            const float q = Vb + delta * dV / Wb;
-            const float iq = 1.0f / q;
-            // dL/dx
-            gin[s * d + D.B[j]] = gy * q + glq * dV / (Wb * q);
-            // dL/dW_k and dL/dV_k through y and log q
-            float GW[K], GV[K + 1];
-            const float dlq_dWlt = -dV / (Wb * q);                       // k < b (through delta)
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float gw = 0.f;
-                if (k < b) gw = gy * (0.5f * (V[k] + V[k + 1]) - q) + glq * dlq_dWlt;
-                if (k == b) gw = -gy * delta * delta * dV / (2.f * Wb * Wb) - glq * delta * dV / (Wb * Wb) * iq;
-                GW[k] = gw;
-            }
-#pragma unroll
-            for (int k = 0; k <= K; ++k) {
-                float gv = 0.f;
-                if (k < b) gv += gy * 0.5f * W[k];
-                if (k >= 1 && k <= b) gv += gy * 0.5f * W[k - 1];
-                if (k == b) gv += gy * (delta - delta * delta / (2.f * Wb)) + glq * (1.f - delta / Wb) * iq;
-                if (k == b + 1) gv += gy * delta * delta / (2.f * Wb) + glq * (delta / Wb) * iq;
-                GV[k] = gv;
-            }
-            // through the normalisation of V: V_k = e_k / Z
-            float S = 0.f;
-#pragma unroll
-            for (int k = 0; k <= K; ++k) S += GV[k] * V[k];
-#pragma unroll
-            for (int k = 0; k < K; ++k) GW[k] -= 0.5f * (V[k] + V[k + 1]) * S;
-#pragma unroll
-            for (int k = 0; k <= K; ++k) {
-                const float c = 0.5f * ((k >= 1 ? W[k - 1] : 0.f) + (k < K ? W[k] : 0.f));
-                draw[K + k] = V[k] * (GV[k] - c * S);
-            }
-            // through the softmax of the widths
-            float SW = 0.f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) SW += GW[k] * W[k];
-#pragma unroll
-            for (int k = 0; k < K; ++k) draw[k] = W[k] * (GW[k] - SW);
+            gin[s * d + D.B[j]] = pq_backward<K>(raw, h_in[s * d + D.B[j]], gout[s * d + D.B[j]], glq,
+                                                 [draw](int k, float v) { draw[k] = v; });
         }
     }
 }
@@ -661,7 +599,31 @@ inline int launch_coupling_bwd(const Shape &S, const LayerDesc &D, const float *
 struct Work {
     float *hs, *o, *dO, *gA, *gB, *logq, *gl;
     __nv_bfloat16 *r1, *r2, *dz1, *dz2;
+    float *part;               // fused training: per-block partial gradients
+    long long part_stride;
+    int part_rows;
+    unsigned char *mirror;     // fused kernels: the bf16 weight mirror
 };
+
+// Fused training scratch for n samples: the mirror and the partial-gradient rows (one per
+// backward block, at most kFusedPartRowsMax, each as long as the largest layer).
+inline void fused_extent(const Shape &S, long long n, size_t &mirror_bytes, long long &stride, int &rows)
+{
+    FusedFlow F;
+    mirror_bytes = 0;
+    stride = 0;
+    rows = 0;
+    if (!fused_layout(S, F)) return;
+    mirror_bytes = F.total_bytes;
+    long long pos = 0, big = 0;
+    for (int l = 0; l < S.L; ++l) {
+        const long long p0 = pos;
+        describe(S, l, pos);
+        big = std::max(big, pos - p0);
+    }
+    stride = (big + 63) / 64 * 64;
+    rows = (int)std::min<long long>((n + kFusedBwdRows - 1) / kFusedBwdRows, kFusedPartRowsMax);
+}
 
 inline size_t work_bytes(const Shape &S, long long n, int &nout_max)
 {
@@ -669,9 +631,13 @@ inline size_t work_bytes(const Shape &S, long long n, int &nout_max)
     long long pos = 0;
     for (int l = 0; l < S.L; ++l) nout_max = std::max(nout_max, describe(S, l, pos).nout);
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t mb;
+    long long stride;
+    int rows;
+    fused_extent(S, n, mb, stride, rows);
     return al(sizeof(float) * (size_t)(S.L + 1) * n * S.d) + 2 * al(sizeof(float) * (size_t)n * nout_max) +
            4 * al(sizeof(__nv_bfloat16) * (size_t)n * S.H) + 2 * al(sizeof(float) * (size_t)n * S.d) +
-           2 * al(sizeof(float) * (size_t)n);
+           2 * al(sizeof(float) * (size_t)n) + al(mb) + al(sizeof(float) * (size_t)stride * rows);
 }
 
 inline Work carve(const Shape &S, long long n, void *base)
@@ -691,7 +657,11 @@ inline Work carve(const Shape &S, long long n, void *base)
     w.gA = (float *)q; q += al(sizeof(float) * (size_t)n * S.d);
     w.gB = (float *)q; q += al(sizeof(float) * (size_t)n * S.d);
     w.logq = (float *)q; q += al(sizeof(float) * (size_t)n);
-    w.gl = (float *)q;
+    w.gl = (float *)q; q += al(sizeof(float) * (size_t)n);
+    size_t mb;
+    fused_extent(S, n, mb, w.part_stride, w.part_rows);
+    w.mirror = (unsigned char *)q; q += al(mb);
+    w.part = (float *)q;
     return w;
 }
 
@@ -840,6 +810,13 @@ int mcubes_flow_grad_dev(const mcubes_flow_shape *shape, const float *d_params, 
     int nm;
     if (!d_work || work_bytes < flow::work_bytes(S, n, nm) || ((uintptr_t)d_work & 255u)) return MCUBES_ERR_WORKSPACE;
     flow::Work w = flow::carve(S, n, d_work);
+    flow::FusedFlow F;
+    if (w.part_rows > 0 && flow::fused_layout(S, F)) {
+        const flow::FusedTrainWork W{w.hs, w.gA, w.gB, w.gl, w.part, w.part_stride, w.part_rows, w.mirror};
+        const int st = flow::fused_grad(F, d_params, n, S.d, d_x, d_w, loss_kind, d_grad, d_loss, W,
+                                        (cudaStream_t)stream);
+        if (st != flow::kFusedUnsupported) return st;
+    }
     const int sms = flow::sms_of_device();
     if (sms <= 0) return cuda_status(cudaErrorNoDevice);
     return cuda_status((cudaError_t)flow::run_grad(S, d_params, n, d_x, d_w, loss_kind, d_grad, d_loss, w, sms,

@@ -9,6 +9,7 @@
 // The VEGAS grid stays: it seeds the training data, and its frozen-grid iterations at the same
 // sample budget are the reference for each flow estimate's variance.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -20,6 +21,11 @@
 #include "internal.h"
 
 using namespace mcubes;
+using flow::FusedFlow;
+using flow::FusedLayer;
+using flow::kFThreads;
+using flow::kFWarps;
+using flow::kFusedUnsupported;
 
 namespace {
 
@@ -220,76 +226,9 @@ __global__ void flow_eval_kernel(const SampleSpec S, const IntegrandParams ip, d
 // operand layout of the next. The output of the last GEMM goes to a per-warp shared buffer, two
 // axes at a time, and each lane then transforms one (sample, axis) pair with the same
 // pq_transform as the per-layer kernels.
-constexpr int kFWarps = 8, kFThreads = kFWarps * 32, kFSub = 4, kFRows = kFWarps * 16 * kFSub;
-constexpr int kFMaxLayers = 16;
-constexpr int kFusedUnsupported = -1;   // internal: the shape does not fit the fused kernel
-
-struct FusedLayer {
-    int nA, nB;
-    int A[flow::kMaxAB], B[flow::kMaxAB];
-    uint32_t off, bytes;                 // the layer's block in the mirror (bytes, multiples of 16)
-    uint32_t oW2, oW3, ob1, ob2, ob3;    // byte offsets inside the block (W1 at 0)
-    uint32_t pW1, pb1, pW2, pb2, pW3, pb3;   // offsets of the FP32 master parameters (floats)
-};
-
-struct FusedFlow {
-    int L, H, K, SW;                     // SW: output slot width 2K+1 rounded up to 8
-    uint32_t max_bytes, total_bytes;
-    FusedLayer lay[kFMaxLayers];
-};
-
-inline uint32_t al16(uint32_t b) { return (b + 15u) & ~15u; }
-
-// Host: the mirror layout of a flow shape. Returns false when the shape needs more layers than
-// the fused path takes.
-bool fused_layout(const flow::Shape &S, FusedFlow &F)
-{
-    if (S.L > kFMaxLayers) return false;
-    std::memset(&F, 0, sizeof(F));
-    F.L = S.L;
-    F.H = S.H;
-    F.K = S.K;
-    F.SW = (2 * S.K + 1 + 7) & ~7;
-    const uint32_t LD0 = flow::kK0 + 8, LDH = (uint32_t)S.H + 8;
-    long long pos = 0;
-    uint32_t off = 0;
-    for (int l = 0; l < S.L; ++l) {
-        const flow::LayerDesc D = flow::describe(S, l, pos);
-        FusedLayer &Y = F.lay[l];
-        Y.nA = D.nA;
-        Y.nB = D.nB;
-        for (int i = 0; i < flow::kMaxAB; ++i) {
-            Y.A[i] = D.A[i];
-            Y.B[i] = D.B[i];
-        }
-        Y.pW1 = (uint32_t)D.offW1;
-        Y.pb1 = (uint32_t)D.offb1;
-        Y.pW2 = (uint32_t)D.offW2;
-        Y.pb2 = (uint32_t)D.offb2;
-        Y.pW3 = (uint32_t)D.offW3;
-        Y.pb3 = (uint32_t)D.offb3;
-        uint32_t b = al16(2u * S.H * LD0);
-        Y.oW2 = b;
-        b = al16(b + 2u * S.H * LDH);
-        Y.oW3 = b;
-        b = al16(b + 2u * (uint32_t)(D.nB * F.SW) * LDH);
-        Y.ob1 = b;
-        b = al16(b + 4u * S.H);
-        Y.ob2 = b;
-        b = al16(b + 4u * S.H);
-        Y.ob3 = b;
-        b = al16(b + 4u * (uint32_t)(D.nB * F.SW));
-        Y.bytes = b;
-        Y.off = off;
-        off += b;
-        F.max_bytes = std::max(F.max_bytes, b);
-    }
-    F.total_bytes = off;
-    return true;
-}
-
-// The bf16 mirror of the FP32 parameters in the fused kernel's shared layout: W1 [H][kK0 + 8],
-// W2 [H][H + 8], W3 [|B| SW][H + 8] (slot j at rows j SW .. j SW + 2K), zero padding; biases FP32.
+// The bf16 mirror of the FP32 parameters in the fused kernels' shared layout: W1 [H][kK0 + 8],
+// W2 [H][H + 8], W3 [round16(|B| SW)][H + 8] (slot j at rows j SW .. j SW + 2K), zero padding;
+// biases FP32.
 // blockIdx.y is the layer.
 __global__ void mirror_kernel(const FusedFlow F, const float *__restrict__ p, unsigned char *__restrict__ mirror)
 {
@@ -302,7 +241,7 @@ __global__ void mirror_kernel(const FusedFlow F, const float *__restrict__ p, un
     float *b1 = reinterpret_cast<float *>(base + Y.ob1);
     float *b2 = reinterpret_cast<float *>(base + Y.ob2);
     float *b3 = reinterpret_cast<float *>(base + Y.ob3);
-    const int n1 = H * LD0, n2 = H * LDH, n3 = Y.nB * F.SW * LDH;
+    const int n1 = H * LD0, n2 = H * LDH, n3 = flow::round16(Y.nB * F.SW) * LDH;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 + n2 + n3 + 2 * H + Y.nB * F.SW;
          e += gridDim.x * blockDim.x) {
         if (e < n1) {
@@ -313,7 +252,7 @@ __global__ void mirror_kernel(const FusedFlow F, const float *__restrict__ p, un
             W2[f] = __float2bfloat16_rn(c < H ? p[Y.pW2 + r * H + c] : 0.f);
         } else if (e < n1 + n2 + n3) {
             const int f = e - n1 - n2, r = f / LDH, c = f - r * LDH, j = r / F.SW, k = r - j * F.SW;
-            W3[f] = __float2bfloat16_rn((c < H && k < no) ? p[Y.pW3 + (j * no + k) * H + c] : 0.f);
+            W3[f] = __float2bfloat16_rn((c < H && k < no && j < Y.nB) ? p[Y.pW3 + (j * no + k) * H + c] : 0.f);
         } else if (e < n1 + n2 + n3 + H) {
             b1[e - n1 - n2 - n3] = p[Y.pb1 + e - n1 - n2 - n3];
         } else if (e < n1 + n2 + n3 + 2 * H) {
@@ -331,6 +270,8 @@ constexpr int fused_min_blocks()
     return H <= 64 ? 2 : 1;
 }
 
+constexpr int kFSub = 4, kFRows = kFWarps * 16 * kFSub;   // 512 samples per block tile
+
 template <int H, int K>
 size_t fused_smem(const FusedFlow &F, int d)
 {
@@ -347,15 +288,14 @@ __global__ void __launch_bounds__(kFThreads, fused_min_blocks<H, K>())
                        const IntegrandParams ip, long long i0, long long n, float *__restrict__ x_out,
                        float *__restrict__ lq_out, float *__restrict__ w_out)
 {
-    constexpr int SW = (2 * K + 1 + 7) & ~7, NT3 = SW / 8, OS = SW + 1, LD0 = flow::kK0 + 8, LDH = H + 8;
+    constexpr int SW = (2 * K + 1 + 7) & ~7, OS = SW + 1;
     extern __shared__ __align__(16) unsigned char smem[];
     const int d = S.d, HS = d | 1;
     unsigned char *wbuf = smem;
     float *hs = reinterpret_cast<float *>(smem + F.max_bytes);
     float *lqs = hs + kFRows * HS;
     float *obuf = lqs + kFRows;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int row = lane & 15, half = lane >> 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, row = lane & 15, half = lane >> 4;
     float *ob = obuf + warp * 2 * 16 * OS;
     const float ig = 1.0f / (float)S.g;
     const long long ntiles = (n + kFRows - 1) / kFRows;
@@ -387,102 +327,9 @@ __global__ void __launch_bounds__(kFThreads, fused_min_blocks<H, K>())
                 for (uint32_t e = threadIdx.x; e < Y.bytes / 16u; e += kFThreads) dst[e] = src[e];
             }
             __syncthreads();
-            const __nv_bfloat16 *W1 = reinterpret_cast<const __nv_bfloat16 *>(wbuf);
-            const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(wbuf + Y.oW2);
-            const __nv_bfloat16 *W3 = reinterpret_cast<const __nv_bfloat16 *>(wbuf + Y.oW3);
-            const float *b1 = reinterpret_cast<const float *>(wbuf + Y.ob1);
-            const float *b2 = reinterpret_cast<const float *>(wbuf + Y.ob2);
-            const float *b3 = reinterpret_cast<const float *>(wbuf + Y.ob3);
-            const int cA0 = 2 * t, cA1 = 2 * t + 1;
-            const int xA0 = cA0 < Y.nA ? Y.A[cA0] : -1, xA1 = cA1 < Y.nA ? Y.A[cA1] : -1;
             for (int sub = 0; sub < kFSub; ++sub) {
                 const int R0 = (warp * kFSub + sub) * 16;
-                // GEMM 1 operand: the A axes of rows R0 + g and R0 + g + 8, columns >= |A| zero
-                uint32_t a1[4];
-                {
-                    const float *hA = hs + (R0 + g) * HS, *hB = hs + (R0 + g + 8) * HS;
-                    a1[0] = flow::pack_bf16(xA0 >= 0 ? hA[xA0] : 0.f, xA1 >= 0 ? hA[xA1] : 0.f);
-                    a1[1] = flow::pack_bf16(xA0 >= 0 ? hB[xA0] : 0.f, xA1 >= 0 ? hB[xA1] : 0.f);
-                    a1[2] = 0u;
-                    a1[3] = 0u;
-                }
-                uint32_t a2[H / 16][4];
-                {
-                    float acc[H / 8][4] = {};
-#pragma unroll
-                    for (int nt = 0; nt < H / 8; ++nt) {
-                        const __nv_bfloat16 *bp = W1 + (nt * 8 + g) * LD0 + 2 * t;
-                        flow::mma16816(acc[nt], a1, flow::ld32(bp), flow::ld32(bp + 8));
-                    }
-#pragma unroll
-                    for (int kt = 0; kt < H / 16; ++kt) {
-                        const int c = 16 * kt + 2 * t;
-                        a2[kt][0] = flow::pack_bf16(fmaxf(acc[2 * kt][0] + b1[c], 0.f), fmaxf(acc[2 * kt][1] + b1[c + 1], 0.f));
-                        a2[kt][1] = flow::pack_bf16(fmaxf(acc[2 * kt][2] + b1[c], 0.f), fmaxf(acc[2 * kt][3] + b1[c + 1], 0.f));
-                        a2[kt][2] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][0] + b1[c + 8], 0.f),
-                                                    fmaxf(acc[2 * kt + 1][1] + b1[c + 9], 0.f));
-                        a2[kt][3] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][2] + b1[c + 8], 0.f),
-                                                    fmaxf(acc[2 * kt + 1][3] + b1[c + 9], 0.f));
-                    }
-                }
-                uint32_t a3[H / 16][4];
-                {
-                    float acc[H / 8][4] = {};
-#pragma unroll
-                    for (int kt = 0; kt < H / 16; ++kt)
-#pragma unroll
-                        for (int nt = 0; nt < H / 8; ++nt) {
-                            const __nv_bfloat16 *bp = W2 + (nt * 8 + g) * LDH + kt * 16 + 2 * t;
-                            flow::mma16816(acc[nt], a2[kt], flow::ld32(bp), flow::ld32(bp + 8));
-                        }
-#pragma unroll
-                    for (int kt = 0; kt < H / 16; ++kt) {
-                        const int c = 16 * kt + 2 * t;
-                        a3[kt][0] = flow::pack_bf16(fmaxf(acc[2 * kt][0] + b2[c], 0.f), fmaxf(acc[2 * kt][1] + b2[c + 1], 0.f));
-                        a3[kt][1] = flow::pack_bf16(fmaxf(acc[2 * kt][2] + b2[c], 0.f), fmaxf(acc[2 * kt][3] + b2[c + 1], 0.f));
-                        a3[kt][2] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][0] + b2[c + 8], 0.f),
-                                                    fmaxf(acc[2 * kt + 1][1] + b2[c + 9], 0.f));
-                        a3[kt][3] = flow::pack_bf16(fmaxf(acc[2 * kt + 1][2] + b2[c + 8], 0.f),
-                                                    fmaxf(acc[2 * kt + 1][3] + b2[c + 9], 0.f));
-                    }
-                }
-                float lq = 0.f;
-                for (int jp = 0; jp < Y.nB; jp += 2) {
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const int j = jp + hh;
-                        if (j < Y.nB) {   // warp-uniform
-                            float acc[NT3][4] = {};
-#pragma unroll
-                            for (int kt = 0; kt < H / 16; ++kt)
-#pragma unroll
-                                for (int nt = 0; nt < NT3; ++nt) {
-                                    const __nv_bfloat16 *bp = W3 + (j * SW + nt * 8 + g) * LDH + kt * 16 + 2 * t;
-                                    flow::mma16816(acc[nt], a3[kt], flow::ld32(bp), flow::ld32(bp + 8));
-                                }
-                            float *o = ob + hh * 16 * OS;
-#pragma unroll
-                            for (int nt = 0; nt < NT3; ++nt) {
-                                const int c = nt * 8 + 2 * t;
-                                o[g * OS + c] = acc[nt][0] + b3[j * SW + c];
-                                o[g * OS + c + 1] = acc[nt][1] + b3[j * SW + c + 1];
-                                o[(g + 8) * OS + c] = acc[nt][2] + b3[j * SW + c];
-                                o[(g + 8) * OS + c + 1] = acc[nt][3] + b3[j * SW + c + 1];
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    const int j = jp + half;
-                    if (j < Y.nB) {
-                        float *hv = hs + (R0 + row) * HS + Y.B[j];
-                        float out, q;
-                        flow::pq_transform<K>(ob + half * 16 * OS + row * OS, *hv, 1, out, q);
-                        *hv = out;
-                        lq += __logf(q);
-                    }
-                    __syncwarp();
-                }
-                lq += __shfl_xor_sync(0xffffffffu, lq, 16);
+                const float lq = flow::layer_rows16<H, K>(Y, wbuf, hs, HS, R0, ob, 1);
                 if (half == 0) lqs[R0 + row] += lq;
             }
         }
@@ -560,17 +407,31 @@ int launch_fused_hk(const FusedFlow &F, const unsigned char *mirror, const Sampl
                     long long i0, long long n, float *x, float *lq, float *w, cudaStream_t s)
 {
     const size_t smem = fused_smem<H, K>(F, S.d);
+    // per device: the opt-in limit raised once to the device maximum, the limits read once
+    static int optin_c[64], sms_c[64];
+    static std::atomic<uint64_t> known{0};
     int dev = 0, optin = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 64 && (known.load(std::memory_order_acquire) >> dev & 1u)) {
+        optin = optin_c[dev];
+        sms = sms_c[dev];
+    } else {
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(flow_sample_kernel<H, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (dev < 64) {
+            optin_c[dev] = optin;
+            sms_c[dev] = sms;
+            known.fetch_or(1ull << dev, std::memory_order_release);
+        }
+    }
     if (smem > (size_t)optin) return kFusedUnsupported;
-    e = cudaFuncSetAttribute(flow_sample_kernel<H, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flow_sample_kernel<H, K>, kFThreads, smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (per_sm < 1) return kFusedUnsupported;
+    // resident blocks per SM: shared memory (228 KB an SM, 1 KB reserved a block), then the
+    // launch bound
+    per_sm = std::max(1, std::min(fused_min_blocks<H, K>(), (int)(233472 / (smem + 1024))));
     const long long tiles = (n + kFRows - 1) / kFRows;
     const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
     flow_sample_kernel<H, K><<<(unsigned)grid, kFThreads, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w);
@@ -600,12 +461,6 @@ int launch_fused(const FusedFlow &F, const unsigned char *mirror, const SampleSp
     case 128: return launch_fused_h<128>(F, mirror, S, ip, i0, n, x, lq, w, s);
     default: return MCUBES_ERR_INVALID_ARG;
     }
-}
-
-int build_mirror(const FusedFlow &F, const float *d_params, unsigned char *mirror, cudaStream_t s)
-{
-    mirror_kernel<<<dim3(64, (unsigned)F.L), 256, 0, s>>>(F, d_params, mirror);
-    return cuda_status(cudaGetLastError());
 }
 
 // Weights for training: variance loss w^2, KL |w|, normalised so a batch of `batch` sums to 1
@@ -666,11 +521,23 @@ double seconds_since(std::chrono::steady_clock::time_point t0)
 
 }  // namespace
 
+namespace mcubes {
+namespace flow {
+
+int build_mirror(const FusedFlow &F, const float *d_params, unsigned char *mirror, cudaStream_t s)
+{
+    mirror_kernel<<<dim3(64, (unsigned)F.L), 256, 0, s>>>(F, d_params, mirror);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace flow
+}  // namespace mcubes
+
 extern "C" size_t mcubes_flow_sample_work_bytes(const mcubes_flow_shape *shape)
 {
     if (!shape || mcubes_flow_param_count(shape) <= 0) return 0;
     FusedFlow F;
-    if (!fused_layout(flow::Shape{shape->d, shape->layers, shape->hidden, shape->bins}, F)) return 0;
+    if (!flow::fused_layout(flow::Shape{shape->d, shape->layers, shape->hidden, shape->bins}, F)) return 0;
     return F.total_bytes;
 }
 
@@ -684,7 +551,7 @@ extern "C" int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const floa
     if (mcubes_flow_param_count(shape) <= 0) return MCUBES_ERR_INVALID_ARG;
     const flow::Shape S{shape->d, shape->layers, shape->hidden, shape->bins};
     FusedFlow F;
-    if (!fused_layout(S, F)) return MCUBES_ERR_INVALID_ARG;
+    if (!flow::fused_layout(S, F)) return MCUBES_ERR_INVALID_ARG;
     if (!d_work || work_bytes < F.total_bytes || ((uintptr_t)d_work & 255u)) return MCUBES_ERR_WORKSPACE;
     Problem pb;
     int st = prepare(integrand_id, params, S.d, ncall, seed, 0, 0, 0, MCUBES_FP32_EVAL, pb);
@@ -695,7 +562,7 @@ extern "C" int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const floa
                         (uint32_t)iteration << 16, job, S.d, integrand_id};
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *mirror = (unsigned char *)d_work;
-    if ((st = build_mirror(F, d_params, mirror, s))) return st;
+    if ((st = flow::build_mirror(F, d_params, mirror, s))) return st;
     st = launch_fused(F, mirror, SS, pb.P.ip, i0, n, d_x, d_logq, d_w, s);
     return st == kFusedUnsupported ? MCUBES_ERR_INVALID_ARG : st;
 }
@@ -742,7 +609,7 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     const long long nchunk = chunk_cubes * p;
     const long long nwork = std::max<long long>(cfg->batch, nchunk);
     FusedFlow FF;
-    const bool fused_ok = fused_layout(flow::Shape{sh.d, sh.layers, sh.hidden, sh.bins}, FF);
+    const bool fused_ok = flow::fused_layout(flow::Shape{sh.d, sh.layers, sh.hidden, sh.bins}, FF);
     const size_t wbytes = mcubes_flow_work_bytes(&sh, nwork);
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t bytes = al(sizeof(double) * d * kGS) + 2 * al(sizeof(float) * ntr * d) + 3 * al(sizeof(float) * ntr) +
@@ -850,7 +717,7 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     t0 = std::chrono::steady_clock::now();
     if ((st = cuda_status(cudaMemsetAsync(d_sums, 0, sizeof(double) * 2 * cfg->flow_iters, s)))) return finish(st);
     bool fused = fused_ok;
-    if (fused && (st = build_mirror(FF, d_par, d_mirror, s))) return finish(st);
+    if (fused && (st = flow::build_mirror(FF, d_par, d_mirror, s))) return finish(st);
     for (int it = 0; it < cfg->flow_iters; ++it) {
         SampleSpec F{(uint32_t)m, (uint32_t)p, (uint32_t)g, (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32),
                      (uint32_t)(itmax + 2 + it) << 16, 0x20000000u, d, integrand_id};

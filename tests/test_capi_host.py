@@ -156,12 +156,14 @@ def test_integrate_range_argument_checks(capi):
 
 def test_flow_sample_work_bytes_and_argument_checks(capi):
     """The fused sampler's scratch is the bf16 weight mirror: per layer W1 [H][24], W2 [H][H+8],
-    W3 [|B| SW][H+8] (bf16) and the biases (FP32), each 16-byte aligned; SW = 2K+1 rounded up to 8.
+    W3 [|B| SW rounded up to 16][H+8] (bf16) and the biases (FP32), each 16-byte aligned; SW = 2K+1
+    rounded up to 8.
     Argument and workspace checks answer before any CUDA call."""
     def layer_bytes(H, nB, K):
         al = lambda b: (b + 15) // 16 * 16
         SW = (2 * K + 1 + 7) // 8 * 8
-        return al(2 * H * 24) + al(2 * H * (H + 8)) + al(2 * nB * SW * (H + 8)) + 2 * al(4 * H) + al(4 * nB * SW)
+        r16 = lambda v: (v + 15) // 16 * 16
+        return al(2 * H * 24) + al(2 * H * (H + 8)) + al(2 * r16(nB * SW) * (H + 8)) + 2 * al(4 * H) + al(4 * nB * SW)
     assert capi.flow_sample_work_bytes(capi.flow_shape(8, 4, 64, 16)) == 4 * layer_bytes(64, 4, 16)
     # d = 7: |B| = 4, 3, 3, 4 (upper half, lower half, odd axes, even axes)
     n7 = capi.flow_sample_work_bytes(capi.flow_shape(7, 4, 32, 8))

@@ -162,11 +162,13 @@ def test_fused_flow_sampling_matches_oracle(capi, d, L, H, K, fid, ncall, i0, n)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("d,L,H,K,sub,scale", [(4, 2, 32, 4, None, 0.2), (8, 4, 64, 16, 400, 0.1)])
+@pytest.mark.parametrize("d,L,H,K,sub,scale", [(4, 2, 32, 4, None, 0.2), (8, 4, 64, 16, 400, 0.1),
+                                                (7, 3, 32, 8, 300, 0.15), (8, 2, 128, 16, 300, 0.1)])
 def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, scale, kind):
     """Weight scale 0.1 at d = 8 is the regime training works in (it starts at the identity);
     with much larger random weights bf16 noise compounds through four layers of backprop and
-    the comparison measures that noise rather than the kernels."""
+    the comparison measures that noise rather than the kernels. Widths up to 64 run the fused
+    training kernels; width 128 does not fit their shared memory and runs the per-layer chain."""
     n = 300
     p = _params(d, L, H, K, seed=7 + d, scale=scale)
     rng = np.random.default_rng(2)
@@ -195,6 +197,39 @@ def test_flow_gradient_matches_finite_differences(capi, d, L, H, K, sub, scale, 
     cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
     rel = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     assert cos > 0.998 and rel < 0.05, (cos, rel)
+
+
+def test_fused_gradient_is_additive_over_samples(capi):
+    """The loss is a weighted sum over samples, so the gradient of a batch is the sum of its
+    halves' gradients. At 40,000 samples the backward blocks each take several 128-sample tiles
+    and accumulate them; the halves (20,000 each) take one tile per block."""
+    d, L, H, K = 8, 4, 64, 16
+    n = 40000
+    shape = capi.flow_shape(d, L, H, K)
+    p = _params(d, L, H, K, seed=11, scale=0.1)
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0.0, 1.0, (n, d)).astype(np.float32)
+    w = rng.exponential(1.0, n).astype(np.float32)
+    w /= w.sum()
+    dp = torch.from_numpy(p).cuda()
+    out = {}
+    for kind in (0, 1):
+        grads = []
+        for lo, hi in ((0, n), (0, n // 2), (n // 2, n)):
+            ws, nb, keep = _work(capi, shape, hi - lo)
+            dx = torch.from_numpy(x[lo:hi].copy()).cuda()
+            dw = torch.from_numpy(w[lo:hi].copy()).cuda()
+            gr = torch.zeros(p.size, dtype=torch.float32, device="cuda")
+            ls = torch.zeros(1, dtype=torch.float32, device="cuda")
+            capi.flow_grad_dev(shape, dp, hi - lo, dx, dw, kind, gr, ls, ws, nb)
+            torch.cuda.synchronize()
+            grads.append((gr.cpu().numpy().astype(np.float64), float(ls.item())))
+        (g_all, l_all), (g1, l1), (g2, l2) = grads
+        rel = np.linalg.norm(g_all - (g1 + g2)) / np.linalg.norm(g_all)
+        assert rel < 1e-4, (kind, rel)
+        assert abs(l_all - (l1 + l2)) <= 1e-4 * abs(l_all), (kind, l_all, l1 + l2)
+        out[kind] = g_all
+    assert np.all(np.isfinite(out[0])) and np.all(np.isfinite(out[1]))
 
 
 def test_adam_step(capi):
