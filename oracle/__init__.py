@@ -2,7 +2,8 @@
 
 A plain FP64 C restatement of one m-Cubes iteration (paper Sec. 3.2, Algorithm 2), the VEGAS
 grid refinement it relies on (Lepage 1978), the benchmark integrands (Sec. 5, Eq. 1-6 and the
-addition integrand) and Philox4x32-10 (Salmon et al., SC'11), wrapped with ctypes.
+addition integrand), Philox4x32-10 (Salmon et al., SC'11), and the PAGANI region evaluation
+(Sec. 3.1) with the Genz-Malik degree-7/5 rule and a simple adaptive driver, wrapped with ctypes.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
 legs of ``bench.py`` may import this package. The CUDA library never loads it and shares
@@ -25,6 +26,7 @@ DOUBLE_GAUSSIAN, ROTATED_GAUSSIAN = 8, 9
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mcubes_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "pagani_oracle.c")]
 _LIB = os.path.join(_HERE, "libmcubes_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,10 +34,10 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+               "-shared", "-Wall", "-o", tmp] + _SRCS + ["-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -62,6 +64,15 @@ def lib():
             L.orc_adapted_grid.argtypes = [i32, i32, dp, i64, i32, u64, u32, i32, dp]
             L.orc_sample_points.argtypes = [i32, i32, dp, i64, u64, i32, u32, i32, dp, i64, i64,
                                             dp, dp, ctypes.POINTER(ctypes.c_int32), dp, dp]
+            L.orc_gm_count.argtypes = [i32]
+            L.orc_gm_count.restype = i32
+            L.orc_gm_weights.argtypes = [i32, dp, dp]
+            L.orc_gm_points.argtypes = [i32, dp, ctypes.POINTER(ctypes.c_int32)]
+            L.orc_gm_points.restype = i32
+            L.orc_pagani_evaluate.argtypes = [i32, i32, dp, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_int32), dp]
+            L.orc_pagani_evaluate.restype = i32
+            L.orc_pagani_integrate.argtypes = [i32, i32, dp, ctypes.c_double, i32, i64, i32, dp]
+            L.orc_pagani_integrate.restype = i32
             _lib = L
     return _lib
 
@@ -184,3 +195,46 @@ def adapted_grid(fid, d, params, n, iters, seed, job=0, mode=0) -> np.ndarray:
     B = np.empty((d, ND + 1))
     _check(lib().orc_adapted_grid(fid, d, _dp(par), n, iters, seed, job, mode, _dp(B)), "adapted_grid")
     return B
+
+
+# ------------------------------------------------------------------------------ PAGANI
+def gm_rule(d: int):
+    """The Genz-Malik degree-7/5 rule on [-1, 1]^d: points (n x d), class of each point (1..5),
+    weights per class for degree 7 and degree 5."""
+    L = lib()
+    n = L.orc_gm_count(d)
+    if n <= 0:
+        raise ValueError(f"unsupported d = {d}")
+    U = np.empty((n, d))
+    cls = np.empty(n, dtype=np.int32)
+    _check(L.orc_gm_points(d, _dp(U), cls.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "gm_points")
+    w7 = np.empty(5)
+    w5 = np.empty(5)
+    L.orc_gm_weights(d, _dp(w7), _dp(w5))
+    return U, cls, w7, w5
+
+
+def pagani_evaluate(fid, d, params, lo, length, want_fourth=False):
+    """One region: (I, E, split axis[, fourth differences])."""
+    par = _f64(params)
+    lo = _f64(lo)
+    length = _f64(length)
+    I = ctypes.c_double()
+    E = ctypes.c_double()
+    ax = ctypes.c_int32()
+    fourth = np.empty(d) if want_fourth else None
+    _check(lib().orc_pagani_evaluate(fid, d, _dp(par), _dp(lo), _dp(length), ctypes.byref(I), ctypes.byref(E),
+                                     ctypes.byref(ax), _dp(fourth)), "pagani_evaluate")
+    if want_fourth:
+        return I.value, E.value, ax.value, fourth
+    return I.value, E.value, ax.value
+
+
+def pagani_integrate(fid, d, params, rel_tol, max_iters=40, max_regions=1 << 20, init_split=2):
+    """Adaptive run; dict(estimate, error, evaluated, iterations, status, active)."""
+    par = _f64(params)
+    out = np.zeros(6)
+    _check(lib().orc_pagani_integrate(fid, d, _dp(par), float(rel_tol), int(max_iters), int(max_regions),
+                                      int(init_split), _dp(out)), "pagani_integrate")
+    return dict(estimate=out[0], error=out[1], evaluated=int(out[2]), iterations=int(out[3]), status=int(out[4]),
+                active=int(out[5]))
