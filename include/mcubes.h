@@ -293,6 +293,48 @@ int mcubes_integrate_batch(int n_jobs, const mcubes_job *jobs, int itmax, int it
 int mcubes_tune_batch(int n_jobs, const mcubes_job *jobs, int precision, mcubes_batch_tuning *out);
 
 /* ---------------------------------------------------------------------------------------
+ * PAGANI, the paper's other workload (Sec. 3.1): the region-evaluation kernel (the PAGANI-kernel
+ * algorithm) and an adaptive driver around it. FP64 throughout.
+ *   Rule (the paper defers it to PAGANI; the reading here): the Genz-Malik fully symmetric rule
+ *   of degree 7 with its embedded rule of degree 5 on each region, f_eval = 1 + 4d + 2d(d-1) + 2^d
+ *   points; I = the degree-7 estimate, E = |I7 - I5|, and the split axis of the region = the
+ *   largest fourth divided difference along the axes (ties -- within 1e-12 of the larger
+ *   difference and of the largest |f| at the centre and axis points -- go to the longest side,
+ *   then the lowest axis).
+ *   Regions: row-major n x d arrays of low corners and side lengths.
+ * Supported: 2 <= d <= 16 (f_eval grows as 2^d).
+ * --------------------------------------------------------------------------------------- */
+typedef struct mcubes_pagani_result {
+    double estimate, error;
+    int64_t regions_evaluated;  /* over all iterations */
+    int32_t iterations;
+    int32_t status;             /* 0 converged, 1 iteration limit, 2 region limit */
+    int64_t active_regions;     /* regions evaluated in the last iteration */
+} mcubes_pagani_result;
+
+/* f_eval of the rule at dimension d, or 0 if unsupported. */
+int mcubes_pagani_rule_points(int d);
+
+/* The PAGANI kernel on n_regions device regions (d_lo, d_len: n x d FP64): d_I, d_E (FP64) and
+ * d_axis (int32) per region. params as mcubes_integrate. Asynchronous on stream (NULL: the legacy
+ * default stream). Errors: INVALID_ARG, UNSUPPORTED_DIM (d < 2 or d > 16), UNKNOWN_INTEGRAND, CUDA. */
+int mcubes_pagani_evaluate_dev(int integrand_id, const double *params, int d, int64_t n_regions,
+                               const double *d_lo, const double *d_len, double *d_I, double *d_E,
+                               int32_t *d_axis, void *stream);
+
+/* Adaptive integration over [0,1]^d (reading; the paper describes the kernel only). The cube starts
+ * as init_split^d equal regions. Each iteration evaluates every active region; with the running
+ * totals I = I_done + sum I_r and E = E_done + sum E_r it stops once E <= rel_tol |I|. Otherwise a
+ * region with E_r <= rel_tol |I| V_r is finished (joins I_done, E_done) and every other region is
+ * halved along its split axis (lower half first, children in the parents' order). The run also
+ * stops after max_iters iterations, when no region is left, or when the next set would exceed
+ * max_regions (at most 2^31 - 1). Synchronous; allocates and frees its own device memory
+ * (about 32 d max_regions bytes). Errors: as mcubes_pagani_evaluate_dev; INVALID_ARG for
+ * rel_tol <= 0, max_iters < 1, init_split < 1 or init_split^d > max_regions; NONFINITE. */
+int mcubes_pagani_integrate(int integrand_id, const double *params, int d, double rel_tol, int max_iters,
+                            int64_t max_regions, int init_split, mcubes_pagani_result *out);
+
+/* ---------------------------------------------------------------------------------------
  * Learned proposal (the target's extension; the paper's m-Cubes uses the VEGAS grid only): a
  * coupling flow on [0,1]^d (neural importance sampling: coupling layers whose transformed axes
  * go through piecewise-quadratic CDFs computed by a ReLU MLP). The MLPs run on the tensor

@@ -21,7 +21,9 @@
  * Integral estimate I7 = (V / 2^d) sum_k w7_k S_k, with S_k the sum of f over class k and V the
  * region's volume; error estimate E = |I7 - I5|; split axis: the largest fourth divided
  * difference |f(l2 e_i) + f(-l2 e_i) - 2 f(0) - (l2/l3)^2 (f(l3 e_i) + f(-l3 e_i) - 2 f(0))|,
- * with ties (within 1e-12 relative, or all zero) going to the longest side, then the lowest axis.
+ * with ties going to the longest side, then the lowest axis. Two differences tie when they are
+ * within 1e-12 of the larger of them and of the largest |f| at the centre and axis points (below
+ * that a fourth difference is rounding noise).
  *
  * Only the test-suite and the benchmark's CPU-baseline leg may load this file. It shares no
  * code with the CUDA library.
@@ -142,6 +144,10 @@ int orc_pagani_evaluate(int id, int d, const double *par, const double *lo, cons
     *E = fabs(i7 - i5);
     /* fourth differences: class-2 points of axis i at 1 + 2i (+), 2 + 2i (-); class 3 at 1 + 2d + 2i, ... */
     const double r = pg_lambda2(2) / pg_lambda2(3), f0 = fv[0];
+    /* rounding noise of a fourth difference is a few ulps of the largest |f| it combines: below
+     * 1e-12 of that, differences are ties */
+    double fscale = fabs(f0);
+    for (int p = 1; p < 1 + 4 * d; ++p) fscale = fmax(fscale, fabs(fv[p]));
     double best = -1.0;
     int bi = 0;
     for (int i = 0; i < d; ++i) {
@@ -149,7 +155,7 @@ int orc_pagani_evaluate(int id, int d, const double *par, const double *lo, cons
         const double a3 = fv[1 + 2 * d + 2 * i] + fv[2 + 2 * d + 2 * i] - 2.0 * f0;
         const double D = fabs(a2 - r * a3);
         if (fourth) fourth[i] = D;
-        const double tie = 1e-12 * fmax(D, best);
+        const double tie = 1e-12 * fmax(fmax(D, best), fscale);
         if (D > best + tie) {
             best = D;
             bi = i;

@@ -49,6 +49,11 @@ class Tuning(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
+class PaganiResult(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("error", ctypes.c_double), ("regions_evaluated", ctypes.c_int64),
+                ("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("active_regions", ctypes.c_int64)]
+
+
 class FlowShape(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("layers", ctypes.c_int32), ("hidden", ctypes.c_int32),
                 ("bins", ctypes.c_int32)]
@@ -118,6 +123,9 @@ def _load():
                                        vp]),
         "mcubes_flow_adam_dev": (i32, [i64, vp, vp, vp, vp, i32, ctypes.c_float, vp]),
         "mcubes_flow_integrate": (i32, [i32, dp, i32, ctypes.POINTER(FlowConfig), vp, ctypes.POINTER(FlowReport)]),
+        "mcubes_pagani_rule_points": (i32, [i32]),
+        "mcubes_pagani_evaluate_dev": (i32, [i32, dp, i32, i64, vp, vp, vp, vp, vp, vp]),
+        "mcubes_pagani_integrate": (i32, [i32, dp, i32, dbl, i32, i64, i32, ctypes.POINTER(PaganiResult)]),
         "mcubes_flow_sample_work_bytes": (ctypes.c_size_t, [ctypes.POINTER(FlowShape)]),
         "mcubes_flow_sample_dev": (i32, [ctypes.POINTER(FlowShape), vp, i32, dp, i64, u64, i32, u32, i64, i64, vp, vp,
                                          vp, dp, vp, ctypes.c_size_t, vp]),
@@ -403,6 +411,27 @@ def flow_forward_dev(shape, d_params, n, d_x, d_z, d_logq, d_work, work_bytes, s
 def flow_inverse_dev(shape, d_params, n, d_z, d_x, d_logq, d_work, work_bytes, stream=None):
     _check(_lib.mcubes_flow_inverse_dev(ctypes.byref(shape), _dptr(d_params), int(n), _dptr(d_z), _dptr(d_x),
                                         _dptr(d_logq), _dptr(d_work), int(work_bytes), _stream(stream)), "flow_inverse")
+
+
+def pagani_rule_points(d: int) -> int:
+    return int(_lib.mcubes_pagani_rule_points(int(d)))
+
+
+def pagani_evaluate_dev(fid, params, d, n, d_lo, d_len, d_I, d_E, d_axis, stream=None):
+    """The PAGANI kernel on n device regions (lo, len: n x d FP64) -> I, E (FP64), axis (int32)."""
+    par, pp = _par(fid, d, params)
+    _check(_lib.mcubes_pagani_evaluate_dev(int(fid), pp, int(d), int(n), _dptr(d_lo), _dptr(d_len), _dptr(d_I),
+                                           _dptr(d_E), _dptr(d_axis), _stream(stream)), "pagani_evaluate")
+
+
+def pagani_integrate(fid, params, d, rel_tol, max_iters=40, max_regions=1 << 22, init_split=2):
+    """Adaptive PAGANI run: dict(estimate, error, regions_evaluated, iterations, status, active_regions)."""
+    par, pp = _par(fid, d, params)
+    r = PaganiResult()
+    _check(_lib.mcubes_pagani_integrate(int(fid), pp, int(d), float(rel_tol), int(max_iters), int(max_regions),
+                                        int(init_split), ctypes.byref(r)), "pagani_integrate")
+    return dict(estimate=r.estimate, error=r.error, regions_evaluated=r.regions_evaluated, iterations=r.iterations,
+                status=r.status, active_regions=r.active_regions)
 
 
 def flow_sample_work_bytes(shape: FlowShape) -> int:

@@ -182,3 +182,21 @@ def test_flow_sample_work_bytes_and_argument_checks(capi):
     assert _status(lambda: call(nb=nb - 16)) == 8
     assert _status(lambda: call(i0=781250 - 50)) == 1       # past the iteration's m p samples
     assert _status(lambda: call(p=None)) == 1
+
+
+def test_pagani_rule_size_and_argument_checks(capi):
+    for d in range(2, 17):
+        assert capi.pagani_rule_points(d) == 1 + 4 * d + 2 * d * (d - 1) + 2 ** d
+    assert capi.pagani_rule_points(1) == 0 and capi.pagani_rule_points(17) == 0
+    par = W.genz_params(W.GAUSSIAN, 3)
+    ev = lambda fid=W.GAUSSIAN, d=3, n=10, p=1 << 20, params=par: capi.pagani_evaluate_dev(
+        fid, params, d, n, p, p, p, p, p)
+    assert _status(lambda: ev(d=1, params=W.genz_params(W.GAUSSIAN, 1))) == 2
+    assert _status(lambda: ev(d=17, params=np.ones(34))) == 2
+    assert _status(lambda: ev(fid=10)) == 3
+    assert _status(lambda: ev(n=-1)) == 1
+    assert _status(lambda: ev(p=None)) == 1
+    assert _status(lambda: capi.pagani_integrate(W.GAUSSIAN, par, 3, 0.0)) == 1
+    assert _status(lambda: capi.pagani_integrate(W.GAUSSIAN, par, 3, 1e-3, max_iters=0)) == 1
+    assert _status(lambda: capi.pagani_integrate(W.GAUSSIAN, par, 3, 1e-3, init_split=0)) == 1
+    assert _status(lambda: capi.pagani_integrate(W.GAUSSIAN, par, 3, 1e-3, max_regions=7, init_split=2)) == 1
