@@ -266,6 +266,56 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20):
     return out
 
 
+# ------------------------------------------------------------------------------ PAGANI
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, NVIDIA's figure (no measured FP64 peak is recorded)
+
+
+def pagani_leg(capi, W, torch, dev, pars, mcubes64):
+    """The paper's other workload (Sec. 3.1): the PAGANI region-evaluation kernel on 2^18 random
+    regions of [0,1]^8 for each Genz family (regions/s, integrand evaluations/s, and FP64
+    operations/s against the nominal FP64 peak, counting 6 d + 2 FP64 operations a point: the
+    map to the region and the family's per-axis arithmetic, the class sum, the exp), and the
+    adaptive driver to a relative error of 1e-3 per family (wall time, regions, status, and its
+    estimate against the m-Cubes FP64 estimate of the same run)."""
+    d = 8
+    n = 1 << 18
+    rng = np.random.default_rng(0)
+    lo = torch.from_numpy(rng.uniform(0.0, 0.5, (n, d))).to(dev)
+    ln = torch.from_numpy(rng.uniform(0.05, 0.5, (n, d))).to(dev)
+    dI = torch.empty(n, dtype=torch.float64, device=dev)
+    dE = torch.empty_like(dI)
+    dax = torch.empty(n, dtype=torch.int32, device=dev)
+    npts = capi.pagani_rule_points(d)
+    kern = {}
+    for fid in W.GENZ6:
+        capi.pagani_evaluate_dev(fid, pars[fid], d, n, lo, ln, dI, dE, dax)   # warm-up
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record()
+        for _ in range(reps):
+            capi.pagani_evaluate_dev(fid, pars[fid], d, n, lo, ln, dI, dE, dax)
+        b.record()
+        b.synchronize()
+        sec = a.elapsed_time(b) * 1e-3 / reps
+        ops = (6 * d + 2) * npts * n
+        kern[W.NAMES[fid]] = {"regions_per_s": n / sec, "evaluations_per_s": n * npts / sec,
+                              "fp64_tflops": ops / sec / 1e12,
+                              "fp64_frac_of_nominal": ops / sec / 1e12 / FP64_NOMINAL_TFLOPS, "ms": sec * 1e3}
+    adapt = {}
+    for fid in W.GENZ6:
+        t0 = time.perf_counter()
+        r = capi.pagani_integrate(fid, pars[fid], d, 1e-3, max_iters=40, max_regions=1 << 22, init_split=2)
+        el = time.perf_counter() - t0
+        ref = mcubes64.get(fid)
+        adapt[W.NAMES[fid]] = dict(r, seconds=el,
+                                   vs_mcubes_fp64_sigma=(abs(r["estimate"] - ref["estimate"]) /
+                                                         math.hypot(r["error"], ref["error"]) if ref else None))
+    return {"d": d, "rule_points": npts, "kernel": kern, "adaptive_1e-3": adapt,
+            "kernel_config": f"{n} random regions, lo ~ U[0, 0.5], len ~ U[0.05, 0.5], a_i ~ U[5,15], u_i ~ U[0.2,0.8]"}
+
+
 # ------------------------------------------------------------------------------ our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -280,6 +330,7 @@ def main():
     ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (4096-job) leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
+    ap.add_argument("--no-pagani", action="store_true", help="skip the PAGANI leg")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling runs)")
     ap.add_argument("--train-steps", type=int, default=2000, help="flow training steps in the learned leg")
     args = ap.parse_args()
@@ -531,6 +582,10 @@ def main():
     if not args.no_learned and rank == 0:
         learned = learned_leg(capi, W, args.train_steps)
 
+    pagani = None
+    if not args.no_pagani and rank == 0:
+        pagani = pagani_leg(capi, W, torch, dev, pars, res64)
+
     # ---- CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -582,6 +637,7 @@ def main():
             "time_to_1e-3": tta,
             "batch": batch,
             "learned": learned,
+            "pagani": pagani,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
