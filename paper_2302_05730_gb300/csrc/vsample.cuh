@@ -175,14 +175,14 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
     const T magic = F32 ? (T)8388608.0f : (T)4503599627370496.0;   // 2^23 / 2^52
     const uint32_t p = P.p;
     const float inv_p32 = (float)P.inv_p;
-    // global-histogram scale (FP32: (F / sigma)^2; FP64: nd^(2d))
+    // global-histogram scale (FP32: (F / sigma)^2; FP64: 1, the contribution already carries nd^d)
     double gscale = 0.0;
     if constexpr (kGlobalHist) {
         if constexpr (F32) {
             const double r = P.fscale / (double)hsig;
             gscale = r * r;
         } else {
-            gscale = P.fscale * P.fscale;
+            gscale = 1.0;
         }
     }
 
@@ -281,7 +281,10 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                     const float ws = w * hsig;
                     h = ws * ws;
                 } else {
-                    h = w * w;
+                    // the full weight (with the Jacobian's nd^d) squared: the same range as the
+                    // contribution itself, so it underflows only where the contribution does
+                    const double wf = w * P.fscale;
+                    h = wf * wf;
                 }
                 if constexpr (kGlobalHist) {
                     const double hg = (double)h * gscale;
@@ -370,7 +373,7 @@ __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums 
             const double r = P.fscale / (double)hsig;
             cscale = r * r;
         } else {
-            cscale = P.fscale * P.fscale;
+            cscale = 1.0;   // the block's contributions already carry nd^(2d)
         }
         for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
             const T v = hist[e];

@@ -246,33 +246,126 @@ def test_device_iteration_matches_host_call(capi):
         assert np.allclose(g_out.cpu().numpy(), h["grid"], rtol=0, atol=1e-14 if mode == 0 else 1e-8)
 
 
-def test_probe_outputs_match_oracle_cubes(capi):
-    d, n, fid = 5, 10 ** 6, W.PRODUCT_PEAK
-    par = _params(fid, d)
-    B = _random_grid(d, 5)
+F32_MIN = float(np.finfo(np.float32).tiny)
+
+
+def _weight_error_bounds(fid, d, par, x, w, J, mode):
+    """Bound on the rounding error of each sample weight w = f J in the kernel's precision.
+    The integrand's argument (the exponent, the oscillatory phase) is a sum of d rounded terms,
+    so its absolute error grows with its size, and f's relative error with it; J is a product of
+    d rounded bin widths. FP32-eval weights also underflow below FLT_MIN times the integrand's
+    scale factor F (the peak value: 1, prod a_i^2 for the product peak, e^{sum a min(u, 1)} for
+    the discontinuous family)."""
+    eps = 2.0 ** -24 if mode == 1 else 2.0 ** -53
+    a, u = par[:d], par[d:]
+    aw = np.abs(w)
+    base = eps * (8 + 2 * d)
+    if fid == W.OSCILLATORY:
+        t = np.abs(u[0] + x @ a / (2 * np.pi))
+        delta = aw * base + np.abs(J) * (2 * np.pi * eps * (d + 4) * (t + 1.0) + 4 * eps)
+    elif fid in (W.GAUSSIAN, W.C0, W.DISCONTINUOUS):
+        if fid == W.GAUSSIAN:
+            arg = np.sum((a * (x - u)) ** 2, axis=1)
+        elif fid == W.C0:
+            arg = np.sum(a * np.abs(x - u), axis=1)
+        else:
+            arg = np.abs(x @ a - np.sum(a * np.minimum(u, 1.0)))
+        delta = aw * (base + eps * 1.5 * (d + 4) * arg)
+    elif fid == W.PRODUCT_PEAK:
+        delta = aw * (base + eps * 6 * d)
+    elif fid == W.CORNER_PEAK:
+        delta = aw * (base + eps * 4 * (d + 1))
+    else:
+        delta = aw * (base + eps * d)
+    if mode == 1:
+        # f / F below FLT_MIN, and w / F in the subnormal range (spacing 2^-149)
+        delta = delta + 4 * F32_MIN * _f32_scale(fid, d, par) * np.abs(J) + 2.0 ** -148 * _f32_scale(fid, d, par)
+    return delta
+
+
+def _f32_scale(fid, d, par):
+    """The FP32-eval integrand's scale factor F (the peak value)."""
+    a, u = par[:d], par[d:]
+    return {W.PRODUCT_PEAK: float(np.prod(a ** 2)),
+            W.DISCONTINUOUS: float(np.exp(np.sum(a * np.minimum(u, 1.0))))}.get(fid, 1.0)
+
+
+def _check_probes(capi, fid, d, n, mode, B, shift, par, seed=3, it=0, job=0):
+    """One full V-Sample pass (adjusting) on the device with sub-cube probes: every probed
+    sub-cube's (I_t, V_t) against the oracle's computation of that sub-cube alone, within the
+    rounding the kernel's precision allows for that sub-cube's own samples."""
     g, m, p = capi.stratify(d, n)
-    shift = 10
     dev = torch.device("cuda")
     probe = torch.full(((m >> shift) + 1, 2), -1.0, dtype=torch.float64, device=dev)
     sums = torch.zeros(2, dtype=torch.float64, device=dev)
     C = torch.zeros(d * 500, dtype=torch.float64, device=dev)
+    capi.vsample_dev(fid, par, d, n, seed, it, job, 1, mode, torch.from_numpy(B).to(dev), C, sums,
+                     d_probe=probe, probe_shift=shift)
+    torch.cuda.synchronize()
+    pr = probe.cpu().numpy()
+    s = sums.cpu().numpy()
+    assert np.all(np.isfinite(s)) and s[1] >= 0.0
+    for t in range(0, m, 1 << shift):
+        ref = oracle.vsample(fid, d, par, n, seed, it=it, job=job, mode=mode, adjust=0, B=B, t0=t, t1=t + 1,
+                             per_cube=True)
+        sp = oracle.sample_points(fid, d, par, n, seed, it=it, job=job, mode=mode, B=B, t0=t, t1=t + 1)
+        delta = _weight_error_bounds(fid, d, par, sp["x"], sp["w"], sp["J"], mode)
+        rel = 1e-12 if mode == 0 else 1e-6
+        I_ref, V_ref = ref["cubeI"][0], ref["cubeV"][0]
+        tol_I = rel * abs(I_ref) + delta.sum() / p + 1e-300
+        assert abs(pr[t >> shift, 0] - I_ref) <= tol_I, (t, pr[t >> shift], I_ref, tol_I)
+        # V = sum (w_q - I)^2 / (p (p-1)): a weight error delta_q moves it by at most
+        # 2 sum |w_q - I| delta_q / (p (p-1)) <= 2 max(delta) sqrt(V / (p-1)) (plus delta^2 terms)
+        md = float(delta.max())
+        vf = (8 * EPS if mode == 0 else 4 * F32_W ** 2) * (V_ref + I_ref ** 2 / (p - 1))
+        if mode == 1:   # squared FP32 differences below FLT_MIN (in units of F^2) lose their digits
+            vf += 4 * F32_MIN * _f32_scale(fid, d, par) ** 2
+        tol_V = rel * V_ref + vf + 2 * md * math.sqrt(V_ref / (p - 1)) + 2 * md * md
+        assert abs(pr[t >> shift, 1] - V_ref) <= tol_V, (t, pr[t >> shift], V_ref, tol_V)
+    return m >> shift
+
+
+def test_probe_outputs_match_oracle_cubes(capi):
+    d, n, fid = 5, 10 ** 6, W.PRODUCT_PEAK
     for mode in (0, 1):
-        probe.fill_(-1.0)
-        sums.zero_()
-        capi.vsample_dev(fid, par, d, n, 3, 0, 0, 1, mode, torch.from_numpy(B).to(dev), C, sums,
-                         d_probe=probe, probe_shift=shift)
-        torch.cuda.synchronize()
-        pr = probe.cpu().numpy()
-        for t in range(0, m, 1 << shift):
-            ref = oracle.vsample(fid, d, par, n, 3, it=0, mode=mode, adjust=0, B=B, t0=t, t1=t + 1, per_cube=True)
-            rel = 1e-12 if mode == 0 else 1e-5
-            I_ref, V_ref = ref["cubeI"][0], ref["cubeV"][0]
-            assert abs(pr[t >> shift, 0] - I_ref) <= rel * abs(I_ref) + 1e-300
-            vf = (8 * EPS if mode == 0 else 4 * F32_W ** 2) * (V_ref + I_ref ** 2 / (p - 1))
-            # a single cube has no averaging: FP32 differences of nearly equal weights carry
-            # the weights' own rounding, bounded by 2 |dw| |w| F32_W
-            vr = rel if mode == 0 else 4 * F32_W * math.sqrt(abs(I_ref) ** 2 / max(V_ref, 1e-300))
-            assert abs(pr[t >> shift, 1] - V_ref) <= vr * V_ref + vf
+        _check_probes(capi, fid, d, n, mode, _random_grid(d, 5), 10, _params(fid, d))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fid", list(W.GENZ6))
+def test_headline_size_probes(capi, fid, mode):
+    """The bench's workload at full size: d = 8, 1e8 samples per iteration (m = 9^8 = 43,046,721
+    sub-cubes, p = 2), the default launch shape; every 65,536th sub-cube against the oracle."""
+    d, n = 8, 10 ** 8
+    assert _check_probes(capi, fid, d, n, mode, _random_grid(d, 77), 16, W.genz_params(fid, d, seed=0),
+                         seed=11, it=4, job=0) >= 600
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fid", [W.PRODUCT_PEAK, W.C0])
+def test_large_d10_probes(capi, fid, mode):
+    """d = 10 at 1e9 samples per iteration (g = 7, m = 282,475,249 sub-cubes, p = 3): the cube
+    index stays within its 32-bit counter word; every 2^18-th sub-cube against the oracle."""
+    d, n = 10, 10 ** 9
+    assert _check_probes(capi, fid, d, n, mode, _random_grid(d, 78), 18, W.genz_params(fid, d, seed=0),
+                         seed=12, it=7, job=0) >= 1000
+
+
+def test_batched_full_size_sampled_jobs(capi):
+    """The 4096-job batch of the bench (d ~ U{2..8}, samples per iteration log-uniform in
+    [1e4, 1e7], 8 iterations, 4 adjusting) in one call; the twelve smallest jobs' whole runs
+    against the oracle's (Philox job word = the job's index)."""
+    jobs = W.batch_jobs(4096, seed=0)
+    got = capi.integrate_batch(jobs, 8, 4, precision=0, return_iters=True)
+    assert all(g["status"] == 0 for g in got)
+    order = sorted(range(len(jobs)), key=lambda k: jobs[k]["ncall"])[:12]
+    for k in order:
+        j = jobs[k]
+        est, sig, chi2, iI, iV = oracle.integrate(j["fid"], j["d"], j["params"], j["ncall"], 8, 4, j.get("seed", 0),
+                                                  job=k)
+        g = got[k]
+        assert abs(g["estimate"] - est) <= 1e-10 * max(abs(est), sig), (k, g["estimate"], est)
+        assert math.isclose(g["error"], sig, rel_tol=1e-8), (k, g["error"], sig)
 
 
 # ------------------------------------------------------------------------------ errors
