@@ -135,6 +135,46 @@ __device__ double eval64(int fid, int d, const IntegrandParams &ip, const double
     }
 }
 
+// A region's estimates from its class sums S and its centre and axis values fax: I = I7,
+// E = |I7 - I5| and the split axis (largest fourth difference; ties -- within 1e-12 of the
+// larger difference and of the largest |f| at those points -- to the longest side, then the
+// lowest axis).
+__device__ void finish_region(const PgRule &R, const double (&S)[5], const double *fax, const double *rlen,
+                              double *I, double *E, int *axis)
+{
+    const int d = R.d;
+    double vol = 1.0;
+    for (int i = 0; i < d; ++i) vol *= rlen[i];
+    double i7 = 0.0, i5 = 0.0;
+    for (int k = 0; k < 5; ++k) {
+        i7 += R.w7[k] * S[k];
+        i5 += R.w5[k] * S[k];
+    }
+    const double scale = vol / ldexp(1.0, d);
+    i7 *= scale;
+    i5 *= scale;
+    *I = i7;
+    *E = fabs(i7 - i5);
+    const double f0 = fax[0];
+    double fscale = fabs(f0);   // the rounding-noise scale of the fourth differences
+    for (int p = 1; p < R.base4; ++p) fscale = fmax(fscale, fabs(fax[p]));
+    double best = -1.0;
+    int bi = 0;
+    for (int i = 0; i < d; ++i) {
+        const double a2 = fax[1 + 2 * i] + fax[2 + 2 * i] - 2.0 * f0;
+        const double a3 = fax[R.base3 + 2 * i] + fax[R.base3 + 1 + 2 * i] - 2.0 * f0;
+        const double D = fabs(a2 - R.r23 * a3);
+        const double tie = 1e-12 * fmax(fmax(D, best), fscale);
+        if (D > best + tie) {
+            best = D;
+            bi = i;
+        } else if (fabs(D - best) <= tie && rlen[i] > rlen[bi]) {
+            bi = i;
+        }
+    }
+    *axis = bi;
+}
+
 // Rule point p on [-1, 1]^d (the oracle's order): u, and its class 1..5.
 __device__ __forceinline__ int rule_point(const PgRule &R, int p, double *u)
 {
@@ -168,6 +208,216 @@ __device__ __forceinline__ int rule_point(const PgRule &R, int p, double *u)
     return 5;
 }
 
+// Separable families. A rule point's coordinate on axis i takes one of 9 values (u = 0, +-l2, +-l3,
+// +-l4, +-l5), so a warp tabulates each axis's factor or term at those 9 points once per region, and
+// a point combines table entries instead of evaluating the integrand from scratch:
+//   multiplicative (no transcendental per point): f = prod_i e_i(x_i) with e = exp(-phi) for the
+//   Gaussian and C0, exp(a x) for the discontinuous family (times its cut), 1 / psi for the product
+//   peak; the double Gaussian is the sum of two such products;
+//   additive: f = g(sum_i phi_i(x_i)) for the oscillatory (cos), corner peak and addition families.
+// Classes 1-4 change at most two axes from the centre: they use the centre's product over all but
+// those axes (tabulated per axis and per pair), so no factor is divided out (a factor can underflow
+// to zero). Class 5 combines d table entries.
+constexpr int kPgMaxPairs = kDMax * (kDMax - 1) / 2;
+
+struct PgAxisTab {
+    double t1[kDMax][9];          // per-axis factor (multiplicative) or term (additive)
+    double t2[kDMax][9];          // double Gaussian: the second peak's factors
+    unsigned char out[kDMax][9];  // discontinuous: 1 where x_i >= u_i (outside the cut)
+    double ex1[kDMax], ex2[kDMax];            // centre product (or sum) over all axes but k
+    double px1[kPgMaxPairs], px2[kPgMaxPairs];   // ... over all axes but the pair (i, j)
+    int nout_ex1[kDMax], nout_px[kPgMaxPairs];   // discontinuous: centre cut count without k / (i, j)
+    double all1, all2;
+    int nout_all;
+};
+
+__device__ __forceinline__ bool pg_mult(int fid)
+{
+    return fid == kGaussian || fid == kC0 || fid == kDiscontinuous || fid == kDoubleGaussian || fid == kProductPeak;
+}
+
+// The factor / term of axis i at coordinate x.
+__device__ __forceinline__ void pg_terms(int fid, const IntegrandParams &ip, int i, double x, double &t1, double &t2,
+                                         unsigned char &out)
+{
+    t2 = 0.0;
+    out = 0;
+    switch (fid) {
+    case kOscillatory:
+    case kCornerPeak:
+        t1 = ip.a[i] * x;
+        break;
+    case kProductPeak: {
+        const double t = x - ip.u[i];
+        t1 = 1.0 / fma(t, t, ip.b[i]);
+        break;
+    }
+    case kGaussian: {
+        const double v = ip.a[i] * (x - ip.u[i]);
+        t1 = exp(-(v * v));
+        break;
+    }
+    case kC0:
+        t1 = exp(-(ip.a[i] * fabs(x - ip.u[i])));
+        break;
+    case kDiscontinuous:
+        t1 = exp(ip.a[i] * x);
+        out = x < ip.u[i] ? 0 : 1;
+        break;
+    case kAddition:
+        t1 = x;
+        break;
+    case kDoubleGaussian: {
+        const double v1 = ip.a[i] * (x - ip.u[i]), v2 = ip.a[i] * (x - ip.b[i]);
+        t1 = exp(-(v1 * v1));
+        t2 = exp(-(v2 * v2));
+        break;
+    }
+    default:
+        t1 = 0.0;
+    }
+}
+
+// f from the combined product (multiplicative) or sum (additive).
+__device__ __forceinline__ double pg_outer(int fid, int d, const IntegrandParams &ip, double A, double A2, int nout)
+{
+    switch (fid) {
+    case kOscillatory: return cos(fma(6.283185307179586476925286766559, ip.u[0], A));
+    case kCornerPeak: {
+        const double b = 1.0 + A;
+        double r = 1.0;
+        for (int e = 0; e <= d; ++e) r *= b;
+        return 1.0 / r;
+    }
+    case kAddition: return A;
+    case kDiscontinuous: return nout == 0 ? A : 0.0;
+    case kDoubleGaussian: return A + A2;
+    default: return A;   // Gaussian, C0, product peak
+    }
+}
+
+__device__ __forceinline__ int pair_index(int i, int j, int d)
+{
+    return i * (2 * d - i - 1) / 2 + (j - i - 1);   // pairs i < j in row-major order
+}
+
+__global__ void __launch_bounds__(kPgWarps * 32)
+    pagani_evaluate_sep_kernel(const PgRule R, const IntegrandParams ip, int fid, long long n,
+                               const double *__restrict__ lo, const double *__restrict__ len, double *__restrict__ I,
+                               double *__restrict__ E, int *__restrict__ axis)
+{
+    __shared__ double fax[kPgWarps][kPgAxisPts];
+    __shared__ PgAxisTab tabs[kPgWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = R.d;
+    const bool mult = pg_mult(fid);
+    const int npairs = d * (d - 1) / 2;
+    PgAxisTab &T = tabs[warp];
+    for (long long r = (long long)blockIdx.x * kPgWarps + warp; r < n; r += (long long)gridDim.x * kPgWarps) {
+        const double *rlo = lo + r * d, *rlen = len + r * d;
+        for (int e = lane; e < d * 9; e += 32) {
+            const int i = e / 9, k = e - i * 9;
+            const double lv = k == 0 ? 0.0 : (k <= 2 ? R.l2 : k <= 4 ? R.l3 : k <= 6 ? R.l4 : R.l5);
+            const double u = (k & 1) || k == 0 ? lv : -lv;
+            const double x = rlo[i] + 0.5 * rlen[i] * (1.0 + u);
+            pg_terms(fid, ip, i, x, T.t1[i][k], T.t2[i][k], T.out[i][k]);
+        }
+        __syncwarp();
+        // centre combinations over all axes, all but one, all but a pair
+        for (int e = lane; e < 1 + d + npairs; e += 32) {
+            int skip_i = -1, skip_j = -1;
+            if (e >= 1 && e <= d) {
+                skip_i = e - 1;
+            } else if (e > d) {
+                int pr = e - 1 - d, i = 0;
+                while (pr >= d - 1 - i) {
+                    pr -= d - 1 - i;
+                    ++i;
+                }
+                skip_i = i;
+                skip_j = i + 1 + pr;
+            }
+            double c1 = mult ? 1.0 : 0.0, c2 = mult ? 1.0 : 0.0;
+            int no = 0;
+            for (int i = 0; i < d; ++i) {
+                if (i == skip_i || i == skip_j) continue;
+                c1 = mult ? c1 * T.t1[i][0] : c1 + T.t1[i][0];
+                c2 = mult ? c2 * T.t2[i][0] : c2 + T.t2[i][0];
+                no += T.out[i][0];
+            }
+            if (e == 0) {
+                T.all1 = c1;
+                T.all2 = c2;
+                T.nout_all = no;
+            } else if (e <= d) {
+                T.ex1[e - 1] = c1;
+                T.ex2[e - 1] = c2;
+                T.nout_ex1[e - 1] = no;
+            } else {
+                T.px1[e - 1 - d] = c1;
+                T.px2[e - 1 - d] = c2;
+                T.nout_px[e - 1 - d] = no;
+            }
+        }
+        __syncwarp();
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+        for (int p = lane; p < R.n; p += 32) {
+            double A, A2;
+            int no, cls;
+            if (p == 0) {
+                A = T.all1;
+                A2 = T.all2;
+                no = T.nout_all;
+                cls = 1;
+            } else if (p < R.base4) {
+                const bool c3 = p >= R.base3;
+                const int q = c3 ? p - R.base3 : p - 1, k = q >> 1, idx = (c3 ? 3 : 1) + (q & 1);
+                A = mult ? T.ex1[k] * T.t1[k][idx] : T.ex1[k] + T.t1[k][idx];
+                A2 = mult ? T.ex2[k] * T.t2[k][idx] : 0.0;
+                no = T.nout_ex1[k] + T.out[k][idx];
+                cls = c3 ? 3 : 2;
+            } else if (p < R.base5) {
+                const int q = p - R.base4, sg = q & 3;
+                int pair = q >> 2, i = 0;
+                while (pair >= d - 1 - i) {
+                    pair -= d - 1 - i;
+                    ++i;
+                }
+                const int j = i + 1 + pair, ii = 5 + ((sg >> 1) & 1), ij = 5 + (sg & 1), pi = pair_index(i, j, d);
+                A = mult ? T.px1[pi] * (T.t1[i][ii] * T.t1[j][ij]) : T.px1[pi] + (T.t1[i][ii] + T.t1[j][ij]);
+                A2 = mult ? T.px2[pi] * (T.t2[i][ii] * T.t2[j][ij]) : 0.0;
+                no = T.nout_px[pi] + T.out[i][ii] + T.out[j][ij];
+                cls = 4;
+            } else {
+                const int b = p - R.base5;
+                A = mult ? 1.0 : 0.0;
+                A2 = mult ? 1.0 : 0.0;
+                no = 0;
+                for (int i = 0; i < d; ++i) {
+                    const int idx = 7 + ((b >> i) & 1);
+                    A = mult ? A * T.t1[i][idx] : A + T.t1[i][idx];
+                    A2 = mult ? A2 * T.t2[i][idx] : A2;
+                    no += T.out[i][idx];
+                }
+                cls = 5;
+            }
+            const double f = pg_outer(fid, d, ip, A, A2, no);
+            if (cls == 5) s4 += f;
+            else if (cls == 4) s3 += f;
+            else if (cls == 3) s2 += f;
+            else if (cls == 2) s1 += f;
+            else s0 += f;
+            if (p < R.base4) fax[warp][p] = f;
+        }
+        double S[5] = {s0, s1, s2, s3, s4};
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            for (int o = 16; o > 0; o >>= 1) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o);
+        __syncwarp();
+        if (lane == 0) finish_region(R, S, fax[warp], rlen, I + r, E + r, axis + r);
+        __syncwarp();   // the next region reuses the tables and fax
+    }
+}
+
 __global__ void __launch_bounds__(kPgWarps * 32)
     pagani_evaluate_kernel(const PgRule R, const IntegrandParams ip, int fid, long long n, const double *__restrict__ lo,
                            const double *__restrict__ len, double *__restrict__ I, double *__restrict__ E,
@@ -194,38 +444,7 @@ __global__ void __launch_bounds__(kPgWarps * 32)
         for (int k = 0; k < 5; ++k)
             for (int o = 16; o > 0; o >>= 1) S[k] += __shfl_xor_sync(0xffffffffu, S[k], o);
         __syncwarp();
-        if (lane == 0) {
-            double vol = 1.0;
-            for (int i = 0; i < d; ++i) vol *= rlen[i];
-            double i7 = 0.0, i5 = 0.0;
-            for (int k = 0; k < 5; ++k) {
-                i7 += R.w7[k] * S[k];
-                i5 += R.w5[k] * S[k];
-            }
-            const double scale = vol / ldexp(1.0, d);
-            i7 *= scale;
-            i5 *= scale;
-            I[r] = i7;
-            E[r] = fabs(i7 - i5);
-            const double f0 = fax[warp][0];
-            double fscale = fabs(f0);   // the rounding-noise scale of the fourth differences
-            for (int p = 1; p < R.base4; ++p) fscale = fmax(fscale, fabs(fax[warp][p]));
-            double best = -1.0;
-            int bi = 0;
-            for (int i = 0; i < d; ++i) {
-                const double a2 = fax[warp][1 + 2 * i] + fax[warp][2 + 2 * i] - 2.0 * f0;
-                const double a3 = fax[warp][R.base3 + 2 * i] + fax[warp][R.base3 + 1 + 2 * i] - 2.0 * f0;
-                const double D = fabs(a2 - R.r23 * a3);
-                const double tie = 1e-12 * fmax(fmax(D, best), fscale);
-                if (D > best + tie) {
-                    best = D;
-                    bi = i;
-                } else if (fabs(D - best) <= tie && rlen[i] > rlen[bi]) {
-                    bi = i;
-                }
-            }
-            axis[r] = bi;
-        }
+        if (lane == 0) finish_region(R, S, fax[warp], rlen, I + r, E + r, axis + r);
         __syncwarp();   // the next region reuses fax
     }
 }
@@ -393,7 +612,10 @@ int launch_evaluate(const PgRule &R, const IntegrandParams &ip, int fid, long lo
     const int sms = num_sms();
     if (sms <= 0) return cuda_status(cudaErrorNoDevice);
     const long long blocks = std::min<long long>((n + kPgWarps - 1) / kPgWarps, (long long)sms * 16);
-    pagani_evaluate_kernel<<<(unsigned)blocks, kPgWarps * 32, 0, s>>>(R, ip, fid, n, lo, len, I, E, axis);
+    if (fid != kRotatedGaussian && fid != kConstant)
+        pagani_evaluate_sep_kernel<<<(unsigned)blocks, kPgWarps * 32, 0, s>>>(R, ip, fid, n, lo, len, I, E, axis);
+    else
+        pagani_evaluate_kernel<<<(unsigned)blocks, kPgWarps * 32, 0, s>>>(R, ip, fid, n, lo, len, I, E, axis);
     return cuda_status(cudaGetLastError());
 }
 
