@@ -12,6 +12,7 @@
 #include <cstring>
 
 namespace mcubes {
+struct IntegrandParams;
 namespace flow {
 
 constexpr int kTileRows = 64;      // samples per CTA tile (4 warps x 16 rows)
@@ -363,6 +364,39 @@ inline bool fused_layout(const Shape &S, FusedFlow &F)
 
 // Writes the mirror of the FP32 parameters d_params (defined with the sampler).
 int build_mirror(const FusedFlow &F, const float *d_params, unsigned char *mirror, cudaStream_t s);
+
+// ------------------------------------------------------------------------------ tcgen05 sampler
+// The tensor-core (tcgen05) form of the fused sampler (flow_tc.cu): weights in the K-major,
+// unswizzled core-matrix layout per layer (W1 [H][16], W2 [H][H], W3 [N3][H] bf16 with
+// N3 = |B| SW rounded up to 16, then b1, b2, b3 in FP32).
+struct TcLayer {
+    int nA, nB, N3;
+    int A[kMaxAB], B[kMaxAB];
+    uint32_t off, bytes;
+    uint32_t oW2, oW3, ob1, ob2, ob3;
+    uint32_t pW1, pb1, pW2, pb2, pW3, pb3;
+};
+
+struct TcFlow {
+    int L, H, K, SW;
+    uint32_t max_bytes, total_bytes;
+    TcLayer lay[kFMaxLayers];
+};
+
+struct TcSample {   // one iteration's stratification and Philox stream
+    uint32_t m, p, g, key0, key1, ctr2_hi, job;
+    int d, fid;
+};
+
+// The mirror layout of a shape; false when the tcgen05 sampler does not take it (H > 128,
+// an output GEMM wider than 256, more than 16 layers).
+bool tc_layout(const Shape &S, TcFlow &F);
+int build_tc_mirror(const TcFlow &F, const float *d_params, unsigned char *mirror, cudaStream_t s);
+// Samples [i0, i0 + n): x, log q (optional) and w = (f / F) / q; *err is set when a bounded wait
+// expired. kFusedUnsupported when the shape does not fit (then use the mma.sync sampler).
+int launch_flow_sample_tc(const TcFlow &F, const unsigned char *mirror, const TcSample &S,
+                          const IntegrandParams &ip, long long i0, long long n, float *x, float *lq,
+                          float *w, int *err, cudaStream_t s);
 
 // Scratch of the fused training step (carved from the flow workspace).
 struct FusedTrainWork {

@@ -419,8 +419,12 @@ int launch_fused_hk(const FusedFlow &F, const unsigned char *mirror, const Sampl
     } else {
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, flow_sample_kernel<H, K>);
+        if (e == cudaSuccess) {
+            optin -= (int)fa.sharedSizeBytes;   // the opt-in limit covers static and dynamic shared memory
             e = cudaFuncSetAttribute(flow_sample_kernel<H, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        }
         if (e != cudaSuccess) return cuda_status(e);
         if (dev < 64) {
             optin_c[dev] = optin;
@@ -533,12 +537,28 @@ int build_mirror(const FusedFlow &F, const float *d_params, unsigned char *mirro
 }  // namespace flow
 }  // namespace mcubes
 
+namespace {
+
+// Scratch of the fused samplers: the larger of the two weight mirrors, then the tcgen05
+// sampler's wait-expiry flag (256 bytes).
+size_t sample_scratch(const flow::Shape &S, bool &tc_ok, flow::TcFlow &T, FusedFlow &F)
+{
+    const bool f_ok = flow::fused_layout(S, F);
+    tc_ok = flow::tc_layout(S, T);
+    if (!f_ok) return 0;
+    const size_t m = std::max<size_t>(F.total_bytes, tc_ok ? T.total_bytes : 0);
+    return ((m + 255) & ~(size_t)255) + 256;
+}
+
+}  // namespace
+
 extern "C" size_t mcubes_flow_sample_work_bytes(const mcubes_flow_shape *shape)
 {
     if (!shape || mcubes_flow_param_count(shape) <= 0) return 0;
     FusedFlow F;
-    if (!flow::fused_layout(flow::Shape{shape->d, shape->layers, shape->hidden, shape->bins}, F)) return 0;
-    return F.total_bytes;
+    flow::TcFlow T;
+    bool tc_ok;
+    return sample_scratch(flow::Shape{shape->d, shape->layers, shape->hidden, shape->bins}, tc_ok, T, F);
 }
 
 extern "C" int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const float *d_params, int integrand_id,
@@ -551,8 +571,11 @@ extern "C" int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const floa
     if (mcubes_flow_param_count(shape) <= 0) return MCUBES_ERR_INVALID_ARG;
     const flow::Shape S{shape->d, shape->layers, shape->hidden, shape->bins};
     FusedFlow F;
-    if (!flow::fused_layout(S, F)) return MCUBES_ERR_INVALID_ARG;
-    if (!d_work || work_bytes < F.total_bytes || ((uintptr_t)d_work & 255u)) return MCUBES_ERR_WORKSPACE;
+    flow::TcFlow T;
+    bool tc_ok;
+    const size_t need = sample_scratch(S, tc_ok, T, F);
+    if (!need) return MCUBES_ERR_INVALID_ARG;
+    if (!d_work || work_bytes < need || ((uintptr_t)d_work & 255u)) return MCUBES_ERR_WORKSPACE;
     Problem pb;
     int st = prepare(integrand_id, params, S.d, ncall, seed, 0, 0, 0, MCUBES_FP32_EVAL, pb);
     if (st) return st;
@@ -562,6 +585,14 @@ extern "C" int mcubes_flow_sample_dev(const mcubes_flow_shape *shape, const floa
                         (uint32_t)iteration << 16, job, S.d, integrand_id};
     cudaStream_t s = (cudaStream_t)stream;
     unsigned char *mirror = (unsigned char *)d_work;
+    int *err = (int *)((char *)d_work + need - 256);
+    if (tc_ok) {   // the tcgen05 sampler where the shape fits it
+        if ((st = cuda_status(cudaMemsetAsync(err, 0, sizeof(int), s)))) return st;
+        if ((st = flow::build_tc_mirror(T, d_params, mirror, s))) return st;
+        const flow::TcSample TS{SS.m, SS.p, SS.g, SS.key0, SS.key1, SS.ctr2_hi, SS.job, SS.d, SS.fid};
+        st = flow::launch_flow_sample_tc(T, mirror, TS, pb.P.ip, i0, n, d_x, d_logq, d_w, err, s);
+        if (st != kFusedUnsupported) return st;
+    }
     if ((st = flow::build_mirror(F, d_params, mirror, s))) return st;
     st = launch_fused(F, mirror, SS, pb.P.ip, i0, n, d_x, d_logq, d_w, s);
     return st == kFusedUnsupported ? MCUBES_ERR_INVALID_ARG : st;
@@ -609,13 +640,16 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     const long long nchunk = chunk_cubes * p;
     const long long nwork = std::max<long long>(cfg->batch, nchunk);
     FusedFlow FF;
-    const bool fused_ok = flow::fused_layout(flow::Shape{sh.d, sh.layers, sh.hidden, sh.bins}, FF);
+    flow::TcFlow TF;
+    bool tc_ok = false;
+    const size_t sample_bytes = sample_scratch(flow::Shape{sh.d, sh.layers, sh.hidden, sh.bins}, tc_ok, TF, FF);
+    const bool fused_ok = sample_bytes > 0;
     const size_t wbytes = mcubes_flow_work_bytes(&sh, nwork);
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t bytes = al(sizeof(double) * d * kGS) + 2 * al(sizeof(float) * ntr * d) + 3 * al(sizeof(float) * ntr) +
                          4 * al(sizeof(float) * npar) + al(sizeof(float) * 2) + al(sizeof(double) * (2 * (size_t)cfg->flow_iters + 2)) +
                          2 * al(sizeof(float) * nchunk * d) + al(sizeof(float) * nchunk) + al(wbytes) +
-                         al(fused_ok ? FF.total_bytes : 16);
+                         al(fused_ok ? sample_bytes : 256);
     char *mem = nullptr;
     if ((st = cuda_status(cudaMalloc(&mem, bytes)))) return st;
     char *q = mem;
@@ -634,7 +668,8 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     float *d_xs = (float *)take(sizeof(float) * nchunk * d);
     float *d_lq = (float *)take(sizeof(float) * nchunk);
     void *d_work = take(wbytes);
-    unsigned char *d_mirror = (unsigned char *)take(fused_ok ? FF.total_bytes : 16);
+    unsigned char *d_mirror = (unsigned char *)take(fused_ok ? sample_bytes : 256);
+    int *d_err = (int *)(d_mirror + (fused_ok ? sample_bytes : 256) - 256);
     cudaStream_t s = nullptr;
     auto finish = [&](int code) {
         if (s) cudaStreamDestroy(s);
@@ -716,14 +751,30 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     // shape fits it (shared memory, at most 16 layers), else the per-layer kernels
     t0 = std::chrono::steady_clock::now();
     if ((st = cuda_status(cudaMemsetAsync(d_sums, 0, sizeof(double) * 2 * cfg->flow_iters, s)))) return finish(st);
-    bool fused = fused_ok;
-    if (fused && (st = flow::build_mirror(FF, d_par, d_mirror, s))) return finish(st);
+    bool fused = fused_ok, use_tc = fused_ok && tc_ok;
+    if ((st = cuda_status(cudaMemsetAsync(d_err, 0, sizeof(int), s)))) return finish(st);
+    if (use_tc && (st = flow::build_tc_mirror(TF, d_par, d_mirror, s))) return finish(st);
+    if (fused && !use_tc && (st = flow::build_mirror(FF, d_par, d_mirror, s))) return finish(st);
     for (int it = 0; it < cfg->flow_iters; ++it) {
         SampleSpec F{(uint32_t)m, (uint32_t)p, (uint32_t)g, (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32),
                      (uint32_t)(itmax + 2 + it) << 16, 0x20000000u, d, integrand_id};
         for (long long c0 = 0; c0 < m; c0 += chunk_cubes) {
             const long long nc = std::min<long long>(chunk_cubes, m - c0);
             const long long ns = nc * p;
+            if (use_tc) {
+                const flow::TcSample TS{F.m, F.p, F.g, F.key0, F.key1, F.ctr2_hi, F.job, F.d, F.fid};
+                st = flow::launch_flow_sample_tc(TF, d_mirror, TS, pb.P.ip, c0 * p, ns, nullptr, nullptr, d_lq, d_err, s);
+                if (st == kFusedUnsupported) {   // switch to the mma.sync sampler for the rest
+                    use_tc = false;
+                    if ((st = flow::build_mirror(FF, d_par, d_mirror, s))) return finish(st);
+                } else {
+                    if (st) return finish(st);
+                    cube_stats_kernel<<<(unsigned)std::min<long long>((nc + 255) / 256, 65535), 256, 0, s>>>(
+                        F, pb.P.fscale, nc, d_lq, d_sums + 2 * it);
+                    if ((st = cuda_status(cudaGetLastError()))) return finish(st);
+                    continue;
+                }
+            }
             if (fused) {
                 st = launch_fused(FF, d_mirror, F, pb.P.ip, c0 * p, ns, nullptr, nullptr, d_lq, s);
                 if (st == kFusedUnsupported) {
@@ -747,10 +798,13 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
     std::vector<double> fs(2 * (size_t)cfg->flow_iters);
     if ((st = cuda_status(cudaMemcpyAsync(fs.data(), d_sums, sizeof(double) * fs.size(), cudaMemcpyDeviceToHost, s))))
         return finish(st);
+    int h_err = 0;
+    if ((st = cuda_status(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s)))) return finish(st);
     if (params_out &&
         (st = cuda_status(cudaMemcpyAsync(params_out, d_par, sizeof(float) * npar, cudaMemcpyDeviceToHost, s))))
         return finish(st);
     if ((st = cuda_status(cudaStreamSynchronize(s)))) return finish(st);
+    if (h_err) return finish(MCUBES_ERR_TIMEOUT);
     out->seconds_flow = seconds_since(t0);
     std::vector<double> fi(2 * (size_t)cfg->flow_iters);
     double vsum = 0.0;

@@ -1,0 +1,499 @@
+// Fused flow sampler on the fifth-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// A 128-thread CTA takes 128 samples at a time: thread t owns sample row t, which is also TMEM
+// lane t of the accumulators. Per coupling layer (sampling direction):
+//   1. each thread writes its row's kept coordinates (bf16) into the GEMM-1 operand in shared
+//      memory; one thread issues tcgen05.mma D1 = A1 W1^T (M = 128, N = H, K = 16) and commits
+//      to an mbarrier;
+//   2. each thread reads its row of D1 from TMEM (tcgen05.ld), adds the bias, applies ReLU and
+//      writes the bf16 row into the GEMM-2 operand; D2 = A2 W2^T (K = H); the same again into
+//      D3 = A3 W3^T (N = |B| SW rounded up to 16, at most 256);
+//   3. each thread reads its row's 2K+1 outputs of every transformed axis straight from TMEM and
+//      runs the piecewise-quadratic inverse (pq_transform) on them.
+// After the last layer each thread evaluates the integrand at its point. Operands are bf16 in the
+// K-major, unswizzled core-matrix layout (8 rows x 16 bytes per core matrix; leading-dimension
+// offset 128 bytes between core matrices along K, stride offset K/8 x 128 bytes between 8-row
+// groups); the weights come from a mirror that already has this layout. Every mbarrier wait is
+// bounded: on expiry the kernel records an error, stops, and frees its TMEM.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/mcubes.h"
+#include "flow_common.cuh"
+#include "integrands.cuh"
+#include "internal.h"
+
+namespace mcubes {
+namespace flow {
+
+namespace {
+
+constexpr int kTcRows = 128;          // samples per CTA tile = TMEM lanes of an M = 128 accumulator
+constexpr int kTcCols = 256;          // TMEM columns a CTA allocates
+constexpr uint32_t kTcWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major core-matrix offset (bytes) of element (r, k) of an operand with Kd columns.
+__host__ __device__ __forceinline__ uint32_t cm_off(int r, int k, int Kd)
+{
+    return (uint32_t)((r >> 3) * (Kd >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start, leading-dimension offset (K direction), stride offset
+// (8-row groups), the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, M = 128.
+__host__ __device__ __forceinline__ uint32_t mma_idesc(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+// D[tmem] (+)= A[128 x Kd] B[N x Kd]^T, Kd a multiple of 16, issued by the calling thread.
+__device__ __forceinline__ void mma_issue(uint32_t tmem, const unsigned char *A, const unsigned char *B, int Kd, int N)
+{
+    const uint32_t idesc = mma_idesc(N), sbo = (uint32_t)(Kd >> 3) * 128u;
+    for (int kk = 0; kk < Kd / 16; ++kk) {
+        const uint64_t ad = smem_desc(su32(A) + kk * 256, 128, sbo);
+        const uint64_t bd = smem_desc(su32(B) + kk * 256, 128, sbo);
+        const uint32_t acc = kk > 0 ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(mbar)));
+}
+
+// Bounded wait for the mbarrier phase `parity`; false when it expired.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kTcWaitLimit && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(su32(mbar)), "r"(parity));
+    return done != 0;
+}
+
+// Eight FP32 columns [col, col + 8) of this warp's 32 TMEM lanes: v[j] = row's column col + j.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;"); }
+
+__device__ __forceinline__ float eval32_rt(int fid, int d, const IntegrandParams &ip, const float *x);
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ mirror
+bool tc_layout(const Shape &S, TcFlow &F)
+{
+    if (S.L > kFMaxLayers || S.H > 128) return false;
+    std::memset(&F, 0, sizeof(F));
+    F.L = S.L;
+    F.H = S.H;
+    F.K = S.K;
+    F.SW = (2 * S.K + 1 + 7) & ~7;
+    long long pos = 0;
+    uint32_t off = 0;
+    for (int l = 0; l < S.L; ++l) {
+        const LayerDesc D = describe(S, l, pos);
+        TcLayer &Y = F.lay[l];
+        Y.nA = D.nA;
+        Y.nB = D.nB;
+        for (int i = 0; i < kMaxAB; ++i) {
+            Y.A[i] = D.A[i];
+            Y.B[i] = D.B[i];
+        }
+        Y.N3 = round16(D.nB * F.SW);
+        if (Y.N3 > kTcCols) return false;
+        Y.pW1 = (uint32_t)D.offW1;
+        Y.pb1 = (uint32_t)D.offb1;
+        Y.pW2 = (uint32_t)D.offW2;
+        Y.pb2 = (uint32_t)D.offb2;
+        Y.pW3 = (uint32_t)D.offW3;
+        Y.pb3 = (uint32_t)D.offb3;
+        uint32_t b = 2u * S.H * 16u;                  // W1: H x 16
+        Y.oW2 = b;
+        b += 2u * S.H * S.H;                          // W2: H x H
+        Y.oW3 = b;
+        b += 2u * (uint32_t)Y.N3 * S.H;               // W3: N3 x H
+        Y.ob1 = b;
+        b += 4u * S.H;
+        Y.ob2 = b;
+        b += 4u * S.H;
+        Y.ob3 = b;
+        b += 4u * (uint32_t)Y.N3;
+        b = (b + 15u) & ~15u;
+        Y.bytes = b;
+        Y.off = off;
+        off += b;
+        F.max_bytes = std::max(F.max_bytes, b);
+    }
+    F.total_bytes = off;
+    return true;
+}
+
+namespace {
+
+// The bf16 mirror in the tcgen05 operand layout (blockIdx.y = layer).
+__global__ void tc_mirror_kernel(const TcFlow F, const float *__restrict__ p, unsigned char *__restrict__ mirror)
+{
+    const TcLayer &Y = F.lay[blockIdx.y];
+    const int H = F.H, no = 2 * F.K + 1, SW = F.SW;
+    unsigned char *base = mirror + Y.off;
+    const int n1 = H * 16, n2 = H * H, n3 = Y.N3 * H;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 + n2 + n3 + 2 * H + Y.N3; e += gridDim.x * blockDim.x) {
+        if (e < n1) {
+            const int r = e / 16, c = e % 16;
+            *reinterpret_cast<__nv_bfloat16 *>(base + cm_off(r, c, 16)) =
+                __float2bfloat16_rn(c < Y.nA ? p[Y.pW1 + r * Y.nA + c] : 0.f);
+        } else if (e < n1 + n2) {
+            const int f = e - n1, r = f / H, c = f % H;
+            *reinterpret_cast<__nv_bfloat16 *>(base + Y.oW2 + cm_off(r, c, H)) = __float2bfloat16_rn(p[Y.pW2 + r * H + c]);
+        } else if (e < n1 + n2 + n3) {
+            const int f = e - n1 - n2, r = f / H, c = f % H, j = r / SW, k = r % SW;
+            const float v = (j < Y.nB && k < no) ? p[Y.pW3 + (j * no + k) * H + c] : 0.f;
+            *reinterpret_cast<__nv_bfloat16 *>(base + Y.oW3 + cm_off(r, c, H)) = __float2bfloat16_rn(v);
+        } else if (e < n1 + n2 + n3 + H) {
+            const int f = e - n1 - n2 - n3;
+            reinterpret_cast<float *>(base + Y.ob1)[f] = p[Y.pb1 + f];
+        } else if (e < n1 + n2 + n3 + 2 * H) {
+            const int f = e - n1 - n2 - n3 - H;
+            reinterpret_cast<float *>(base + Y.ob2)[f] = p[Y.pb2 + f];
+        } else {
+            const int f = e - n1 - n2 - n3 - 2 * H, j = f / SW, k = f % SW;
+            reinterpret_cast<float *>(base + Y.ob3)[f] = (j < Y.nB && k < no) ? p[Y.pb3 + j * no + k] : 0.f;
+        }
+    }
+}
+
+// Bias + ReLU of this thread's TMEM row [col, col + n) into the bf16 operand row of an
+// [128 x n] K-major core-matrix matrix.
+__device__ __forceinline__ void relu_row(uint32_t taddr, const float *bias, unsigned char *op, int row, int n)
+{
+    for (int c0 = 0; c0 < n; c0 += 8) {
+        float v[8];
+        tmem_ld8(taddr + (uint32_t)c0, v);
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            w[j] = pack_bf16(fmaxf(v[2 * j] + bias[c0 + 2 * j], 0.f), fmaxf(v[2 * j + 1] + bias[c0 + 2 * j + 1], 0.f));
+        *reinterpret_cast<uint4 *>(op + cm_off(row, c0, n)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+}  // namespace
+
+// Samples [i0, i0 + n) of one iteration: x (optional), log q (optional), w = (f / F) / q.
+template <int H, int K>
+__global__ void __launch_bounds__(kTcRows, 1)
+    flow_sample_tc_kernel(const TcFlow F, const unsigned char *__restrict__ mirror, const TcSample S,
+                          const IntegrandParams ip, long long i0, long long n, float *__restrict__ x_out,
+                          float *__restrict__ lq_out, float *__restrict__ w_out, int *__restrict__ err)
+{
+    constexpr int SW = (2 * K + 1 + 7) & ~7;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_holder;
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x, warp = tid >> 5, d = S.d, HS = d | 1;
+    unsigned char *wbuf = smem;                                   // F.max_bytes
+    unsigned char *A1 = smem + ((F.max_bytes + 1023u) & ~1023u);  // 128 x 16 bf16
+    unsigned char *A2 = A1 + kTcRows * 16 * 2;                    // 128 x H bf16 (also GEMM-3 operand)
+    float *hs = reinterpret_cast<float *>(A2 + kTcRows * H * 2);  // 128 x HS
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_holder)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    before_sync();
+    __syncthreads();
+    after_sync();
+    const uint32_t tmem = tmem_holder;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = true;
+    float *hr = hs + tid * HS;
+    const float ig = 1.0f / (float)S.g;
+    const long long ntiles = (n + kTcRows - 1) / kTcRows;
+
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long jr = tile * kTcRows + tid;   // this thread's sample, relative to i0
+        if (jr < n) {
+            const long long i = i0 + jr;
+            const uint32_t tc = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
+            uint32_t t = tc;
+            for (int a = 0; a < d; ++a) {
+                const uint32_t c = t % S.g;
+                t /= S.g;
+                const Words4 r = philox4x32_10(tc, q, S.ctr2_hi | (uint32_t)(a >> 2), S.job, S.key0, S.key1);
+                const uint32_t w = (a & 3) == 0 ? r.x : (a & 3) == 1 ? r.y : (a & 3) == 2 ? r.z : r.w;
+                const float u = (float)(w & 0x7FFFFFu) * 1.1920928955078125e-7f;
+                hr[a] = fminf(((float)c + u) * ig, 0.99999994f);
+            }
+        } else {
+            for (int a = 0; a < d; ++a) hr[a] = 0.5f;
+        }
+        float lq = 0.f;
+        for (int l = F.L - 1; l >= 0 && ok; --l) {
+            const TcLayer &Y = F.lay[l];
+            // the previous layer's MMAs and TMEM reads are complete: refill the weights
+            before_sync();
+            __syncthreads();
+            after_sync();
+            {
+                const uint4 *src = reinterpret_cast<const uint4 *>(mirror + Y.off);
+                uint4 *dst = reinterpret_cast<uint4 *>(wbuf);
+                for (uint32_t e = tid; e < Y.bytes / 16u; e += kTcRows) dst[e] = src[e];
+            }
+            const unsigned char *W1 = wbuf, *W2 = wbuf + Y.oW2, *W3 = wbuf + Y.oW3;
+            const float *b1 = reinterpret_cast<const float *>(wbuf + Y.ob1);
+            const float *b2 = reinterpret_cast<const float *>(wbuf + Y.ob2);
+            const float *b3 = reinterpret_cast<const float *>(wbuf + Y.ob3);
+            {   // GEMM-1 operand: this row's kept coordinates, columns >= |A| zero
+                uint32_t w[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c0 = 2 * j, c1 = 2 * j + 1;
+                    w[j] = pack_bf16(c0 < Y.nA ? hr[Y.A[c0]] : 0.f, c1 < Y.nA ? hr[Y.A[c1]] : 0.f);
+                }
+                *reinterpret_cast<uint4 *>(A1 + cm_off(tid, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4 *>(A1 + cm_off(tid, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            proxy_fence();
+            before_sync();
+            __syncthreads();
+            after_sync();
+            if (tid == 0) {
+                mma_issue(tmem, A1, W1, 16, H);
+                mma_commit(&mbar);
+            }
+            if (!__syncthreads_and(mbar_wait(&mbar, phase))) { ok = false; break; }
+            phase ^= 1u;
+            after_sync();
+            relu_row(lane_base, b1, A2, tid, H);        // D1 at columns [0, H)
+            proxy_fence();
+            before_sync();
+            __syncthreads();
+            after_sync();
+            if (tid == 0) {
+                mma_issue(tmem + H, A2, W2, H, H);      // D2 at columns [H, 2H)
+                mma_commit(&mbar);
+            }
+            if (!__syncthreads_and(mbar_wait(&mbar, phase))) { ok = false; break; }   // GEMM 2 has read A2
+            phase ^= 1u;
+            after_sync();
+            relu_row(lane_base + H, b2, A2, tid, H);    // GEMM-3 operand over the GEMM-2 operand
+            proxy_fence();
+            before_sync();
+            __syncthreads();
+            after_sync();
+            if (tid == 0) {
+                mma_issue(tmem, A2, W3, H, Y.N3);       // D3 at columns [0, N3)
+                mma_commit(&mbar);
+            }
+            if (!__syncthreads_and(mbar_wait(&mbar, phase))) { ok = false; break; }
+            phase ^= 1u;
+            after_sync();
+            for (int j = 0; j < Y.nB; ++j) {
+                float raw[SW];
+#pragma unroll
+                for (int c0 = 0; c0 < SW; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(lane_base + (uint32_t)(j * SW + c0), v);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) raw[c0 + u] = v[u] + b3[j * SW + c0 + u];
+                }
+                float out, qv;
+                pq_transform<K>(raw, hr[Y.B[j]], 1, out, qv);
+                hr[Y.B[j]] = out;
+                lq += __logf(qv);
+            }
+        }
+        if (!ok) break;
+        if (jr < n) {
+            float x[kDMax];
+            for (int a = 0; a < d; ++a) x[a] = hr[a];
+            w_out[jr] = eval32_rt(S.fid, d, ip, x) * __expf(-lq);
+            if (x_out)
+                for (int a = 0; a < d; ++a) x_out[jr * d + a] = x[a];
+            if (lq_out) lq_out[jr] = lq;
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    before_sync();
+    __syncthreads();
+    after_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
+namespace {
+
+// The integrand f / F in single precision for a runtime dimension (the FP32-eval forms).
+__device__ __forceinline__ float eval32_rt(int fid, int d, const IntegrandParams &ip, const float *x)
+{
+    float s = 0.f, s2 = 0.f, prod = 1.f;
+    bool inside = true;
+    switch (fid) {
+    case kOscillatory: {
+        for (int i = 0; i < d; ++i) s = fmaf(ip.fa[i], x[i], s);
+        const float t = ip.fc + s;
+        return __cosf(6.28318530717958647692f * (t - rintf(t)));
+    }
+    case kProductPeak:
+        for (int i = 0; i < d; ++i) {
+            const float v = ip.fa[i] * (x[i] - ip.fu[i]);
+            prod *= fmaf(v, v, 1.0f);
+        }
+        return __frcp_rn(prod);
+    case kCornerPeak: {
+        for (int i = 0; i < d; ++i) s = fmaf(ip.fa[i], x[i], s);
+        const float b = 1.0f + s;
+        float r = 1.0f;
+        for (int e = 0; e <= d; ++e) r *= b;
+        return 1.0f / r;
+    }
+    case kGaussian:
+        for (int i = 0; i < d; ++i) {
+            const float v = ip.fa[i] * (x[i] - ip.fu[i]);
+            s = fmaf(v, v, s);
+        }
+        return ex2_approx(-s);
+    case kC0:
+        for (int i = 0; i < d; ++i) s = fmaf(ip.fa[i], fabsf(x[i] - ip.fu[i]), s);
+        return ex2_approx(-s);
+    case kDiscontinuous:
+        for (int i = 0; i < d; ++i) {
+            inside = inside && (x[i] < ip.fu[i]);
+            s = fmaf(ip.fa[i], x[i] - ip.fb[i], s);
+        }
+        return inside ? ex2_approx(s) : 0.f;
+    case kAddition:
+        for (int i = 0; i < d; ++i) s += x[i];
+        return s;
+    case kDoubleGaussian:
+        for (int i = 0; i < d; ++i) {
+            const float v1 = ip.fa[i] * (x[i] - ip.fu[i]);
+            const float v2 = ip.fa[i] * (x[i] - ip.fb[i]);
+            s = fmaf(v1, v1, s);
+            s2 = fmaf(v2, v2, s2);
+        }
+        return ex2_approx(-s) + ex2_approx(-s2);
+    case kRotatedGaussian: {
+        for (int i = 0; i < d; ++i) {
+            float r = 0.f;
+            for (int j = 0; j < d; ++j) r = fmaf(ip.fm[i * d + j], x[j] - ip.fu[j], r);
+            s = fmaf(x[i] - ip.fu[i], r, s);
+        }
+        return ex2_approx(-s);
+    }
+    default:
+        return 1.0f;
+    }
+}
+
+template <int H, int K>
+int launch_tc_hk(const TcFlow &F, const unsigned char *mirror, const TcSample &S, const IntegrandParams &ip,
+                 long long i0, long long n, float *x, float *lq, float *w, int *err, cudaStream_t s)
+{
+    static int optin_c[64], sms_c[64];
+    static std::atomic<uint64_t> known{0};
+    int dev = 0, optin = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 64 && (known.load(std::memory_order_acquire) >> dev & 1u)) {
+        optin = optin_c[dev];
+        sms = sms_c[dev];
+    } else {
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, flow_sample_tc_kernel<H, K>);
+        if (e == cudaSuccess) {
+            optin -= (int)fa.sharedSizeBytes;   // the opt-in limit covers static and dynamic shared memory
+            e = cudaFuncSetAttribute(flow_sample_tc_kernel<H, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        if (dev < 64) {
+            optin_c[dev] = optin;
+            sms_c[dev] = sms;
+            known.fetch_or(1ull << dev, std::memory_order_release);
+        }
+    }
+    const int HS = S.d | 1;
+    size_t smem = (size_t)((F.max_bytes + 1023u) & ~1023u) + (size_t)kTcRows * 16 * 2 + (size_t)kTcRows * H * 2 +
+                  sizeof(float) * (size_t)kTcRows * HS;
+    // TMEM holds 512 columns an SM and a CTA takes kTcCols: a third resident CTA would wait in
+    // tcgen05.alloc, so shared memory is padded to keep at most two on an SM
+    smem = std::max(smem, (size_t)80 * 1024);
+    if (smem + 1024 > (size_t)optin) return kFusedUnsupported;
+    const int per_sm = 512 / kTcCols;
+    const long long tiles = (n + kTcRows - 1) / kTcRows;
+    const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
+    flow_sample_tc_kernel<H, K><<<(unsigned)grid, kTcRows, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w, err);
+    return cuda_status(cudaGetLastError());
+}
+
+template <int H>
+int launch_tc_h(const TcFlow &F, const unsigned char *mirror, const TcSample &S, const IntegrandParams &ip,
+                long long i0, long long n, float *x, float *lq, float *w, int *err, cudaStream_t s)
+{
+    switch (F.K) {
+    case 4: return launch_tc_hk<H, 4>(F, mirror, S, ip, i0, n, x, lq, w, err, s);
+    case 8: return launch_tc_hk<H, 8>(F, mirror, S, ip, i0, n, x, lq, w, err, s);
+    case 16: return launch_tc_hk<H, 16>(F, mirror, S, ip, i0, n, x, lq, w, err, s);
+    default: return kFusedUnsupported;   // K = 32: the raw row does not fit the registers well
+    }
+}
+
+}  // namespace
+
+int build_tc_mirror(const TcFlow &F, const float *d_params, unsigned char *mirror, cudaStream_t s)
+{
+    tc_mirror_kernel<<<dim3(64, (unsigned)F.L), 256, 0, s>>>(F, d_params, mirror);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_flow_sample_tc(const TcFlow &F, const unsigned char *mirror, const TcSample &S, const IntegrandParams &ip,
+                          long long i0, long long n, float *x, float *lq, float *w, int *err, cudaStream_t s)
+{
+    if (n <= 0) return MCUBES_OK;
+    switch (F.H) {
+    case 32: return launch_tc_h<32>(F, mirror, S, ip, i0, n, x, lq, w, err, s);
+    case 64: return launch_tc_h<64>(F, mirror, S, ip, i0, n, x, lq, w, err, s);
+    case 128: return launch_tc_h<128>(F, mirror, S, ip, i0, n, x, lq, w, err, s);
+    default: return kFusedUnsupported;
+    }
+}
+
+}  // namespace flow
+}  // namespace mcubes

@@ -549,7 +549,11 @@ int raise_smem_limit(Kern kern, int optin, std::atomic<uint64_t> &done)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 64 && (done.load(std::memory_order_acquire) >> dev & 1u)) return MCUBES_OK;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess)
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return cuda_status(e);
+    // the opt-in limit covers static and dynamic shared memory
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)) !=
+        cudaSuccess)
         return cuda_status(e);
     if (dev < 64) done.fetch_or(1ull << dev, std::memory_order_release);
     return MCUBES_OK;

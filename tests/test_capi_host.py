@@ -155,19 +155,26 @@ def test_integrate_range_argument_checks(capi):
 
 
 def test_flow_sample_work_bytes_and_argument_checks(capi):
-    """The fused sampler's scratch is the bf16 weight mirror: per layer W1 [H][24], W2 [H][H+8],
-    W3 [|B| SW rounded up to 16][H+8] (bf16) and the biases (FP32), each 16-byte aligned; SW = 2K+1
-    rounded up to 8.
+    """The fused samplers' scratch holds the larger of two bf16 weight mirrors, then a 256-byte
+    flag: the mma.sync layout per layer (W1 [H][24], W2 [H][H+8], W3 [N3][H+8] bf16, biases FP32,
+    16-byte aligned) and the tcgen05 core-matrix layout (W1 [H][16], W2 [H][H], W3 [N3][H] bf16,
+    b1, b2, b3 [N3] FP32), with N3 = |B| SW rounded up to 16, SW = 2K+1 rounded up to 8.
     Argument and workspace checks answer before any CUDA call."""
+    al = lambda b, q=16: (b + q - 1) // q * q
+
     def layer_bytes(H, nB, K):
-        al = lambda b: (b + 15) // 16 * 16
-        SW = (2 * K + 1 + 7) // 8 * 8
-        r16 = lambda v: (v + 15) // 16 * 16
-        return al(2 * H * 24) + al(2 * H * (H + 8)) + al(2 * r16(nB * SW) * (H + 8)) + 2 * al(4 * H) + al(4 * nB * SW)
-    assert capi.flow_sample_work_bytes(capi.flow_shape(8, 4, 64, 16)) == 4 * layer_bytes(64, 4, 16)
+        SW = al(2 * K + 1, 8)
+        return al(2 * H * 24) + al(2 * H * (H + 8)) + al(2 * al(nB * SW) * (H + 8)) + 2 * al(4 * H) + al(4 * nB * SW)
+
+    def tc_layer_bytes(H, nB, K):
+        N3 = al(nB * al(2 * K + 1, 8))
+        return al(32 * H + 2 * H * H + 2 * N3 * H + 8 * H + 4 * N3)
+
+    def scratch(H, K, nbs):
+        return al(max(sum(layer_bytes(H, nb, K) for nb in nbs), sum(tc_layer_bytes(H, nb, K) for nb in nbs)), 256) + 256
+    assert capi.flow_sample_work_bytes(capi.flow_shape(8, 4, 64, 16)) == scratch(64, 16, (4, 4, 4, 4))
     # d = 7: |B| = 4, 3, 3, 4 (upper half, lower half, odd axes, even axes)
-    n7 = capi.flow_sample_work_bytes(capi.flow_shape(7, 4, 32, 8))
-    assert n7 == sum(layer_bytes(32, nb, 8) for nb in (4, 3, 3, 4))
+    assert capi.flow_sample_work_bytes(capi.flow_shape(7, 4, 32, 8)) == scratch(32, 8, (4, 3, 3, 4))
     assert capi.flow_sample_work_bytes(capi.flow_shape(8, 17, 64, 16)) == 0    # more than 16 layers
     assert capi.flow_sample_work_bytes(capi.flow_shape(8, 4, 48, 16)) == 0     # unsupported width
     par = W.genz_params(W.GAUSSIAN, 8)
