@@ -1,7 +1,7 @@
 // Fused flow sampler on the fifth-generation tensor cores (tcgen05, TMEM accumulators).
 //
-// A 128-thread CTA takes 128 samples at a time: thread t owns sample row t, which is also TMEM
-// lane t of the accumulators. Per coupling layer (sampling direction):
+// A 256-thread CTA takes 128 samples at a time: sample row r is TMEM lane r of the accumulators,
+// served by threads r and r + 128. Per coupling layer (sampling direction):
 //   1. each thread writes its row's kept coordinates (bf16) into the GEMM-1 operand in shared
 //      memory; one thread issues tcgen05.mma D1 = A1 W1^T (M = 128, N = H, K = 16) and commits
 //      to an mbarrier;
@@ -193,11 +193,11 @@ __global__ void tc_mirror_kernel(const TcFlow F, const float *__restrict__ p, un
     }
 }
 
-// Bias + ReLU of this thread's TMEM row [col, col + n) into the bf16 operand row of an
-// [128 x n] K-major core-matrix matrix.
-__device__ __forceinline__ void relu_row(uint32_t taddr, const float *bias, unsigned char *op, int row, int n)
+// Bias + ReLU of this thread's TMEM row, columns [half n/2, (half+1) n/2) of [col, col + n), into
+// the bf16 operand row of an [128 x n] K-major core-matrix matrix.
+__device__ __forceinline__ void relu_half(uint32_t taddr, const float *bias, unsigned char *op, int row, int n, int half)
 {
-    for (int c0 = 0; c0 < n; c0 += 8) {
+    for (int c0 = half * (n >> 1); c0 < (half + 1) * (n >> 1); c0 += 8) {
         float v[8];
         tmem_ld8(taddr + (uint32_t)c0, v);
         uint32_t w[4];
@@ -211,8 +211,13 @@ __device__ __forceinline__ void relu_row(uint32_t taddr, const float *bias, unsi
 }  // namespace
 
 // Samples [i0, i0 + n) of one iteration: x (optional), log q (optional), w = (f / F) / q.
+// 256 threads: thread t serves row t mod 128 (TMEM lane; warps w and w + 4 read the same lanes),
+// and its half h = t / 128 takes columns [h H/2, (h+1) H/2) of the ReLU epilogues and every other
+// transformed axis (j = h, h + 2, ...) of the coupling transforms.
+constexpr int kTcThreads = 2 * kTcRows;
+
 template <int H, int K>
-__global__ void __launch_bounds__(kTcRows, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     flow_sample_tc_kernel(const TcFlow F, const unsigned char *__restrict__ mirror, const TcSample S,
                           const IntegrandParams ip, long long i0, long long n, float *__restrict__ x_out,
                           float *__restrict__ lq_out, float *__restrict__ w_out, int *__restrict__ err)
@@ -221,7 +226,8 @@ __global__ void __launch_bounds__(kTcRows, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_holder;
     __shared__ __align__(8) uint64_t mbar;
-    const int tid = threadIdx.x, warp = tid >> 5, d = S.d, HS = d | 1;
+    __shared__ float lq_half[kTcRows];
+    const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), half = tid >> 7, d = S.d, HS = d | 1;
     unsigned char *wbuf = smem;                                   // F.max_bytes
     unsigned char *A1 = smem + ((F.max_bytes + 1023u) & ~1023u);  // 128 x 16 bf16
     unsigned char *A2 = A1 + kTcRows * 16 * 2;                    // 128 x H bf16 (also GEMM-3 operand)
@@ -239,55 +245,56 @@ __global__ void __launch_bounds__(kTcRows, 1)
     __syncthreads();
     after_sync();
     const uint32_t tmem = tmem_holder;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     uint32_t phase = 0;
     bool ok = true;
-    float *hr = hs + tid * HS;
+    float *hr = hs + row * HS;
     const float ig = 1.0f / (float)S.g;
     const long long ntiles = (n + kTcRows - 1) / kTcRows;
 
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const long long jr = tile * kTcRows + tid;   // this thread's sample, relative to i0
-        if (jr < n) {
-            const long long i = i0 + jr;
-            const uint32_t tc = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
-            uint32_t t = tc;
-            for (int a = 0; a < d; ++a) {
-                const uint32_t c = t % S.g;
-                t /= S.g;
-                const Words4 r = philox4x32_10(tc, q, S.ctr2_hi | (uint32_t)(a >> 2), S.job, S.key0, S.key1);
-                const uint32_t w = (a & 3) == 0 ? r.x : (a & 3) == 1 ? r.y : (a & 3) == 2 ? r.z : r.w;
-                const float u = (float)(w & 0x7FFFFFu) * 1.1920928955078125e-7f;
-                hr[a] = fminf(((float)c + u) * ig, 0.99999994f);
+        const long long jr = tile * kTcRows + row;   // this row's sample, relative to i0
+        if (half == 0) {
+            if (jr < n) {
+                const long long i = i0 + jr;
+                const uint32_t tc = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
+                uint32_t t = tc;
+                for (int a = 0; a < d; ++a) {
+                    const uint32_t c = t % S.g;
+                    t /= S.g;
+                    const Words4 r = philox4x32_10(tc, q, S.ctr2_hi | (uint32_t)(a >> 2), S.job, S.key0, S.key1);
+                    const uint32_t w = (a & 3) == 0 ? r.x : (a & 3) == 1 ? r.y : (a & 3) == 2 ? r.z : r.w;
+                    const float u = (float)(w & 0x7FFFFFu) * 1.1920928955078125e-7f;
+                    hr[a] = fminf(((float)c + u) * ig, 0.99999994f);
+                }
+            } else {
+                for (int a = 0; a < d; ++a) hr[a] = 0.5f;
             }
-        } else {
-            for (int a = 0; a < d; ++a) hr[a] = 0.5f;
         }
         float lq = 0.f;
         for (int l = F.L - 1; l >= 0 && ok; --l) {
             const TcLayer &Y = F.lay[l];
-            // the previous layer's MMAs and TMEM reads are complete: refill the weights
+            // the previous layer's MMAs, TMEM reads and coordinate updates are complete
             before_sync();
             __syncthreads();
             after_sync();
             {
                 const uint4 *src = reinterpret_cast<const uint4 *>(mirror + Y.off);
                 uint4 *dst = reinterpret_cast<uint4 *>(wbuf);
-                for (uint32_t e = tid; e < Y.bytes / 16u; e += kTcRows) dst[e] = src[e];
+                for (uint32_t e = tid; e < Y.bytes / 16u; e += kTcThreads) dst[e] = src[e];
             }
             const unsigned char *W1 = wbuf, *W2 = wbuf + Y.oW2, *W3 = wbuf + Y.oW3;
             const float *b1 = reinterpret_cast<const float *>(wbuf + Y.ob1);
             const float *b2 = reinterpret_cast<const float *>(wbuf + Y.ob2);
             const float *b3 = reinterpret_cast<const float *>(wbuf + Y.ob3);
-            {   // GEMM-1 operand: this row's kept coordinates, columns >= |A| zero
-                uint32_t w[8];
+            {   // GEMM-1 operand: this row's kept coordinates, columns >= |A| zero (each half 8 columns)
+                uint32_t w[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int c0 = 2 * j, c1 = 2 * j + 1;
+                for (int j = 0; j < 4; ++j) {
+                    const int c0 = 8 * half + 2 * j, c1 = c0 + 1;
                     w[j] = pack_bf16(c0 < Y.nA ? hr[Y.A[c0]] : 0.f, c1 < Y.nA ? hr[Y.A[c1]] : 0.f);
                 }
-                *reinterpret_cast<uint4 *>(A1 + cm_off(tid, 0, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4 *>(A1 + cm_off(tid, 8, 16)) = make_uint4(w[4], w[5], w[6], w[7]);
+                *reinterpret_cast<uint4 *>(A1 + cm_off(row, 8 * half, 16)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
             proxy_fence();
             before_sync();
@@ -300,31 +307,31 @@ __global__ void __launch_bounds__(kTcRows, 1)
             if (!__syncthreads_and(mbar_wait(&mbar, phase))) { ok = false; break; }
             phase ^= 1u;
             after_sync();
-            relu_row(lane_base, b1, A2, tid, H);        // D1 at columns [0, H)
+            relu_half(lane_base, b1, A2, row, H, half);            // D1 at columns [0, H)
             proxy_fence();
             before_sync();
             __syncthreads();
             after_sync();
             if (tid == 0) {
-                mma_issue(tmem + H, A2, W2, H, H);      // D2 at columns [H, 2H)
+                mma_issue(tmem + H, A2, W2, H, H);                 // D2 at columns [H, 2H)
                 mma_commit(&mbar);
             }
             if (!__syncthreads_and(mbar_wait(&mbar, phase))) { ok = false; break; }   // GEMM 2 has read A2
             phase ^= 1u;
             after_sync();
-            relu_row(lane_base + H, b2, A2, tid, H);    // GEMM-3 operand over the GEMM-2 operand
+            relu_half(lane_base + H, b2, A2, row, H, half);        // GEMM-3 operand over the GEMM-2 operand
             proxy_fence();
             before_sync();
             __syncthreads();
             after_sync();
             if (tid == 0) {
-                mma_issue(tmem, A2, W3, H, Y.N3);       // D3 at columns [0, N3)
+                mma_issue(tmem, A2, W3, H, Y.N3);                  // D3 at columns [0, N3)
                 mma_commit(&mbar);
             }
             if (!__syncthreads_and(mbar_wait(&mbar, phase))) { ok = false; break; }
             phase ^= 1u;
             after_sync();
-            for (int j = 0; j < Y.nB; ++j) {
+            for (int j = half; j < Y.nB; j += 2) {
                 float raw[SW];
 #pragma unroll
                 for (int c0 = 0; c0 < SW; c0 += 8) {
@@ -340,7 +347,10 @@ __global__ void __launch_bounds__(kTcRows, 1)
             }
         }
         if (!ok) break;
-        if (jr < n) {
+        if (half == 1) lq_half[row] = lq;
+        __syncthreads();
+        if (half == 0 && jr < n) {
+            lq += lq_half[row];
             float x[kDMax];
             for (int a = 0; a < d; ++a) x[a] = hr[a];
             w_out[jr] = eval32_rt(S.fid, d, ip, x) * __expf(-lq);
@@ -459,7 +469,7 @@ int launch_tc_hk(const TcFlow &F, const unsigned char *mirror, const TcSample &S
     const int per_sm = 512 / kTcCols;
     const long long tiles = (n + kTcRows - 1) / kTcRows;
     const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
-    flow_sample_tc_kernel<H, K><<<(unsigned)grid, kTcRows, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w, err);
+    flow_sample_tc_kernel<H, K><<<(unsigned)grid, kTcThreads, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w, err);
     return cuda_status(cudaGetLastError());
 }
 
