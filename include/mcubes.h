@@ -93,7 +93,9 @@ typedef struct mcubes_result {
 
 /* Launch tuning. Zero fields take the defaults. */
 typedef struct mcubes_tuning {
-    int32_t block_threads;    /* threads per V-Sample block (64..1024, multiple of 32); default 256 */
+    int32_t block_threads;    /* threads per V-Sample block (64..256, multiple of 32). Default: 256, and
+                                 1024 for FP32 adjusting iterations, whose one block per SM holds the
+                                 lane-interleaved histogram copies */
     int32_t blocks_per_sm;    /* resident blocks per SM to launch (persistent grid); default: occupancy */
     int32_t reserved[6];
 } mcubes_tuning;

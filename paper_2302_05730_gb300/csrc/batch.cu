@@ -221,6 +221,7 @@ struct Plan {
         int st = make_req(nullptr, req);
         if (st) return st;
         req.threads = c.shape.threads;
+        req.user_threads = 1;
         req.blocks_per_sm = 0;
         return cuda_status((cudaError_t)batch_launcher_for(prec, c.fid)(c.d, d_jobs, c.d_tiles, c.n_tiles, it, parity,
                                                                          adjust, c.shape.hist, req, s));

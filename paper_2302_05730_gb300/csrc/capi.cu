@@ -227,12 +227,14 @@ int make_req(const mcubes_tuning *tune, LaunchReq &req)
     MC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     req.num_sms = sms;
     req.threads = kMaxBlockThreads;
+    req.user_threads = 0;
     req.blocks_per_sm = 0;
     if (tune) {
         if (tune->block_threads) {
             if (tune->block_threads < 64 || tune->block_threads > kMaxBlockThreads || tune->block_threads % 32)
                 return MCUBES_ERR_INVALID_ARG;
             req.threads = tune->block_threads;
+            req.user_threads = 1;
         }
         if (tune->blocks_per_sm < 0 || tune->blocks_per_sm > 64) return MCUBES_ERR_INVALID_ARG;
         req.blocks_per_sm = tune->blocks_per_sm;

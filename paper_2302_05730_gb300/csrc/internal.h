@@ -30,6 +30,7 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
 // Launch request of one V-Sample kernel.
 struct LaunchReq {
     int threads;          // threads per block
+    int user_threads;     // 1: threads was requested (else each kernel takes its default size)
     int blocks_per_sm;    // 0: as many as fit (occupancy)
     int num_sms;          // SMs of the device
 };

@@ -12,6 +12,10 @@
 //   5. on adjusting iterations, the bin contributions w^2, added to a block-private
 //      shared-memory histogram.
 //
+// Kernel instances per (d, integrand, precision): HR = 0 for frozen iterations (no histogram
+// code at all) and HR >= 1 copies of the histogram for adjusting ones. The FP32 adjusting
+// kernel keeps HR lane-interleaved copies (see hist_replicas_f32).
+//
 // Per block at the end:
 //   - warp-shuffle and shared-memory reduction of the thread sums, then two FP64 global
 //     atomics into sums[0..1] (Algorithm 2's AtomicAdd into r);
@@ -51,11 +55,24 @@ struct Prec<true> {
     using T2 = float2;
 };
 
-// Shared-memory bytes of one block: the (B, Delta) table and, when adjusting, the histogram.
+// Shared-memory bytes of one block: the (B, Delta) table and hr copies of the histogram.
 template <bool F32>
-__host__ __device__ constexpr size_t vsample_smem_bytes(int d, bool adjust)
+__host__ __device__ constexpr size_t vsample_smem_bytes(int d, int hr)
 {
-    return (size_t)d * kNB * (sizeof(typename Prec<F32>::T2) + (adjust ? sizeof(typename Prec<F32>::T) : 0));
+    return (size_t)d * kNB * (sizeof(typename Prec<F32>::T2) + (size_t)hr * sizeof(typename Prec<F32>::T));
+}
+
+// Histogram copies of the single-job FP32 adjusting kernel. Copy g = lane mod HR holds bin e at
+// word e HR + g, so within one warp-wide atomic only the 32 / HR lanes of a copy can meet in a
+// bank, over that copy's 32 / HR banks. Random bins (which the VEGAS map draws by construction)
+// then collide about half as often: 3.1 FP32 shared atomics per SM clock at HR = 8 against 2.2
+// with one copy, measured on GB300 at 1024 threads per SM. The table and 8 copies fit one
+// 1024-thread block per SM up to d = 11; larger d keeps 4 copies.
+constexpr int kReplThreads = 1024;
+template <int D>
+constexpr int hist_replicas_f32()
+{
+    return vsample_smem_bytes<true>(D, 8) + 2048 <= (size_t)227 * 1024 ? 8 : 4;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -85,6 +102,20 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch
     }
 }
 
+// Shared-memory accesses by 32-bit shared-window address (FP32 path): the table and histogram
+// addresses come straight from the bit pattern of the floored coordinate (below).
+__device__ __forceinline__ float2 lds_f32x2(uint32_t a)
+{
+    float2 v;
+    asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void red_add_f32(uint32_t a, float v)
+{
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 // Resident blocks per SM the FP32-eval kernels are compiled for (register budget 65536 /
 // (256 x blocks)): as many as the shared memory of an adjusting block allows, at most 4. The
 // kernel is bound by shared-memory latency and throughput, so more resident warps keep more
@@ -92,10 +123,10 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *scratch
 #ifndef MCUBES_MAX_MIN_BLOCKS
 #define MCUBES_MAX_MIN_BLOCKS 4
 #endif
-template <int D, bool F32>
+template <int D, bool F32, int HR = 1>
 constexpr int min_blocks_per_sm()
 {
-    if (!F32) return 1;
+    if (!F32 || HR > 1) return 1;
     const size_t smem = vsample_smem_bytes<F32>(D, true) + 1024;
     const int fit = (int)((size_t)(227 * 1024) / smem);
     const int b = fit < MCUBES_MAX_MIN_BLOCKS ? fit : MCUBES_MAX_MIN_BLOCKS;
@@ -109,10 +140,11 @@ struct ThreadSums {
     float cV = 0.0f, eV = 0.0f;     // ... and of the cube variances (times p (p-1))
 };
 
-// Stage a grid into shared memory as (B_k, Delta_k) pairs and clear the histogram. Block-wide.
+// Stage a grid into shared memory as (B_k, Delta_k) pairs and clear n_clear words of the
+// histogram. Block-wide.
 template <int D, bool F32>
 __device__ __forceinline__ void stage_grid(const double *grid, typename Prec<F32>::T2 *tab,
-                                           typename Prec<F32>::T *hist, bool clear_hist)
+                                           typename Prec<F32>::T *hist, int n_clear)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
@@ -125,8 +157,8 @@ __device__ __forceinline__ void stage_grid(const double *grid, typename Prec<F32
         v.x = (T)b0;
         v.y = (T)(b1 - b0);
         tab[e] = v;
-        if (clear_hist) hist[e] = T(0);
     }
+    for (int e = threadIdx.x; e < n_clear; e += blockDim.x) hist[e] = T(0);
     __syncthreads();
 }
 
@@ -147,15 +179,19 @@ __device__ __forceinline__ float histogram_scale(const VsampleParams &P)
 
 // Algorithm 2's loop over this thread's sub-cubes [t, t_end): draws, map, integrand, per-cube
 // statistics and bin contributions. kGlobalHist routes the contributions straight to the
-// job's global C (FP64 atomics) instead of the block's shared histogram.
-template <int D, int FID, bool F32, bool kGlobalHist>
+// job's global C (FP64 atomics) instead of the block's shared histogram; otherwise they go to
+// the HR-copy shared histogram, and HR = 0 compiles them out.
+template <int D, int FID, bool F32, bool kGlobalHist, int HR>
 __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t, const uint32_t t_end,
                                              const typename Prec<F32>::T2 *tab, typename Prec<F32>::T *hist,
                                              const float hsig, ThreadSums &acc)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
-    const bool adjust = P.adjust != 0;
+    static_assert(HR == 0 || HR == 1 || HR == 2 || HR == 4 || HR == 8, "histogram copies: 0, 1, 2, 4 or 8");
+    const bool adjust = (kGlobalHist || HR > 0) && P.adjust != 0;
+    // this lane's histogram copy, as a word offset
+    const int hcopy = HR > 1 ? (int)(threadIdx.x & (HR - 1)) : 0;
 
     // strata digits c_i (axis 0 fastest) and c_i - 1 in the path's precision
     uint32_t dig[D];
@@ -175,6 +211,12 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
     const T magic = F32 ? (T)8388608.0f : (T)4503599627370496.0;   // 2^23 / 2^52
     const uint32_t p = P.p;
     const float inv_p32 = (float)P.inv_p;
+    // FP32: kb = yn + 2^23 rounded down has bit pattern 0x4B000000 + k, so the byte address of
+    // table entry (i, k) is bits(kb) * 8 + tab_adj + i * kNB * 8, and that of this lane's
+    // histogram copy of bin (i, k) is bits(kb) * 4 HR + hist_adj + i * kNB * 4 HR (mod 2^32).
+    constexpr uint32_t kMagicBits = 0x4B000000u;
+    const uint32_t tab_adj = smem_addr(tab) - kMagicBits * 8u;
+    const uint32_t hist_adj = HR > 0 ? smem_addr(hist) + 4u * (uint32_t)hcopy - kMagicBits * (4u * (uint32_t)HR) : 0u;
     // global-histogram scale (FP32: (F / sigma)^2; FP64: 1, the contribution already carries nd^d)
     double gscale = 0.0;
     if constexpr (kGlobalHist) {
@@ -193,7 +235,8 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
             Integrand64<FID, D> f64;
             Integrand32<FID, D> f32;
             T J = T(1);
-            int kofs[D];
+            int kofs[D];        // bin index i nd + k (FP64 path, global histogram)
+            uint32_t haddr[D];  // shared address of the lane's histogram copy of the bin (FP32 path)
 
             constexpr int kDimsPerCall = F32 ? 4 : 2;
             constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
@@ -222,18 +265,25 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                         }
                         // floor(yn) for 0 <= yn < 2^23 (2^52): add the magic number rounding down
                         T kb;
-                        int k;
+                        T2 bw;
                         if constexpr (F32) {
                             kb = __fadd_rd(yn, magic);
-                            k = (int)(__float_as_uint(kb) & 0x7FFFFFu);
+                            const uint32_t kbits = __float_as_uint(kb);
+                            bw = lds_f32x2(kbits * 8u + (tab_adj + (uint32_t)(i * kNB * 8)));
+                            if constexpr (kGlobalHist) {
+                                kofs[i] = i * kNB + (int)(kbits - kMagicBits);
+                            } else if constexpr (HR > 0) {
+                                haddr[i] = kbits * (4u * (uint32_t)HR) + (hist_adj + (uint32_t)(i * kNB * 4 * HR));
+                            }
                             kb = __fsub_rn(kb, magic);
                         } else {
                             kb = __dadd_rd(yn, magic);
-                            k = __double2loint(kb);
+                            const int k = __double2loint(kb);
+                            bw = tab[i * kNB + k];
+                            kofs[i] = i * kNB + k;
                             kb = __dsub_rn(kb, magic);
                         }
                         const T delta = yn - kb;     // exact
-                        const T2 bw = tab[i * kNB + k];
                         T x;
                         if constexpr (F32) {
                             x = __fmaf_rn(bw.y, delta, bw.x);
@@ -247,7 +297,6 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                             // keep J near 1: fold nd^4 in after every fourth axis
                             if ((i & 3) == 3) J *= 6.25e10f;
                         }
-                        kofs[i] = i * kNB + k;
                     }
                 }
             }
@@ -290,9 +339,14 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                     const double hg = (double)h * gscale;
 #pragma unroll
                     for (int i = 0; i < D; ++i) atomicAdd(&P.C[kofs[i]], hg);
-                } else {
+                } else if constexpr (HR > 0) {
+                    if constexpr (F32) {
 #pragma unroll
-                    for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], h);
+                        for (int i = 0; i < D; ++i) red_add_f32(haddr[i], h);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i] * HR + hcopy], h);
+                    }
                 }
             }
         }
@@ -348,9 +402,9 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
 }
 
 // Block reduction of the thread sums, two FP64 global atomics into P.sums (Algorithm 2,
-// AtomicAdd into r), then the flush of the private histogram into P.C. Block-wide; leaves the
-// histogram free for reuse (ends with a barrier).
-template <int D, bool F32>
+// AtomicAdd into r), then the flush of the private histogram (HR copies, summed per bin) into
+// P.C. Block-wide; leaves the histogram free for reuse (ends with a barrier).
+template <int D, bool F32, int HR>
 __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums &acc,
                                              typename Prec<F32>::T *hist, bool flush_hist, float hsig,
                                              double *red_scratch)
@@ -366,7 +420,7 @@ __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums 
         atomicAdd(&P.sums[0], sI * P.fscale);
         atomicAdd(&P.sums[1], sV * P.inv_pp1 * P.fscale * P.fscale);
     }
-    if (flush_hist) {
+    if (HR > 0 && flush_hist) {
         __syncthreads();
         double cscale;
         if constexpr (F32) {
@@ -376,16 +430,33 @@ __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums 
             cscale = 1.0;   // the block's contributions already carry nd^(2d)
         }
         for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
-            const T v = hist[e];
+            T v;
+            if constexpr (F32 && HR >= 4) {
+                // the copies of bin e are HR consecutive words, 16-byte aligned
+                const float4 *q = reinterpret_cast<const float4 *>(hist + (size_t)e * HR);
+                float4 a = q[0];
+#pragma unroll
+                for (int c = 1; c < HR / 4; ++c) {
+                    const float4 b = q[c];
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                }
+                v = (a.x + a.y) + (a.z + a.w);
+            } else {
+                v = hist[(size_t)e * HR];
+#pragma unroll
+                for (int c = 1; c < HR; ++c) v += hist[(size_t)e * HR + c];
+            }
             if (v != T(0)) atomicAdd(&P.C[e], (double)v * cscale);
         }
     }
     __syncthreads();
 }
 
-// One job, whole grid of persistent blocks.
-template <int D, int FID, bool F32>
-__global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>())) vsample_kernel(const VsampleParams P)
+// One job, whole grid of persistent blocks. HR = 0: frozen iteration; HR > 1: FP32 adjusting
+// iteration with HR lane-interleaved histogram copies, one 1024-thread block per SM.
+template <int D, int FID, bool F32, int HR>
+__global__ void __launch_bounds__((HR > 1 ? kReplThreads : kMaxBlockThreads), (min_blocks_per_sm<D, F32, HR>()))
+    vsample_kernel(const VsampleParams P)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
@@ -394,8 +465,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
     T *hist = reinterpret_cast<T *>(smem_raw + (size_t)D * kNB * sizeof(T2));
     __shared__ double red_scratch[64];
 
-    const bool adjust = P.adjust != 0;
-    stage_grid<D, F32>(P.grid, tab, hist, adjust);
+    const bool adjust = HR > 0 && P.adjust != 0;
+    stage_grid<D, F32>(P.grid, tab, hist, adjust ? D * kNB * HR : 0);
 
     // This thread's sub-cube range. Range r = (gtid * P.perm_mul) mod N is a permutation of
     // the N threads (perm_mul is odd and coprime with N): the 32 lanes of a warp start in
@@ -409,8 +480,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
 
     const float hsig = histogram_scale<F32>(P);
     ThreadSums acc;
-    sample_cubes<D, FID, F32, false>(P, t, t_end, tab, hist, hsig, acc);
-    finish_block<D, F32>(P, acc, hist, adjust, hsig, red_scratch);
+    sample_cubes<D, FID, F32, false, HR>(P, t, t_end, tab, hist, hsig, acc);
+    finish_block<D, F32, HR>(P, acc, hist, adjust, hsig, red_scratch);
 }
 
 // ------------------------------------------------------------------------------ batches
@@ -455,7 +526,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
         const BatchTile tile = tiles[ti];
         if ((int)tile.job != cur) {
             if (cur >= 0) {
-                finish_block<D, F32>(P, acc, hist, shared_hist, hsig, red_scratch);
+                finish_block<D, F32, 1>(P, acc, hist, shared_hist, hsig, red_scratch);
                 acc = ThreadSums();
             }
             cur = (int)tile.job;
@@ -470,14 +541,14 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
             P.adjust = adjust;
             P.probe = nullptr;
             hsig = histogram_scale<F32>(P);
-            stage_grid<D, F32>(P.grid, tab, hist, shared_hist);
+            stage_grid<D, F32>(P.grid, tab, hist, shared_hist ? D * kNB : 0);
         }
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
-        sample_cubes<D, FID, F32, kGlobalHist>(P, t, t_end, tab, hist, hsig, acc);
+        sample_cubes<D, FID, F32, kGlobalHist, 1>(P, t, t_end, tab, hist, hsig, acc);
     }
-    if (cur >= 0) finish_block<D, F32>(P, acc, hist, shared_hist, hsig, red_scratch);
+    if (cur >= 0) finish_block<D, F32, 1>(P, acc, hist, shared_hist, hsig, red_scratch);
 }
 
 }  // namespace mcubes

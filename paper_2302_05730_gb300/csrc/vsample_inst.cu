@@ -38,36 +38,36 @@ constexpr int kFid = MCUBES_FID;
 // values for the same device).
 struct InstanceInfo {
     std::atomic<int> ready{0};
-    int occ[2];   // resident blocks per SM at 256 threads, [adjust]
+    int occ;   // resident blocks per SM at the instance's default block size
 };
 
-template <int D>
-int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
+// One single-job launch of vsample_kernel<D, fid, precision, HR>: a persistent grid of
+// num_sms x resident blocks (or the requested blocks per SM).
+template <int D, int HR>
+int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 {
     static InstanceInfo info;
-    auto kern = vsample_kernel<D, kFid, kF32>;
-    const bool adjust = P.adjust != 0;
-    const size_t smem = vsample_smem_bytes<kF32>(D, adjust);
+    auto kern = vsample_kernel<D, kFid, kF32, HR>;
+    constexpr bool kRepl = HR > 1;
+    constexpr int kDefThreads = kRepl ? kReplThreads : kMaxBlockThreads;
+    const size_t smem = vsample_smem_bytes<kF32>(D, HR);
     cudaError_t e;
     if (!info.ready.load(std::memory_order_acquire)) {
-        const size_t smem_max = vsample_smem_bytes<kF32>(D, true);
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
-        for (int a = 0; a < 2; ++a) {
-            int nb = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kMaxBlockThreads,
-                                                              vsample_smem_bytes<kF32>(D, a != 0));
-            if (e != cudaSuccess) return (int)e;
-            info.occ[a] = nb > 0 ? nb : 1;
-        }
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kDefThreads, smem);
+        if (e != cudaSuccess) return (int)e;
+        info.occ = nb > 0 ? nb : 1;
         info.ready.store(1, std::memory_order_release);
     }
-    const int threads = req.threads;
+    const int threads = req.user_threads ? req.threads : kDefThreads;
     int bps = req.blocks_per_sm;
     if (bps <= 0) {
-        bps = info.occ[adjust ? 1 : 0];
-        // occupancy was computed for 256 threads; smaller blocks fit proportionally more
-        if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
+        bps = info.occ;
+        // occupancy was computed for the default block size; smaller blocks fit proportionally
+        // more, up to the shared memory (one block per SM whatever its size when replicated)
+        if (!kRepl && threads < kDefThreads) bps = bps * (kDefThreads / threads);
     }
     uint64_t blocks = (uint64_t)req.num_sms * (uint64_t)bps;
     // at least ~4 sub-cubes per thread so the per-block grid staging stays cheap
@@ -84,24 +84,42 @@ int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
+// Frozen iterations take the histogram-free instance; adjusting ones the FP32 kernel with
+// replicated histogram copies, or the FP64 kernel with one copy.
+template <int D>
+int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
+{
+    if (P.adjust == 0) return launch_hr<D, 0>(P, req, s);
+    if constexpr (kF32) {
+        return launch_hr<D, hist_replicas_f32<D>()>(P, req, s);
+    } else {
+        return launch_hr<D, 1>(P, req, s);
+    }
+}
+
 #if MCUBES_PART == 1
+struct BatchInstanceInfo {
+    std::atomic<int> ready{0};
+    int occ[2];   // resident blocks per SM at 256 threads, [shared histogram]
+};
+
 template <int D, bool kGlobalHist>
 int launch_batch_d(const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration, int parity,
                    int adjust, const LaunchReq &req, cudaStream_t s)
 {
-    static InstanceInfo info;
+    static BatchInstanceInfo info;
     auto kern = vsample_batch_kernel<D, kFid, kF32, kGlobalHist>;
     const bool shared_hist = adjust && !kGlobalHist;
-    const size_t smem = vsample_smem_bytes<kF32>(D, shared_hist);
+    const size_t smem = vsample_smem_bytes<kF32>(D, shared_hist ? 1 : 0);
     cudaError_t e;
     if (!info.ready.load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)vsample_smem_bytes<kF32>(D, true));
+                                 (int)vsample_smem_bytes<kF32>(D, 1));
         if (e != cudaSuccess) return (int)e;
         for (int a = 0; a < 2; ++a) {
             int nb = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kMaxBlockThreads,
-                                                              vsample_smem_bytes<kF32>(D, a != 0));
+                                                              vsample_smem_bytes<kF32>(D, a));
             if (e != cudaSuccess) return (int)e;
             info.occ[a] = nb > 0 ? nb : 1;
         }

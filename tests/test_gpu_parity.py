@@ -161,6 +161,38 @@ def test_vsample_parity_adapted_grid(capi, fid, mode):
     _compare(gpu, ref, mode, B)
 
 
+LAUNCH_SHAPES = [None, dict(block_threads=64), dict(block_threads=96, blocks_per_sm=3),
+                 dict(block_threads=256, blocks_per_sm=2), dict(blocks_per_sm=1), dict(blocks_per_sm=5)]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("fid,d,n", [(W.GAUSSIAN, 3, 30000), (W.OSCILLATORY, 8, 40000), (W.C0, 12, 2 * 3 ** 12 + 5)])
+def test_launch_shapes_match_oracle(capi, fid, d, n, mode):
+    """Every block size and grid shape gives the oracle's sums and bin contributions: the
+    histogram copies (8 at d = 8, 4 at d = 12 in FP32, one in FP64), the frozen instance, and
+    sub-cube ranges cut for any thread count."""
+    par = _params(fid, d, seed=d)
+    B = _random_grid(d, 40 + d)
+    seed, it = 777 + d, 2
+    ref = {a: oracle.vsample(fid, d, par, n, seed, it=it, mode=mode, adjust=a, B=B, per_cube=True) for a in (0, 1)}
+    dev = torch.device("cuda")
+    g_in = torch.from_numpy(B).to(dev)
+    for tune in LAUNCH_SHAPES:
+        for adjust in (1, 0):
+            sums = torch.zeros(2, dtype=torch.float64, device=dev)
+            C = torch.zeros(d * 500, dtype=torch.float64, device=dev)
+            capi.vsample_dev(fid, par, d, n, seed, it, 0, adjust, mode, g_in, C, sums, tune=tune)
+            torch.cuda.synchronize()
+            s = sums.cpu().numpy()
+            m = ref[adjust]["m"]
+            gpu = dict(I=s[0] / m, Var=s[1] / m ** 2)
+            if adjust:
+                gpu["C"] = C.cpu().numpy().reshape(d, 500)
+            else:
+                assert not C.any()
+            _compare(gpu, ref[adjust], mode)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_frozen_iteration_and_uniform_grid(capi, mode):
     d, n, fid = 5, 77777, W.GAUSSIAN
