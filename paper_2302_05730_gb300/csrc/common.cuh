@@ -69,6 +69,8 @@ struct VsampleParams {
     uint32_t probe_mask;     // cube t is probed when (t & probe_mask) == 0
     uint32_t probe_shift;
     uint32_t perm_mul;       // odd multiplier, coprime with the launch's thread count
+    int ih_vmax_exp;         // fixed-point histogram: contributions below 2^ih_vmax_exp units take the
+                             // integer path (set per launch so no bin's 64-bit sum can overflow)
     uint32_t m;              // sub-cubes
     uint32_t p;              // samples per sub-cube
     uint32_t g;              // strata per axis

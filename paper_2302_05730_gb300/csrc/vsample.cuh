@@ -12,9 +12,9 @@
 //   5. on adjusting iterations, the bin contributions w^2, added to a block-private
 //      shared-memory histogram.
 //
-// Kernel instances per (d, integrand, precision): HR = 0 for frozen iterations (no histogram
-// code at all) and HR >= 1 copies of the histogram for adjusting ones. The FP32 adjusting
-// kernel keeps HR lane-interleaved copies (see hist_replicas_f32).
+// Kernel instances per (d, integrand, precision) by histogram kind HK: 0 for frozen iterations
+// (no histogram code at all); 1 for FP64 adjusting iterations (one shared copy); 2 for FP32
+// adjusting iterations (a fixed-point histogram, see IntHist).
 //
 // Per block at the end:
 //   - warp-shuffle and shared-memory reduction of the thread sums, then two FP64 global
@@ -62,18 +62,59 @@ __host__ __device__ constexpr size_t vsample_smem_bytes(int d, int hr)
     return (size_t)d * kNB * (sizeof(typename Prec<F32>::T2) + (size_t)hr * sizeof(typename Prec<F32>::T));
 }
 
-// Histogram copies of the single-job FP32 adjusting kernel. Copy g = lane mod HR holds bin e at
-// word e HR + g, so within one warp-wide atomic only the 32 / HR lanes of a copy can meet in a
-// bank, over that copy's 32 / HR banks. Random bins (which the VEGAS map draws by construction)
-// then collide about half as often: 3.1 FP32 shared atomics per SM clock at HR = 8 against 2.2
-// with one copy, measured on GB300 at 1024 threads per SM. The table and 8 copies fit one
-// 1024-thread block per SM up to d = 11; larger d keeps 4 copies.
+// The fixed-point histogram of the FP32 adjusting kernel (HK = 2).
+//
+// A contribution h (FP32, >= 0) becomes v = h q with q = 2^e a power of two chosen per block, so
+// the product is exact. Zero contributions add nothing. When 2^14 <= v < vmax = 2^ih_vmax_exp (at
+// most 2^44) it is rounded to a 64-bit integer (exact above 2^23, within 2^-15 relative below) and
+// added to the bin with native u32 shared atomics:
+//   - the low word to one of R lane-interleaved copies (copy g = lane mod R holds bin e at word
+//     e R + g, so only the 32 / R lanes of a copy can meet in a bank);
+//   - the high word, plus 1 when the low add wrapped (detected from the atomic's old value), to a
+//     single high word per bin.
+// Other contributions (below 2^14 or from vmax up, infinite or NaN) go to an FP32 side copy with
+// FP32 shared atomics. Every bin therefore keeps a relative precision of 2^-15 or better, whatever
+// the scale. The host sets vmax so that a block's samples times vmax stays below 2^63: no bin's
+// sum can overflow. The flush adds (low copies + 2^32 high) / q + side into the FP64 C.
+//
+// Why: an FP32 shared atomic costs about four times a u32 one under random bins (it reads the
+// word, adds and compares-and-swaps), and the histogram's atomics bound adjusting iterations.
+//
+// The scale only decides which path a contribution takes. It comes from a pilot, each thread's
+// first sample: with P+ the pilot's fraction of positive contributions and g+ their geometric
+// mean, q = 2^28 P+ / g+ (exponent rounded), which puts the typical positive contribution near the
+// middle of the 29 octaves the integer path covers (weighting by P+ keeps the block's mean
+// contribution there for sparse integrands). A block whose pilot has no positive contribution
+// sends every contribution to the side copy.
 constexpr int kReplThreads = 1024;
+constexpr float kIntHistLo = 16384.0f;             // 2^14: smallest contribution (units) on the integer path
+constexpr double kIntHistCentre = 28.0;            // log2 of the scaled P+-weighted pilot mean
 template <int D>
-constexpr int hist_replicas_f32()
+__host__ __device__ constexpr size_t int_hist_smem_bytes(int r)
 {
-    return vsample_smem_bytes<true>(D, 8) + 2048 <= (size_t)227 * 1024 ? 8 : 4;
+    return (size_t)D * kNB * (sizeof(float2) + 4 * (size_t)r + 4 + 4);
 }
+template <int D>
+__host__ __device__ constexpr int int_hist_copies()
+{
+    return int_hist_smem_bytes<D>(8) + 2048 <= (size_t)227 * 1024 ? 8 : int_hist_smem_bytes<D>(4) + 2048 <= (size_t)227 * 1024 ? 4 : 2;
+}
+
+// Shared-memory bytes of one single-job block with histogram kind HK.
+template <int D, bool F32, int HK>
+__host__ __device__ constexpr size_t single_smem_bytes()
+{
+    return HK == 2 ? int_hist_smem_bytes<D>(int_hist_copies<D>()) : vsample_smem_bytes<F32>(D, HK);
+}
+
+// Shared-window addresses of a block's fixed-point histogram, and its scale.
+struct IntHist {
+    uint32_t lo;     // R low-word copies: bin e, copy g at word e R + g
+    uint32_t hi;     // one high word per bin
+    uint32_t side;   // one FP32 word per bin
+    float q;         // 2^e: fixed-point units per unit of contribution
+    float vmax;      // contributions of vmax units or more go to the side copy
+};
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -114,6 +155,34 @@ __device__ __forceinline__ void red_add_f32(uint32_t a, float v)
 {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v));
 }
+__device__ __forceinline__ uint32_t atom_add_u32(uint32_t a, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v));
+    return old;
+}
+__device__ __forceinline__ void red_add_u32(uint32_t a, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+// hi + the carry out of old + lo (two integer adds: add with carry-out, add with carry-in)
+__device__ __forceinline__ uint32_t add_carry(uint32_t old, uint32_t lo, uint32_t hi)
+{
+    uint32_t sum, c;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;" : "=r"(sum), "=r"(c) : "r"(old), "r"(lo), "r"(hi));
+    return c;
+}
+// round(v) for a float 2^14 <= v < 2^44, from its bits with integer operations (a 64-bit float
+// conversion would run on the FP64 pipe): v = M 2^s with the 24-bit significand M and
+// s = exponent - 23 in [-9, 20]; halves round up.
+__device__ __forceinline__ unsigned long long round_to_u64(float v)
+{
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t M = (b & 0x7FFFFFu) | 0x800000u;
+    const int s = (int)(b >> 23) - 150;
+    return s >= 0 ? (unsigned long long)M << s : (unsigned long long)((M + (1u << (-s - 1))) >> -s);
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Resident blocks per SM the FP32-eval kernels are compiled for (register budget 65536 /
@@ -123,10 +192,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 #ifndef MCUBES_MAX_MIN_BLOCKS
 #define MCUBES_MAX_MIN_BLOCKS 4
 #endif
-template <int D, bool F32, int HR = 1>
+template <int D, bool F32, int HK = 1>
 constexpr int min_blocks_per_sm()
 {
-    if (!F32 || HR > 1) return 1;
+    if (!F32 || HK == 2) return 1;
     const size_t smem = vsample_smem_bytes<F32>(D, true) + 1024;
     const int fit = (int)((size_t)(227 * 1024) / smem);
     const int b = fit < MCUBES_MAX_MIN_BLOCKS ? fit : MCUBES_MAX_MIN_BLOCKS;
@@ -140,11 +209,11 @@ struct ThreadSums {
     float cV = 0.0f, eV = 0.0f;     // ... and of the cube variances (times p (p-1))
 };
 
-// Stage a grid into shared memory as (B_k, Delta_k) pairs and clear n_clear words of the
-// histogram. Block-wide.
+// Stage a grid into shared memory as (B_k, Delta_k) pairs and clear n_clear 4-byte words of the
+// histogram region that follows it. Block-wide.
 template <int D, bool F32>
 __device__ __forceinline__ void stage_grid(const double *grid, typename Prec<F32>::T2 *tab,
-                                           typename Prec<F32>::T *hist, int n_clear)
+                                           void *hist, int n_clear)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
@@ -158,7 +227,8 @@ __device__ __forceinline__ void stage_grid(const double *grid, typename Prec<F32
         v.y = (T)(b1 - b0);
         tab[e] = v;
     }
-    for (int e = threadIdx.x; e < n_clear; e += blockDim.x) hist[e] = T(0);
+    uint32_t *h = reinterpret_cast<uint32_t *>(hist);
+    for (int e = threadIdx.x; e < n_clear; e += blockDim.x) h[e] = 0u;
     __syncthreads();
 }
 
@@ -179,19 +249,22 @@ __device__ __forceinline__ float histogram_scale(const VsampleParams &P)
 
 // Algorithm 2's loop over this thread's sub-cubes [t, t_end): draws, map, integrand, per-cube
 // statistics and bin contributions. kGlobalHist routes the contributions straight to the
-// job's global C (FP64 atomics) instead of the block's shared histogram; otherwise they go to
-// the HR-copy shared histogram, and HR = 0 compiles them out.
-template <int D, int FID, bool F32, bool kGlobalHist, int HR>
-__device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t, const uint32_t t_end,
-                                             const typename Prec<F32>::T2 *tab, typename Prec<F32>::T *hist,
-                                             const float hsig, ThreadSums &acc)
+// job's global C (FP64 atomics) instead of the block's shared histogram; otherwise HK picks the
+// block's histogram (0: none, 1: one shared copy `hist`, 2: the fixed-point histogram `ih`).
+// kPilot: evaluate only sample q = 0 of sub-cube t and return its contribution (w sigma)^2,
+// touching nothing else.
+template <int D, int FID, bool F32, bool kGlobalHist, int HK, bool kPilot = false>
+__device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t, const uint32_t t_end,
+                                              const typename Prec<F32>::T2 *tab, typename Prec<F32>::T *hist,
+                                              const IntHist &ih, const float hsig, ThreadSums &acc)
 {
     using T = typename Prec<F32>::T;
     using T2 = typename Prec<F32>::T2;
-    static_assert(HR == 0 || HR == 1 || HR == 2 || HR == 4 || HR == 8, "histogram copies: 0, 1, 2, 4 or 8");
-    const bool adjust = (kGlobalHist || HR > 0) && P.adjust != 0;
-    // this lane's histogram copy, as a word offset
-    const int hcopy = HR > 1 ? (int)(threadIdx.x & (HR - 1)) : 0;
+    static_assert(HK >= 0 && HK <= 2, "histogram kind: 0, 1 or 2");
+    static_assert(HK != 2 || F32, "the fixed-point histogram is the FP32 path's");
+    static_assert(!kPilot || (F32 && HK == 2), "the pilot serves the fixed-point histogram");
+    const bool adjust = (kGlobalHist || HK > 0) && P.adjust != 0;
+    constexpr int kR = HK == 2 ? int_hist_copies<D>() : 1;
 
     // strata digits c_i (axis 0 fastest) and c_i - 1 in the path's precision
     uint32_t dig[D];
@@ -212,11 +285,16 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
     const uint32_t p = P.p;
     const float inv_p32 = (float)P.inv_p;
     // FP32: kb = yn + 2^23 rounded down has bit pattern 0x4B000000 + k, so the byte address of
-    // table entry (i, k) is bits(kb) * 8 + tab_adj + i * kNB * 8, and that of this lane's
-    // histogram copy of bin (i, k) is bits(kb) * 4 HR + hist_adj + i * kNB * 4 HR (mod 2^32).
+    // table entry (i, k) is bits(kb) * 8 + tab_adj + i * kNB * 8 (mod 2^32), and the histogram
+    // words of bin (i, k) follow the same pattern: one shared copy (HK = 1) at bits(kb) * 4 +
+    // hist_adj; fixed point (HK = 2) with this lane's low word at bits(kb) * 4 R + lo_adj and the
+    // high and side words at bits(kb) * 4 + hi_adj / side_adj (each plus i times the axis stride).
     constexpr uint32_t kMagicBits = 0x4B000000u;
     const uint32_t tab_adj = smem_addr(tab) - kMagicBits * 8u;
-    const uint32_t hist_adj = HR > 0 ? smem_addr(hist) + 4u * (uint32_t)hcopy - kMagicBits * (4u * (uint32_t)HR) : 0u;
+    const uint32_t hist_adj = HK == 1 ? smem_addr(hist) - kMagicBits * 4u : 0u;
+    const uint32_t lo_adj = HK == 2 ? ih.lo + 4u * (threadIdx.x & (uint32_t)(kR - 1)) - kMagicBits * (4u * kR) : 0u;
+    const uint32_t hi_adj = HK == 2 ? ih.hi - kMagicBits * 4u : 0u;
+    const uint32_t side_adj = HK == 2 ? ih.side - kMagicBits * 4u : 0u;
     // global-histogram scale (FP32: (F / sigma)^2; FP64: 1, the contribution already carries nd^d)
     double gscale = 0.0;
     if constexpr (kGlobalHist) {
@@ -236,7 +314,7 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
             Integrand32<FID, D> f32;
             T J = T(1);
             int kofs[D];        // bin index i nd + k (FP64 path, global histogram)
-            uint32_t haddr[D];  // shared address of the lane's histogram copy of the bin (FP32 path)
+            uint32_t kbb[D];    // bit pattern of yn + 2^23 rounded down: 0x4B000000 + k (FP32 path)
 
             constexpr int kDimsPerCall = F32 ? 4 : 2;
             constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
@@ -272,8 +350,8 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                             bw = lds_f32x2(kbits * 8u + (tab_adj + (uint32_t)(i * kNB * 8)));
                             if constexpr (kGlobalHist) {
                                 kofs[i] = i * kNB + (int)(kbits - kMagicBits);
-                            } else if constexpr (HR > 0) {
-                                haddr[i] = kbits * (4u * (uint32_t)HR) + (hist_adj + (uint32_t)(i * kNB * 4 * HR));
+                            } else {
+                                kbb[i] = kbits;
                             }
                             kb = __fsub_rn(kb, magic);
                         } else {
@@ -311,6 +389,10 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                 w = f64.finish(P.ip) * J;   // Jacobian without nd^d (applied per block)
             }
 
+            if constexpr (kPilot) {
+                const float ws = w * hsig;
+                return ws * ws;
+            }
             if constexpr (F32) {
                 if (q == 0) {
                     w0 = w;
@@ -339,13 +421,28 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
                     const double hg = (double)h * gscale;
 #pragma unroll
                     for (int i = 0; i < D; ++i) atomicAdd(&P.C[kofs[i]], hg);
-                } else if constexpr (HR > 0) {
+                } else if constexpr (HK == 1) {
                     if constexpr (F32) {
 #pragma unroll
-                        for (int i = 0; i < D; ++i) red_add_f32(haddr[i], h);
+                        for (int i = 0; i < D; ++i) red_add_f32(kbb[i] * 4u + (hist_adj + (uint32_t)(i * kNB * 4)), h);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i] * HR + hcopy], h);
+                        for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], h);
+                    }
+                } else if constexpr (HK == 2) {
+                    const float vf = h * ih.q;   // exact: q is a power of two
+                    if (vf >= kIntHistLo && vf < ih.vmax) {
+                        const unsigned long long v = round_to_u64(vf);
+                        const uint32_t vlo = (uint32_t)v, vhi = (uint32_t)(v >> 32);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) {
+                            const uint32_t old = atom_add_u32(kbb[i] * (4u * kR) + (lo_adj + (uint32_t)(i * kNB * 4 * kR)), vlo);
+                            const uint32_t c = add_carry(old, vlo, vhi);
+                            if (c != 0u) red_add_u32(kbb[i] * 4u + (hi_adj + (uint32_t)(i * kNB * 4)), c);
+                        }
+                    } else if (h != 0.0f) {   // outside the range, infinite or NaN
+#pragma unroll
+                        for (int i = 0; i < D; ++i) red_add_f32(kbb[i] * 4u + (side_adj + (uint32_t)(i * kNB * 4)), h);
                     }
                 }
             }
@@ -399,15 +496,17 @@ __device__ __forceinline__ void sample_cubes(const VsampleParams &P, uint32_t t,
             }
         }
     }
+    return 0.0f;
 }
 
 // Block reduction of the thread sums, two FP64 global atomics into P.sums (Algorithm 2,
-// AtomicAdd into r), then the flush of the private histogram (HR copies, summed per bin) into
-// P.C. Block-wide; leaves the histogram free for reuse (ends with a barrier).
-template <int D, bool F32, int HR>
+// AtomicAdd into r), then the flush of the block's histogram into P.C: one shared copy (HK = 1),
+// or the fixed-point histogram (HK = 2; per bin, (low copies + 2^32 high) / q + side). Block-wide;
+// leaves the histogram free for reuse (ends with a barrier).
+template <int D, bool F32, int HK>
 __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums &acc,
-                                             typename Prec<F32>::T *hist, bool flush_hist, float hsig,
-                                             double *red_scratch)
+                                             typename Prec<F32>::T *hist, const IntHist &ih, bool flush_hist,
+                                             float hsig, double *red_scratch)
 {
     using T = typename Prec<F32>::T;
     double sI = acc.sI, sV = acc.sV;
@@ -420,7 +519,7 @@ __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums 
         atomicAdd(&P.sums[0], sI * P.fscale);
         atomicAdd(&P.sums[1], sV * P.inv_pp1 * P.fscale * P.fscale);
     }
-    if (HR > 0 && flush_hist) {
+    if (HK > 0 && flush_hist) {
         __syncthreads();
         double cscale;
         if constexpr (F32) {
@@ -429,33 +528,45 @@ __device__ __forceinline__ void finish_block(const VsampleParams &P, ThreadSums 
         } else {
             cscale = 1.0;   // the block's contributions already carry nd^(2d)
         }
-        for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
-            T v;
-            if constexpr (F32 && HR >= 4) {
-                // the copies of bin e are HR consecutive words, 16-byte aligned
-                const float4 *q = reinterpret_cast<const float4 *>(hist + (size_t)e * HR);
-                float4 a = q[0];
+        if constexpr (HK == 2) {
+            constexpr int kR = int_hist_copies<D>();
+            const uint32_t *lo = reinterpret_cast<const uint32_t *>(hist);
+            const uint32_t *hi = lo + (size_t)D * kNB * kR;
+            const float *side = reinterpret_cast<const float *>(hi + (size_t)D * kNB);
+            const double inv_q = 1.0 / (double)ih.q;
+            for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
+                unsigned long long sum = (unsigned long long)hi[e] << 32;
+                if constexpr (kR >= 4) {
+                    // the copies of bin e are kR consecutive words, 16-byte aligned
+                    const uint4 *q4 = reinterpret_cast<const uint4 *>(lo + (size_t)e * kR);
 #pragma unroll
-                for (int c = 1; c < HR / 4; ++c) {
-                    const float4 b = q[c];
-                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                    for (int c = 0; c < kR / 4; ++c) {
+                        const uint4 b = q4[c];
+                        sum += (unsigned long long)b.x + b.y + (unsigned long long)b.z + b.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kR; ++c) sum += lo[(size_t)e * kR + c];
                 }
-                v = (a.x + a.y) + (a.z + a.w);
-            } else {
-                v = hist[(size_t)e * HR];
-#pragma unroll
-                for (int c = 1; c < HR; ++c) v += hist[(size_t)e * HR + c];
+                double v = (double)side[e];
+                if (sum != 0ull) v += (double)sum * inv_q;
+                if (v != 0.0) atomicAdd(&P.C[e], v * cscale);
             }
-            if (v != T(0)) atomicAdd(&P.C[e], (double)v * cscale);
+        } else {
+            for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
+                const T v = hist[e];
+                if (v != T(0)) atomicAdd(&P.C[e], (double)v * cscale);
+            }
         }
     }
     __syncthreads();
 }
 
-// One job, whole grid of persistent blocks. HR = 0: frozen iteration; HR > 1: FP32 adjusting
-// iteration with HR lane-interleaved histogram copies, one 1024-thread block per SM.
-template <int D, int FID, bool F32, int HR>
-__global__ void __launch_bounds__((HR > 1 ? kReplThreads : kMaxBlockThreads), (min_blocks_per_sm<D, F32, HR>()))
+// One job, whole grid of persistent blocks. HK = 0: frozen iteration; HK = 1: FP64 adjusting
+// iteration; HK = 2: FP32 adjusting iteration with the fixed-point histogram, one 1024-thread
+// block per SM.
+template <int D, int FID, bool F32, int HK>
+__global__ void __launch_bounds__((HK == 2 ? kReplThreads : kMaxBlockThreads), (min_blocks_per_sm<D, F32, HK>()))
     vsample_kernel(const VsampleParams P)
 {
     using T = typename Prec<F32>::T;
@@ -464,9 +575,13 @@ __global__ void __launch_bounds__((HR > 1 ? kReplThreads : kMaxBlockThreads), (m
     T2 *tab = reinterpret_cast<T2 *>(smem_raw);
     T *hist = reinterpret_cast<T *>(smem_raw + (size_t)D * kNB * sizeof(T2));
     __shared__ double red_scratch[64];
+    __shared__ float pilot_q, pilot_vmax;
 
-    const bool adjust = HR > 0 && P.adjust != 0;
-    stage_grid<D, F32>(P.grid, tab, hist, adjust ? D * kNB * HR : 0);
+    constexpr int kR = HK == 2 ? int_hist_copies<D>() : 1;
+    const bool adjust = HK > 0 && P.adjust != 0;
+    // histogram words: one copy (HK = 1, T-sized), or kR low copies + high + side (HK = 2)
+    const int n_clear = !adjust ? 0 : HK == 2 ? D * kNB * (kR + 2) : D * kNB * (int)(sizeof(T) / 4);
+    stage_grid<D, F32>(P.grid, tab, hist, n_clear);
 
     // This thread's sub-cube range. Range r = (gtid * P.perm_mul) mod N is a permutation of
     // the N threads (perm_mul is odd and coprime with N): the 32 lanes of a warp start in
@@ -480,8 +595,44 @@ __global__ void __launch_bounds__((HR > 1 ? kReplThreads : kMaxBlockThreads), (m
 
     const float hsig = histogram_scale<F32>(P);
     ThreadSums acc;
-    sample_cubes<D, FID, F32, false, HR>(P, t, t_end, tab, hist, hsig, acc);
-    finish_block<D, F32, HR>(P, acc, hist, adjust, hsig, red_scratch);
+    IntHist ih{0u, 0u, 0u, 0.0f, 0.0f};
+    if constexpr (HK == 2) {
+        ih.lo = smem_addr(hist);
+        ih.hi = ih.lo + 4u * (uint32_t)(D * kNB * kR);
+        ih.side = ih.hi + 4u * (uint32_t)(D * kNB);
+        ih.vmax = ldexpf(1.0f, P.ih_vmax_exp);
+        if (adjust) {
+            // pilot: the threads' first contributions (their count, the positive ones' count and
+            // the positive ones' mean log2)
+            double lg = 0.0, npos = 0.0, nall = t < t_end ? 1.0 : 0.0;
+            if (t < t_end) {
+                const float hp = sample_cubes<D, FID, F32, false, HK, true>(P, t, t + 1, tab, hist, ih, hsig, acc);
+                if (hp > 0.0f && hp <= 3.0e38f) {
+                    lg = (double)log2f(fmaxf(hp, 1.17549435e-38f));
+                    npos = 1.0;
+                }
+            }
+            block_sum2(lg, npos, red_scratch);
+            double nall_sum = nall, unused = 0.0;
+            __syncthreads();   // red_scratch is reused
+            block_sum2(nall_sum, unused, red_scratch);
+            if (threadIdx.x == 0) {
+                float q = 1.0f, vmax = 0.0f;   // no positive pilot contribution: all to the side copy
+                if (npos > 0.0 && nall_sum > 0.0) {
+                    const double e = kIntHistCentre + log2(npos / nall_sum) - lg / npos;
+                    q = ldexpf(1.0f, (int)rint(fmin(fmax(e, -120.0), 120.0)));
+                    vmax = ih.vmax;
+                }
+                pilot_q = q;
+                pilot_vmax = vmax;
+            }
+            __syncthreads();
+            ih.q = pilot_q;
+            ih.vmax = pilot_vmax;
+        }
+    }
+    sample_cubes<D, FID, F32, false, HK>(P, t, t_end, tab, hist, ih, hsig, acc);
+    finish_block<D, F32, HK>(P, acc, hist, ih, adjust, hsig, red_scratch);
 }
 
 // ------------------------------------------------------------------------------ batches
@@ -499,6 +650,9 @@ struct BatchJob {
 struct BatchTile {
     uint32_t job, c0, c1, pad;
 };
+
+// The batched kernel keeps one shared copy of the histogram (or none, with kGlobalHist).
+__device__ constexpr IntHist kNoIntHist{0u, 0u, 0u, 0.0f, 0.0f};
 
 template <int D, int FID, bool F32, bool kGlobalHist>
 __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()))
@@ -526,7 +680,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
         const BatchTile tile = tiles[ti];
         if ((int)tile.job != cur) {
             if (cur >= 0) {
-                finish_block<D, F32, 1>(P, acc, hist, shared_hist, hsig, red_scratch);
+                finish_block<D, F32, 1>(P, acc, hist, kNoIntHist, shared_hist, hsig, red_scratch);
                 acc = ThreadSums();
             }
             cur = (int)tile.job;
@@ -541,14 +695,14 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
             P.adjust = adjust;
             P.probe = nullptr;
             hsig = histogram_scale<F32>(P);
-            stage_grid<D, F32>(P.grid, tab, hist, shared_hist ? D * kNB : 0);
+            stage_grid<D, F32>(P.grid, tab, hist, shared_hist ? D * kNB * (int)(sizeof(T) / 4) : 0);
         }
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
-        sample_cubes<D, FID, F32, kGlobalHist, 1>(P, t, t_end, tab, hist, hsig, acc);
+        sample_cubes<D, FID, F32, kGlobalHist, 1>(P, t, t_end, tab, hist, kNoIntHist, hsig, acc);
     }
-    if (cur >= 0) finish_block<D, F32, 1>(P, acc, hist, shared_hist, hsig, red_scratch);
+    if (cur >= 0) finish_block<D, F32, 1>(P, acc, hist, kNoIntHist, shared_hist, hsig, red_scratch);
 }
 
 }  // namespace mcubes

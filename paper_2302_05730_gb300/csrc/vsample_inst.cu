@@ -41,16 +41,16 @@ struct InstanceInfo {
     int occ;   // resident blocks per SM at the instance's default block size
 };
 
-// One single-job launch of vsample_kernel<D, fid, precision, HR>: a persistent grid of
+// One single-job launch of vsample_kernel<D, fid, precision, HK>: a persistent grid of
 // num_sms x resident blocks (or the requested blocks per SM).
-template <int D, int HR>
+template <int D, int HK>
 int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 {
     static InstanceInfo info;
-    auto kern = vsample_kernel<D, kFid, kF32, HR>;
-    constexpr bool kRepl = HR > 1;
+    auto kern = vsample_kernel<D, kFid, kF32, HK>;
+    constexpr bool kRepl = HK == 2;   // one 1024-thread block per SM
     constexpr int kDefThreads = kRepl ? kReplThreads : kMaxBlockThreads;
-    const size_t smem = vsample_smem_bytes<kF32>(D, HR);
+    constexpr size_t smem = single_smem_bytes<D, kF32, HK>();
     cudaError_t e;
     if (!info.ready.load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -80,21 +80,23 @@ int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     uint64_t mul = (uint64_t)((double)n * 0.6180339887498949) | 1u;
     while (std::gcd(mul, n) != 1) mul += 2;
     Q.perm_mul = (uint32_t)(mul % n == 0 ? 1 : mul % n);
+    // fixed-point histogram range: a block adds at most (its threads x the longest thread range x
+    // p) contributions to one bin; each below 2^e keeps the 64-bit sum below 2^63
+    const uint64_t spb = (((uint64_t)P.m + n - 1) / n) * (uint64_t)P.p * (uint64_t)threads;
+    int lg = 0;
+    while ((1ull << lg) < spb) ++lg;
+    Q.ih_vmax_exp = 63 - lg < 44 ? 63 - lg : 44;
     kern<<<(unsigned)blocks, threads, smem, s>>>(Q);
     return (int)cudaGetLastError();
 }
 
-// Frozen iterations take the histogram-free instance; adjusting ones the FP32 kernel with
-// replicated histogram copies, or the FP64 kernel with one copy.
+// Frozen iterations take the histogram-free instance; adjusting ones the FP32 kernel with the
+// fixed-point histogram, or the FP64 kernel with one shared copy.
 template <int D>
 int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 {
     if (P.adjust == 0) return launch_hr<D, 0>(P, req, s);
-    if constexpr (kF32) {
-        return launch_hr<D, hist_replicas_f32<D>()>(P, req, s);
-    } else {
-        return launch_hr<D, 1>(P, req, s);
-    }
+    return launch_hr<D, kF32 ? 2 : 1>(P, req, s);
 }
 
 #if MCUBES_PART == 1

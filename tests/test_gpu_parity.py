@@ -193,6 +193,22 @@ def test_launch_shapes_match_oracle(capi, fid, d, n, mode):
             _compare(gpu, ref[adjust], mode)
 
 
+@pytest.mark.parametrize("fid,d,n,a,u", [
+    (W.DISCONTINUOUS, 8, 200000, 9.0, 0.3),    # nonzero on 0.3^8 = 7e-5 of the cube: most pilots see only zeros
+    (W.GAUSSIAN, 8, 400000, 25.0, 0.5),       # contributions over hundreds of octaves on the uniform grid
+    (W.PRODUCT_PEAK, 6, 300000, 40.0, 0.35),
+])
+def test_fp32_histogram_extreme_spreads(capi, fid, d, n, a, u):
+    """FP32 bin contributions whose sizes defeat any one fixed-point scale: sparse integrands
+    (blocks whose pilot sees no positive contribution) and peaks on the uniform grid (most
+    contributions far below or above the block's scale) against the oracle's C."""
+    par = np.concatenate([np.full(d, a), np.full(d, u)])
+    for it, B in [(0, None), (3, _random_grid(d, 17))]:
+        gpu = capi.vsample_once(fid, par, d, n, 4242, iteration=it, adjust=1, precision=1, grid_in=B)
+        ref = oracle.vsample(fid, d, par, n, 4242, it=it, mode=1, adjust=1, B=B, per_cube=True)
+        _compare(gpu, ref, 1, B)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_frozen_iteration_and_uniform_grid(capi, mode):
     d, n, fid = 5, 77777, W.GAUSSIAN
