@@ -36,8 +36,8 @@ NCALL = 10 ** 8
 # DRAM bytes (read + write) per vsample_kernel<8, oscillatory, FP32-eval> launch at d = 8, 1e8 samples
 # per iteration, from one ncu capture of this kernel as it stands: the mean over the 5 adjusting and
 # 5 frozen launches of one integration, and each kind's own mean.
-VSAMPLE_DRAM_BYTES = 115098
-VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 141619, "frozen": 88576}
+VSAMPLE_DRAM_BYTES = 104422
+VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 136141, "frozen": 72704}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts: 152 SMs, 4 SM sub-partitions x 32 lanes issue one instruction per clock.
@@ -637,8 +637,8 @@ def main():
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the 10 "
                                            "launches of one full-size integration "
                                            "(profiles/vsample_fp32_d8_genz6_n1e8_launches.md)",
-                         "kernel": "vsample_kernel<8, fid, FP32, HR> (adjusting launches: HR = 8 histogram "
-                                   "copies, 152 x 1024; frozen launches: HR = 0, 608 x 256)",
+                         "kernel": "vsample_kernel<8, fid, FP32, HK> (adjusting launches: HK = 2, fixed-point "
+                                   "histogram, 152 x 1024; frozen launches: HK = 0, 608 x 256)",
                          "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_kms, "by_kind": kinds,
                          "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})"},
             "cpu_baseline": cpu,
