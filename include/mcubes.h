@@ -95,7 +95,7 @@ typedef struct mcubes_result {
 typedef struct mcubes_tuning {
     int32_t block_threads;    /* threads per V-Sample block (64..256, multiple of 32). Default: 256, and
                                  1024 for FP32 adjusting iterations, whose one block per SM holds the
-                                 lane-interleaved histogram copies */
+                                 fixed-point histogram */
     int32_t blocks_per_sm;    /* resident blocks per SM to launch (persistent grid); default: occupancy */
     int32_t reserved[6];
 } mcubes_tuning;

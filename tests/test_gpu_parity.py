@@ -168,9 +168,10 @@ LAUNCH_SHAPES = [None, dict(block_threads=64), dict(block_threads=96, blocks_per
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("fid,d,n", [(W.GAUSSIAN, 3, 30000), (W.OSCILLATORY, 8, 40000), (W.C0, 12, 2 * 3 ** 12 + 5)])
 def test_launch_shapes_match_oracle(capi, fid, d, n, mode):
-    """Every block size and grid shape gives the oracle's sums and bin contributions: the
-    histogram copies (8 at d = 8, 4 at d = 12 in FP32, one in FP64), the frozen instance, and
-    sub-cube ranges cut for any thread count."""
+    """Every block size and grid shape gives the oracle's sums and bin contributions: the FP32
+    fixed-point histogram (8 low-word copies at d = 8, 4 at d = 12; its per-block pilot scale with
+    any block size), the FP64 histogram, the frozen instance, and sub-cube ranges cut for any
+    thread count."""
     par = _params(fid, d, seed=d)
     B = _random_grid(d, 40 + d)
     seed, it = 777 + d, 2
