@@ -13,8 +13,13 @@
 // After the last layer each thread evaluates the integrand at its point. Operands are bf16 in the
 // K-major, unswizzled core-matrix layout (8 rows x 16 bytes per core matrix; leading-dimension
 // offset 128 bytes between core matrices along K, stride offset K/8 x 128 bytes between 8-row
-// groups); the weights come from a mirror that already has this layout. Every mbarrier wait is
-// bounded: on expiry the kernel records an error, stops, and frees its TMEM.
+// groups); the weights come from a mirror that already has this layout.
+//
+// A layer's weights reach shared memory by one bulk asynchronous copy (cp.async.bulk, completed on
+// an mbarrier by transaction bytes). With two weight buffers (when they fit), the copy of the next
+// layer in the CTA's sequence (or of the next tile's first layer) is issued at the start of a
+// layer and runs while that layer computes. Every mbarrier wait is bounded: on expiry the kernel
+// records an error, waits (bounded) for its copies still in flight, stops and frees its TMEM.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -100,6 +105,17 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// One thread: expect `bytes` on mbar and start the bulk copy global -> shared that delivers them.
+// src, dst and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(mbar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(mbar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
@@ -220,16 +236,18 @@ template <int H, int K>
 __global__ void __launch_bounds__(kTcThreads, 1)
     flow_sample_tc_kernel(const TcFlow F, const unsigned char *__restrict__ mirror, const TcSample S,
                           const IntegrandParams ip, long long i0, long long n, float *__restrict__ x_out,
-                          float *__restrict__ lq_out, float *__restrict__ w_out, int *__restrict__ err)
+                          float *__restrict__ lq_out, float *__restrict__ w_out, int *__restrict__ err, const int nbuf)
 {
     constexpr int SW = (2 * K + 1 + 7) & ~7;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_holder;
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t wbar[2];   // weight buffers: the bulk copies' completion
     __shared__ float lq_half[kTcRows];
     const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), half = tid >> 7, d = S.d, HS = d | 1;
-    unsigned char *wbuf = smem;                                   // F.max_bytes
-    unsigned char *A1 = smem + ((F.max_bytes + 1023u) & ~1023u);  // 128 x 16 bf16
+    const uint32_t wstride = (F.max_bytes + 1023u) & ~1023u;
+    unsigned char *const wbuf0 = smem, *const wbuf1 = smem + wstride;   // nbuf buffers of F.max_bytes
+    unsigned char *A1 = smem + (size_t)nbuf * wstride;           // 128 x 16 bf16
     unsigned char *A2 = A1 + kTcRows * 16 * 2;                    // 128 x H bf16 (also GEMM-3 operand)
     float *hs = reinterpret_cast<float *>(A2 + kTcRows * H * 2);  // 128 x HS
     if (warp == 0) {
@@ -239,6 +257,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&wbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&wbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     before_sync();
@@ -251,6 +271,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float *hr = hs + row * HS;
     const float ig = 1.0f / (float)S.g;
     const long long ntiles = (n + kTcRows - 1) / kTcRows;
+    // the CTA's layer sequence: step s is layer L - 1 - s mod L of its (s / L)-th tile, with
+    // weights in buffer s mod nbuf, that buffer's (s / nbuf)-th use
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long n_steps = my_tiles * F.L;
+    uint32_t issued0 = 0u, issued1 = 0u, used0 = 0u, used1 = 0u;   // thread 0: copies issued / waited
+    auto issue = [&](long long st) {
+        const int b = (int)(st % nbuf);
+        const TcLayer &Z = F.lay[F.L - 1 - (int)(st % F.L)];
+        proxy_fence();   // earlier generic reads of the buffer come before the async write
+        bulk_copy_g2s(b ? wbuf1 : wbuf0, mirror + Z.off, Z.bytes, &wbar[b]);
+        if (b) ++issued1; else ++issued0;
+    };
+    if (tid == 0 && n_steps > 0) issue(0);
+    long long step = 0;
 
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const long long jr = tile * kTcRows + row;   // this row's sample, relative to i0
@@ -272,17 +306,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         float lq = 0.f;
-        for (int l = F.L - 1; l >= 0 && ok; --l) {
+        for (int l = F.L - 1; l >= 0 && ok; --l, ++step) {
             const TcLayer &Y = F.lay[l];
-            // the previous layer's MMAs, TMEM reads and coordinate updates are complete
+            // the previous layer's MMAs, TMEM reads, bias reads and coordinate updates are complete
             before_sync();
             __syncthreads();
             after_sync();
-            {
-                const uint4 *src = reinterpret_cast<const uint4 *>(mirror + Y.off);
-                uint4 *dst = reinterpret_cast<uint4 *>(wbuf);
-                for (uint32_t e = tid; e < Y.bytes / 16u; e += kTcThreads) dst[e] = src[e];
+            // the next step's weights into the other buffer (with one buffer: this step's), then
+            // wait for this step's
+            const int b = (int)(step % nbuf);
+            if (tid == 0) {
+                if (nbuf == 2 && step + 1 < n_steps) issue(step + 1);
+                if (nbuf == 1) issue(step);
             }
+            if (!__syncthreads_and(mbar_wait(&wbar[b], (uint32_t)((step / nbuf) & 1)))) { ok = false; break; }
+            if (tid == 0) {
+                if (b) ++used1; else ++used0;
+            }
+            const unsigned char *wbuf = b ? wbuf1 : wbuf0;
             const unsigned char *W1 = wbuf, *W2 = wbuf + Y.oW2, *W3 = wbuf + Y.oW3;
             const float *b1 = reinterpret_cast<const float *>(wbuf + Y.ob1);
             const float *b2 = reinterpret_cast<const float *>(wbuf + Y.ob2);
@@ -359,7 +400,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lq_out) lq_out[jr] = lq;
         }
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        // bulk copies still in flight write this CTA's shared memory: wait for them (bounded)
+        for (; used0 < issued0; ++used0) mbar_wait(&wbar[0], used0 & 1u);
+        for (; used1 < issued1; ++used1) mbar_wait(&wbar[1], used1 & 1u);
+    }
     before_sync();
     __syncthreads();
     after_sync();
@@ -460,8 +506,16 @@ int launch_tc_hk(const TcFlow &F, const unsigned char *mirror, const TcSample &S
         }
     }
     const int HS = S.d | 1;
-    size_t smem = (size_t)((F.max_bytes + 1023u) & ~1023u) + (size_t)kTcRows * 16 * 2 + (size_t)kTcRows * H * 2 +
-                  sizeof(float) * (size_t)kTcRows * HS;
+    const size_t wstride = (size_t)((F.max_bytes + 1023u) & ~1023u);
+    const size_t rest = (size_t)kTcRows * 16 * 2 + (size_t)kTcRows * H * 2 + sizeof(float) * (size_t)kTcRows * HS;
+    // two weight buffers (the next layer's copy overlaps this layer) when two CTAs an SM still fit
+    // them, else one
+    int nbuf = 2;
+    size_t smem = 2 * wstride + rest;
+    if (2 * (smem + 1024) > (size_t)optin) {
+        nbuf = 1;
+        smem = wstride + rest;
+    }
     // TMEM holds 512 columns an SM and a CTA takes kTcCols: a third resident CTA would wait in
     // tcgen05.alloc, so shared memory is padded to keep at most two on an SM
     smem = std::max(smem, (size_t)80 * 1024);
@@ -469,7 +523,7 @@ int launch_tc_hk(const TcFlow &F, const unsigned char *mirror, const TcSample &S
     const int per_sm = 512 / kTcCols;
     const long long tiles = (n + kTcRows - 1) / kTcRows;
     const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
-    flow_sample_tc_kernel<H, K><<<(unsigned)grid, kTcThreads, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w, err);
+    flow_sample_tc_kernel<H, K><<<(unsigned)grid, kTcThreads, smem, s>>>(F, mirror, S, ip, i0, n, x, lq, w, err, nbuf);
     return cuda_status(cudaGetLastError());
 }
 
