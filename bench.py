@@ -190,7 +190,7 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "genz6-d8-n1e8 (oracle sample)", "d": D, "ncall": NCALL,
+            "config": {"workload": "genz6-d8-n1e8-fp32eval", "d": D, "ncall": NCALL,
                        "families": [W.NAMES[f] for f in W.GENZ6], "sample_cubes_per_family_step": cubes},
             "cpu_baseline": {"value": v, "unit": "samples/s", "cores": threads, "kind": "oracle",
                              "sample": f"{cubes} sub-cubes ({cubes * p} samples) of each of the 6 families per step, "
