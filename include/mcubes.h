@@ -456,6 +456,21 @@ int mcubes_last_cuda_error(void);
 /* Release the calling thread's cached device workspace and stream. */
 void mcubes_shutdown(void);
 
+/* Allocation fault hook (for testing the error paths). After mcubes_fail_alloc(n) with n >= 1,
+ * the n-th device or pinned-host allocation the library makes from then on (any thread) fails as
+ * if out of memory: the call that needed it returns MCUBES_ERR_ALLOC, having released what it
+ * had allocated, and later calls allocate afresh. n = 0 disarms the hook. The environment
+ * variable MCUBES_FAULT_ALLOC=n arms it the same way at the library's first allocation.
+ * Returns the number of allocations made since the library loaded. */
+int64_t mcubes_fail_alloc(int64_t n);
+
+/* Bounds-checked builds (libmcubes_checked.so): the kernels check every computed bin, sub-cube
+ * and probe index against its bound; a failed check skips the access and is counted. Returns
+ * the count since the last reset (and, if first is not NULL, the first failure as site << 48 |
+ * index: site 1 table bin, 2 global bin, 3 sub-cube, 4 probe slot, 5 batch tile range), then
+ * resets it when reset != 0. Returns -1 from a normal build. Synchronizes the device. */
+int64_t mcubes_checked_violations(int reset, int64_t *first);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,8 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmcubes.so")
+# MCUBES_LIB selects another build of the library (the bounds-checked libmcubes_checked.so)
+LIB_PATH = os.environ.get("MCUBES_LIB") or os.path.join(_HERE, "libmcubes.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "mcubes.h")
 
 NBINS = 500
@@ -133,6 +134,8 @@ def _load():
         "mcubes_status_string": (ctypes.c_char_p, [i32]),
         "mcubes_last_cuda_error": (i32, []),
         "mcubes_shutdown": (None, []),
+        "mcubes_checked_violations": (i64, [i32, ctypes.POINTER(i64)]),
+        "mcubes_fail_alloc": (i64, [i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -507,3 +510,17 @@ def last_cuda_error() -> int:
 
 def shutdown() -> None:
     _lib.mcubes_shutdown()
+
+
+def checked_violations(reset: bool = True):
+    """(failed index checks since the last reset, first failure's site << 48 | index) of a
+    bounds-checked build; None from a normal build."""
+    first = ctypes.c_int64(0)
+    n = int(_lib.mcubes_checked_violations(1 if reset else 0, ctypes.byref(first)))
+    return None if n < 0 else (n, int(first.value))
+
+
+def fail_alloc(n: int) -> int:
+    """Arm the allocation fault hook: the n-th allocation the library makes from now fails as if
+    out of memory (0 disarms). Returns the number of allocations made so far."""
+    return int(_lib.mcubes_fail_alloc(int(n)))

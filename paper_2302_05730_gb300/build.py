@@ -7,6 +7,10 @@ library needs only the driver. Objects are rebuilt when a source or header is ne
 
     python -m paper_2302_05730_gb300.build [--force] [--jobs N] [--checked]
 
+--checked builds a separate library, libmcubes_checked.so (objects in _build_checked), whose
+kernels check every computed bin, sub-cube and probe index against its bound and count failures
+(mcubes_checked_violations) instead of accessing out of bounds. Load it with MCUBES_LIB.
+
 MCUBES_NVCC_EXTRA adds nvcc flags to every unit (objects are not rebuilt when only it changes:
 use --force).
 """
@@ -26,6 +30,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libmcubes.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libmcubes_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -60,14 +66,15 @@ def _deps_mtime():
 
 
 def build(force: bool = False, jobs: int | None = None, checked: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     dep_t = _deps_mtime()
     extra = ["-DMCUBES_CHECKED=1"] if checked else []
     extra += os.environ.get("MCUBES_NVCC_EXTRA", "").split()   # extra nvcc flags (e.g. -D overrides)
     todo, objs = [], []
     for name, src, defs in _units():
-        obj = os.path.join(BUILD, name + ".o")
+        obj = os.path.join(build_dir, name + ".o")
         objs.append(obj)
         stale = force or not os.path.exists(obj) or \
             os.path.getmtime(obj) < max(os.path.getmtime(src), dep_t)
@@ -85,11 +92,11 @@ def build(force: bool = False, jobs: int | None = None, checked: bool = False, v
         n = jobs or min(len(todo), os.cpu_count() or 4)
         with ThreadPoolExecutor(max_workers=n) as ex:
             list(ex.map(run, todo))
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 def main():

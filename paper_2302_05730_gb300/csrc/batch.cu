@@ -131,7 +131,7 @@ struct Plan {
         const size_t b_ptr = al(sizeof(double *) * n), b_dims = al(sizeof(int) * n);
         const size_t b_rb = al(sizeof(uint32_t) * n_rebin_blocks);
         const size_t total = b_jobs + b_sums + b_C + 2 * b_grid + 3 * b_ptr + b_dims + 2 * b_rb;
-        int st = cuda_status(cudaMalloc(&dmem, total));
+        int st = cuda_status(mc_malloc((void **)&dmem, total));
         if (st) return st;
         char *q = dmem;
         d_jobs = (BatchJob *)q; q += b_jobs;
@@ -207,7 +207,7 @@ struct Plan {
                 c.samples += (size_t)(m * (uint64_t)pb[j].p);
             }
             c.n_tiles = (int)tl.size();
-            int st = cuda_status(cudaMalloc(&c.d_tiles, sizeof(BatchTile) * tl.size()));
+            int st = cuda_status(mc_malloc((void **)&c.d_tiles, sizeof(BatchTile) * tl.size()));
             if (!st) st = cuda_status(cudaMemcpy(c.d_tiles, tl.data(), sizeof(BatchTile) * tl.size(), cudaMemcpyHostToDevice));
             classes.push_back(c);
             if (st) return st;

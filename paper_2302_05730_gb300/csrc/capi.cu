@@ -1,8 +1,10 @@
 // C ABI of libmcubes.so (declared in include/mcubes.h): argument checks, stratification,
 // per-thread device workspace, the iteration loop of m-Cubes (paper Sec. 3.2) and the
 // inverse-variance combination of the iteration estimates.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -13,9 +15,68 @@ using namespace mcubes;
 
 namespace {
 thread_local int g_last_cuda_error = 0;
+
+// Allocation fault hook: allocation number g_fail_at (counted from 1 over the library's life)
+// fails; 0 = never. MCUBES_FAULT_ALLOC=n arms it at the first allocation.
+std::atomic<int64_t> g_alloc_count{0};
+std::atomic<int64_t> g_fail_at{0};
+std::atomic<int> g_env_read{0};
+
+bool alloc_should_fail()
+{
+    if (!g_env_read.exchange(1)) {
+        const char *e = std::getenv("MCUBES_FAULT_ALLOC");
+        if (e && *e) {
+            const long long n = std::atoll(e);
+            if (n > 0) g_fail_at.store(g_alloc_count.load() + n);
+        }
+    }
+    const int64_t k = g_alloc_count.fetch_add(1) + 1;
+    int64_t at = g_fail_at.load();
+    return at > 0 && k == at && g_fail_at.compare_exchange_strong(at, 0);
+}
 }  // namespace
 
 namespace mcubes {
+
+#if MCUBES_CHECKED
+// [0] failed index checks, [1] the first failure (site << 48 | index)
+__device__ unsigned long long g_bounds_chk[2];
+#endif
+
+// The bounds-check words of a checked build (null otherwise): every launch's VsampleParams
+// carries them.
+unsigned long long *bounds_words()
+{
+#if MCUBES_CHECKED
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bounds_chk) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return (unsigned long long *)p;
+#else
+    return nullptr;
+#endif
+}
+
+cudaError_t mc_malloc(void **p, size_t bytes)
+{
+    if (alloc_should_fail()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t mc_malloc_host(void **p, size_t bytes)
+{
+    if (alloc_should_fail()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
 
 int cuda_status(cudaError_t e)
 {
@@ -107,6 +168,8 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
     P.ctr2_hi = (uint32_t)iteration << 16;
     P.job = job;
     P.adjust = adjust ? 1 : 0;
+    static unsigned long long *const chk = bounds_words();
+    P.chk = chk;
     P.R = (double)kNB / (double)pb.g;
     P.R32 = (float)P.R;
     P.ycap = std::nextafter((double)kNB, 0.0);
@@ -310,26 +373,31 @@ int workspace(int iters, size_t host_bytes, Workspace *&out)
     MC_TRY(cudaGetDevice(&dev));
     Workspace &w = g_ws;
     if (w.device != dev) {
+        // all or nothing: a failure releases what was made, so the next call starts afresh
         w.release();
         w.device = dev;
-        MC_TRY(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
         const size_t gb = sizeof(double) * MCUBES_DMAX * kGridStride;
-        MC_TRY(cudaMalloc(&w.d_grid[0], gb));
-        MC_TRY(cudaMalloc(&w.d_grid[1], gb));
-        MC_TRY(cudaMalloc(&w.d_C, sizeof(double) * MCUBES_DMAX * kNB));
+        int st = cuda_status(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+        if (!st) st = cuda_status(mc_malloc((void **)&w.d_grid[0], gb));
+        if (!st) st = cuda_status(mc_malloc((void **)&w.d_grid[1], gb));
+        if (!st) st = cuda_status(mc_malloc((void **)&w.d_C, sizeof(double) * MCUBES_DMAX * kNB));
+        if (st) {
+            w.release();
+            return st;
+        }
     }
     if (iters > w.iter_cap) {
         if (w.d_iter) MC_TRY(cudaFree(w.d_iter));
         w.d_iter = nullptr;
         w.iter_cap = 0;
-        MC_TRY(cudaMalloc(&w.d_iter, sizeof(double) * 2 * (size_t)iters));
+        MC_TRY(mc_malloc((void **)&w.d_iter, sizeof(double) * 2 * (size_t)iters));
         w.iter_cap = iters;
     }
     if (host_bytes > w.h_pin_bytes) {
         if (w.h_pin) MC_TRY(cudaFreeHost(w.h_pin));
         w.h_pin = nullptr;
         w.h_pin_bytes = 0;
-        MC_TRY(cudaMallocHost(&w.h_pin, host_bytes));
+        MC_TRY(mc_malloc_host((void **)&w.h_pin, host_bytes));
         w.h_pin_bytes = host_bytes;
     }
     out = &w;
@@ -413,6 +481,38 @@ const char *mcubes_status_string(int status)
 int mcubes_last_cuda_error(void) { return g_last_cuda_error; }
 
 void mcubes_shutdown(void) { g_ws.release(); }
+
+int64_t mcubes_checked_violations(int reset, int64_t *first)
+{
+#if MCUBES_CHECKED
+    unsigned long long *w = bounds_words();
+    if (!w) return -1;
+    unsigned long long h[2] = {0ull, 0ull};
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h, w, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    if (first) *first = (int64_t)h[1];
+    if (reset) {
+        const unsigned long long z[2] = {0ull, 0ull};
+        if (cudaMemcpy(w, z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) (void)cudaGetLastError();
+    }
+    return (int64_t)h[0];
+#else
+    (void)reset;
+    if (first) *first = 0;
+    return -1;
+#endif
+}
+
+int64_t mcubes_fail_alloc(int64_t n)
+{
+    g_env_read.store(1);   // an explicit call overrides the environment
+    const int64_t made = g_alloc_count.load();
+    g_fail_at.store(n > 0 ? made + n : 0);
+    return made;
+}
 
 int mcubes_stratify(int d, int64_t ncall, int64_t *g, int64_t *m, int64_t *p)
 {

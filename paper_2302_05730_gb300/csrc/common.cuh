@@ -42,6 +42,26 @@ __host__ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c
     return Words4{c0, c1, c2, c3};
 }
 
+// Bounds checks of bounds-checked builds (-DMCUBES_CHECKED=1). mc_check(chk, i, n, site) is true
+// when 0 <= i < n; otherwise it counts the failure in chk[0], records the first as
+// site << 48 | index in chk[1], and returns false so that the caller skips the access. In normal
+// builds it is the constant true.
+#ifndef MCUBES_CHECKED
+#define MCUBES_CHECKED 0
+#endif
+__device__ __forceinline__ bool mc_check(unsigned long long *chk, long long i, long long n, unsigned site)
+{
+#if MCUBES_CHECKED
+    if (i >= 0 && i < n) return true;
+    if (chk != nullptr && atomicAdd(&chk[0], 1ull) == 0ull)
+        chk[1] = ((unsigned long long)site << 48) | ((unsigned long long)i & 0xFFFFFFFFFFFFull);
+    return false;
+#else
+    (void)chk; (void)i; (void)n; (void)site;
+    return true;
+#endif
+}
+
 // Integrand parameters as the kernels consume them. The FP64 path reads a and u as given;
 // the FP32 path reads pre-scaled single-precision forms prepared on the host (see
 // integrands.cuh for what each family stores).
@@ -86,6 +106,7 @@ struct VsampleParams {
     double inv_pp1;          // 1 / (p (p - 1))
     double fscale;           // FP32 path: f = fscale * (kernel's scaled integrand)
     double log_fscale;       // log(fscale), or 0
+    unsigned long long *chk; // bounds-checked builds: [0] failed checks, [1] the first one (else null)
     IntegrandParams ip;
 };
 

@@ -651,7 +651,7 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
                          2 * al(sizeof(float) * nchunk * d) + al(sizeof(float) * nchunk) + al(wbytes) +
                          al(fused_ok ? sample_bytes : 256);
     char *mem = nullptr;
-    if ((st = cuda_status(cudaMalloc(&mem, bytes)))) return st;
+    if ((st = cuda_status(mc_malloc((void **)&mem, bytes)))) return st;
     char *q = mem;
     auto take = [&](size_t b) { char *r = q; q += al(b); return r; };
     double *d_grid = (double *)take(sizeof(double) * d * kGS);

@@ -23,6 +23,10 @@ inline int param_len(int fid, int d) { return fid == 9 ? d * d + d : 2 * d; }
 
 // Host helpers of capi.cu, shared with the batched path.
 int cuda_status(cudaError_t e);   // MCUBES_* status of a CUDA error (records it per thread)
+// Every device / pinned-host allocation of the library goes through these (the fault hook of
+// mcubes_fail_alloc sits here).
+cudaError_t mc_malloc(void **p, size_t bytes);
+cudaError_t mc_malloc_host(void **p, size_t bytes);
 int stratify(int d, int64_t n, int64_t *g, int64_t *m, int64_t *p);
 int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, int iteration,
             uint32_t job, int adjust, int prec, Problem &pb);

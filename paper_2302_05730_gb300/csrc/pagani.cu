@@ -662,7 +662,7 @@ extern "C" int mcubes_pagani_integrate(int integrand_id, const double *params, i
     const size_t bytes = 4 * al(rb) + 2 * al(sizeof(double) * cap) + 3 * al(sizeof(int) * cap) +
                          al(sizeof(int) * nb_max) + al(sizeof(double) * 4) + al(sizeof(long long));
     char *mem = nullptr;
-    if ((st = cuda_status(cudaMalloc(&mem, bytes)))) return st;
+    if ((st = cuda_status(mc_malloc((void **)&mem, bytes)))) return st;
     char *q = mem;
     auto take = [&](size_t b) { char *r = q; q += al(b); return r; };
     double *lo[2] = {(double *)take(rb), (double *)take(rb)};

@@ -307,6 +307,7 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
     }
 
     for (; t < t_end; ++t) {
+        if (!mc_check(P.chk, t, P.m, 3)) break;
         T S1 = T(0), S2 = T(0), w0 = T(0);   // FP64: plain sums; FP32: w0 and shifted sums
 
         for (uint32_t q = 0; q < p; ++q) {
@@ -346,7 +347,8 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
                         T2 bw;
                         if constexpr (F32) {
                             kb = __fadd_rd(yn, magic);
-                            const uint32_t kbits = __float_as_uint(kb);
+                            uint32_t kbits = __float_as_uint(kb);
+                            if (!mc_check(P.chk, (long long)kbits - (long long)kMagicBits, kNB, 1)) kbits = kMagicBits;
                             bw = lds_f32x2(kbits * 8u + (tab_adj + (uint32_t)(i * kNB * 8)));
                             if constexpr (kGlobalHist) {
                                 kofs[i] = i * kNB + (int)(kbits - kMagicBits);
@@ -356,7 +358,8 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
                             kb = __fsub_rn(kb, magic);
                         } else {
                             kb = __dadd_rd(yn, magic);
-                            const int k = __double2loint(kb);
+                            int k = __double2loint(kb);
+                            if (!mc_check(P.chk, k, kNB, 1)) k = 0;
                             bw = tab[i * kNB + k];
                             kofs[i] = i * kNB + k;
                             kb = __dsub_rn(kb, magic);
@@ -420,7 +423,8 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
                 if constexpr (kGlobalHist) {
                     const double hg = (double)h * gscale;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) atomicAdd(&P.C[kofs[i]], hg);
+                    for (int i = 0; i < D; ++i)
+                        if (mc_check(P.chk, kofs[i], D * kNB, 2)) atomicAdd(&P.C[kofs[i]], hg);
                 } else if constexpr (HK == 1) {
                     if constexpr (F32) {
 #pragma unroll
@@ -449,7 +453,8 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
         }
 
         // per sub-cube mean and variance (Algorithm 2 UpdateVariance)
-        const bool probe_this = P.probe != nullptr && (t & P.probe_mask) == 0;
+        const bool probe_this = P.probe != nullptr && (t & P.probe_mask) == 0 &&
+                                mc_check(P.chk, t >> P.probe_shift, (long long)(P.m >> P.probe_shift) + 1, 4);
         if constexpr (F32) {
             // Single precision on the shifted sums: mean = w0 + D1/p, p(p-1) V = D2 - D1^2/p.
             // The shift keeps D2 - D1^2/p free of the cancellation of S2 - S1^2/p. The
@@ -697,6 +702,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
             hsig = histogram_scale<F32>(P);
             stage_grid<D, F32>(P.grid, tab, hist, shared_hist ? D * kNB * (int)(sizeof(T) / 4) : 0);
         }
+        if (!mc_check(P.chk, (long long)tile.c1 - 1, P.m, 5) || !mc_check(P.chk, tile.c0, (long long)tile.c1, 5)) continue;
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
