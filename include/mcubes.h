@@ -28,6 +28,13 @@
  *     rotated Gaussian takes d^2 + d (see MCUBES_ROTATED_GAUSSIAN).
  *   - Calls from different host threads are safe. Each thread has its own cached workspace,
  *     released by mcubes_shutdown() on that thread.
+ *   - Run log: with MCUBES_LOG=<file> in the environment, mcubes_integrate, mcubes_integrate_ex
+ *     and mcubes_integrate_range append JSON lines to the file: one per iteration
+ *     ({"event": "iteration", "it", "adjust", "I", "sigma", "running_estimate", "running_error",
+ *     "running_chi2_dof", "samples"}) and one per call ({"event": "run", "integrand", "d",
+ *     "samples_per_iter", "itmax", "iter_adjust", "iterations", "precision", "ms",
+ *     "samples_per_s", and for whole runs "estimate", "error", "chi2_dof"}). Non-finite values
+ *     are written as null.
  */
 #ifndef MCUBES_H
 #define MCUBES_H

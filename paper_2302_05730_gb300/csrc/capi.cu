@@ -1,11 +1,14 @@
 // C ABI of libmcubes.so (declared in include/mcubes.h): argument checks, stratification,
 // per-thread device workspace, the iteration loop of m-Cubes (paper Sec. 3.2) and the
 // inverse-variance combination of the iteration estimates.
+#include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "../../include/mcubes.h"
@@ -596,6 +599,88 @@ int run_range(Problem &pb, int itmax, int iter_adjust, int it_begin, int it_end,
 
 extern "C" {
 
+namespace {
+
+// Run log: with MCUBES_LOG=<file> in the environment, every whole-run call appends one JSON line
+// per iteration (its estimate and sigma, and the running inverse-variance combination with its
+// chi^2/dof) and a summary line (the result, wall time, samples/s).
+void json_num(std::string &o, double v)
+{
+    char b[40];
+    if (std::isfinite(v)) {
+        std::snprintf(b, sizeof(b), "%.17g", v);
+        o += b;
+    } else {
+        o += "null";
+    }
+}
+
+void log_run(const char *call, const Problem &pb, int itmax, int iter_adjust, int it_begin,
+             const std::vector<double> &I, const std::vector<double> &V, const mcubes_result *res, double ms)
+{
+    const char *path = std::getenv("MCUBES_LOG");
+    if (!path || !*path) return;
+    std::string o;
+    char b[256];
+    const double samples = (double)pb.m * (double)pb.p;
+    double sw = 0.0, swI = 0.0, swI2 = 0.0;
+    for (size_t k = 0; k < I.size(); ++k) {
+        const int it = it_begin + (int)k;
+        std::snprintf(b, sizeof(b), "{\"event\": \"iteration\", \"call\": \"%s\", \"it\": %d, \"adjust\": %s, \"I\": ", call,
+                      it, it < iter_adjust ? "true" : "false");
+        o += b;
+        json_num(o, I[k]);
+        o += ", \"sigma\": ";
+        json_num(o, std::sqrt(V[k]));
+        // running combination over this call's iterations so far
+        if (V[k] > 0.0) {
+            const double w = 1.0 / V[k];
+            sw += w;
+            swI += w * I[k];
+            swI2 += w * I[k] * I[k];
+        }
+        const double est = sw > 0.0 ? swI / sw : I[k];
+        const double chi2 = k > 0 && sw > 0.0 ? std::max(0.0, swI2 - swI * swI / sw) / (double)k : 0.0;
+        o += ", \"running_estimate\": ";
+        json_num(o, est);
+        o += ", \"running_error\": ";
+        json_num(o, sw > 0.0 ? 1.0 / std::sqrt(sw) : 0.0);
+        o += ", \"running_chi2_dof\": ";
+        json_num(o, chi2);
+        std::snprintf(b, sizeof(b), ", \"samples\": %.0f}\n", samples);
+        o += b;
+    }
+    std::snprintf(b, sizeof(b),
+                  "{\"event\": \"run\", \"call\": \"%s\", \"integrand\": %d, \"d\": %d, \"samples_per_iter\": %.0f, "
+                  "\"itmax\": %d, \"iter_adjust\": %d, \"iterations\": %d, \"precision\": \"%s\", \"ms\": ",
+                  call, pb.fid, pb.d, samples, itmax, iter_adjust, (int)I.size(),
+                  pb.prec == MCUBES_FP32_EVAL ? "fp32_eval" : "fp64");
+    o += b;
+    json_num(o, ms);
+    o += ", \"samples_per_s\": ";
+    json_num(o, ms > 0.0 ? samples * (double)I.size() / (ms * 1e-3) : 0.0);
+    if (res) {
+        o += ", \"estimate\": ";
+        json_num(o, res->estimate);
+        o += ", \"error\": ";
+        json_num(o, res->error);
+        o += ", \"chi2_dof\": ";
+        json_num(o, res->chi2_dof);
+    }
+    o += "}\n";
+    if (FILE *f = std::fopen(path, "a")) {
+        std::fwrite(o.data(), 1, o.size(), f);
+        std::fclose(f);
+    }
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
 int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t ncall, int itmax,
                         int iter_adjust, uint64_t seed, int precision, const mcubes_tuning *tune,
                         void *stream, double *iter_out, const double *grid_in, double *grid_out,
@@ -609,7 +694,9 @@ int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t n
     if (!st) st = prepare(integrand_id, params, d, ncall, seed, 0, 0, iter_adjust > 0, precision, pb);
     if (!st && grid_in && !grid_ok(grid_in, d)) st = MCUBES_ERR_INVALID_ARG;
     std::vector<double> I, V;
+    const auto t0 = std::chrono::steady_clock::now();
     if (!st) st = run_range(pb, itmax, iter_adjust, 0, itmax, grid_in, 0.0, tune, stream, I, V, grid_out);
+    const double ms = ms_since(t0);
     if (st) {
         if (out) out->status = st;
         return st;
@@ -623,6 +710,7 @@ int mcubes_integrate_ex(int integrand_id, const double *params, int d, int64_t n
     out->iters_done = itmax;
     out->samples_per_iter = pb.m * pb.p;
     out->status = MCUBES_OK;
+    log_run("integrate", pb, itmax, iter_adjust, 0, I, V, out, ms);
     return MCUBES_OK;
 }
 
@@ -640,12 +728,15 @@ int mcubes_integrate_range(int integrand_id, const double *params, int d, int64_
     if (st) return st;
     if (grid_in && !grid_ok(grid_in, d)) return MCUBES_ERR_INVALID_ARG;
     std::vector<double> I, V;
+    const auto t0 = std::chrono::steady_clock::now();
     st = run_range(pb, itmax, iter_adjust, it_begin, it_end, grid_in, prev_estimate, nullptr, stream, I, V, grid_out);
+    const double ms = ms_since(t0);
     if (st) return st;
     for (int k = 0; k < it_end - it_begin; ++k) {
         iter_out[2 * k] = I[k];
         iter_out[2 * k + 1] = V[k];
     }
+    log_run("integrate_range", pb, itmax, iter_adjust, it_begin, I, V, nullptr, ms);
     return MCUBES_OK;
 }
 

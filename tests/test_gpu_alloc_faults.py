@@ -146,3 +146,41 @@ def test_environment_variable_arms_the_hook(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert "status %d" % ALLOC in out.stdout and "then 3" in out.stdout, out.stdout
+
+
+def test_run_log_lines(tmp_path):
+    """MCUBES_LOG=<file>: one JSON line per iteration and one per call, matching the returned
+    per-iteration results and estimate (a child process with the variable set)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    log = tmp_path / "run.jsonl"
+    out_json = tmp_path / "out.json"
+    code = (
+        "import sys, json; sys.path.insert(0, %r)\n"
+        "from paper_2302_05730_gb300 import capi, workloads as W\n"
+        "par = W.genz_params(W.C0, 4)\n"
+        "r = capi.integrate(W.C0, par, 4, 40000, 5, 2, 3, precision=1, return_iters=True)\n"
+        "q = capi.integrate_range(W.C0, par, 4, 40000, 5, 2, 0, 2, 3, precision=0)\n"
+        "json.dump({'est': r['estimate'], 'err': r['error'], 'iters': r['iters'].tolist()}, open(%r, 'w'))\n"
+        % (root, str(out_json)))
+    env = dict(os.environ, MCUBES_LOG=str(log))
+    p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-3000:]
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    ref = json.loads(out_json.read_text())
+    it_lines = [x for x in lines if x["event"] == "iteration" and x["call"] == "integrate"]
+    runs = [x for x in lines if x["event"] == "run"]
+    assert len(it_lines) == 5 and [x["it"] for x in it_lines] == list(range(5))
+    assert [x["adjust"] for x in it_lines] == [True, True, False, False, False]
+    for x, (I, V) in zip(it_lines, ref["iters"]):
+        assert math.isclose(x["I"], I, rel_tol=1e-15) and math.isclose(x["sigma"], math.sqrt(V), rel_tol=1e-15)
+    assert [r["call"] for r in runs] == ["integrate", "integrate_range"]
+    assert math.isclose(runs[0]["estimate"], ref["est"], rel_tol=1e-15)
+    assert math.isclose(it_lines[-1]["running_estimate"], ref["est"], rel_tol=1e-12)
+    assert runs[0]["precision"] == "fp32_eval" and runs[1]["precision"] == "fp64" and runs[1]["iterations"] == 2
+    assert runs[0]["ms"] > 0 and runs[0]["samples_per_s"] > 0
