@@ -36,8 +36,8 @@ NCALL = 10 ** 8
 # DRAM bytes (read + write) per vsample_kernel<8, oscillatory, FP32-eval> launch at d = 8, 1e8 samples
 # per iteration, from one ncu capture of this kernel as it stands: the mean over the 5 adjusting and
 # 5 frozen launches of one integration, and each kind's own mean.
-VSAMPLE_DRAM_BYTES = 104422
-VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 136141, "frozen": 72704}
+VSAMPLE_DRAM_BYTES = 125210
+VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 183245, "frozen": 67174}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts: 152 SMs, 4 SM sub-partitions x 32 lanes issue one instruction per clock.
@@ -231,7 +231,10 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
     for name, fid, par in cases:
         I = abs(exact.get(name, 1.0))
         target = (1e-3 * I) ** 2
-        # plain m-Cubes on the same integrand: per-iteration time and variance after adaptation
+        # plain m-Cubes on the same integrand: per-iteration time and variance after adaptation (after
+        # one untimed call of each precision, which sets up the kernels' launch attributes)
+        for prec in (capi.FP64, capi.FP32_EVAL):
+            capi.integrate(fid, par, 8, n_it, 2, 1, 0, precision=prec)
         t0 = time.perf_counter()
         pl = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP64, return_iters=True)
         t64 = (time.perf_counter() - t0) / 9
