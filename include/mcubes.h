@@ -306,7 +306,12 @@ int mcubes_tune_batch(int n_jobs, const mcubes_job *jobs, int precision, mcubes_
  * algorithm) and an adaptive driver around it. FP64 throughout.
  *   Rule (the paper defers it to PAGANI; the reading here): the Genz-Malik fully symmetric rule
  *   of degree 7 with its embedded rule of degree 5 on each region, f_eval = 1 + 4d + 2d(d-1) + 2^d
- *   points; I = the degree-7 estimate, E = |I7 - I5|, and the split axis of the region = the
+ *   points, and three lower-degree rules on the same points (degree 3 on the centre and the
+ *   +-l2 e_i points, degree 3 on the centre and the +-l3 e_i points, the centre alone): five
+ *   rules, as the paper's kernel accumulates. I = the degree-7 estimate; E = |R7 - R5| when the
+ *   differences of successive degrees fall at least fourfold (|R7 - R5| <= |R5 - R3| / 4 <=
+ *   |R3 - R1| / 16, each difference its largest over the two degree-3 rules), else the largest of
+ *   them; the split axis of the region = the
  *   largest fourth divided difference along the axes (ties -- within 1e-12 of the larger
  *   difference and of the largest |f| at the centre and axis points -- go to the longest side,
  *   then the lowest axis).

@@ -67,6 +67,11 @@ def lib():
             L.orc_gm_count.argtypes = [i32]
             L.orc_gm_count.restype = i32
             L.orc_gm_weights.argtypes = [i32, dp, dp]
+            L.orc_gm_rules.argtypes = [i32, dp]
+            L.orc_pagani_rules.argtypes = [i32, i32, dp, dp, dp, dp]
+            L.orc_pagani_rules.restype = i32
+            L.orc_pagani_error.argtypes = [dp]
+            L.orc_pagani_error.restype = ctypes.c_double
             L.orc_gm_points.argtypes = [i32, dp, ctypes.POINTER(ctypes.c_int32)]
             L.orc_gm_points.restype = i32
             L.orc_pagani_evaluate.argtypes = [i32, i32, dp, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_int32), dp]
@@ -212,6 +217,26 @@ def gm_rule(d: int):
     w5 = np.empty(5)
     L.orc_gm_weights(d, _dp(w7), _dp(w5))
     return U, cls, w7, w5
+
+
+def gm_rules(d: int) -> np.ndarray:
+    """Class weights (5 rules x 5 classes) of R7, R5, R3a, R3b, R1 on [-1, 1]^d."""
+    W = np.empty((5, 5))
+    lib().orc_gm_rules(d, _dp(W))
+    return W
+
+
+def pagani_rules(fid, d, params, lo, ln) -> np.ndarray:
+    """The five rule values (R7, R5, R3a, R3b, R1) of one region."""
+    out = np.empty(5)
+    _check(lib().orc_pagani_rules(fid, d, _dp(_f64(params)), _dp(_f64(lo)), _dp(_f64(ln)), _dp(out)), "pagani_rules")
+    return out
+
+
+def pagani_error(rules) -> float:
+    """The region error estimate from the five rule values (R7, R5, R3a, R3b, R1)."""
+    R = np.ascontiguousarray(rules, dtype=np.float64)
+    return float(lib().orc_pagani_error(_dp(R)))
 
 
 def pagani_evaluate(fid, d, params, lo, length, want_fourth=False):

@@ -18,8 +18,18 @@
  *             w3 = 2^d (1820 - 400 d)/19683, w4 = 2^d 200/19683, w5 = 6859/19683;
  *   degree 5: w1 = 2^d (729 - 950 d + 50 d^2)/729, w2 = 2^d 245/486,
  *             w3 = 2^d (265 - 100 d)/1458, w4 = 2^d 25/729, w5 = 0.
+ * The paper's kernel accumulates five quadrature rules per region and takes the error from them;
+ * the reading adds three lower-degree rules on the same points, from the moment conditions
+ * (exact for 1 and x_i^2 on [-1, 1]^d, whose integrals are 2^d and 2^d / 3):
+ *   R3a, degree 3 on classes 1, 2: w2 = 2^d / (6 l2^2), w1 = 2^d - 2 d w2;
+ *   R3b, degree 3 on classes 1, 3: w3 = 2^d / (6 l3^2), w1 = 2^d - 2 d w3;
+ *   R1, degree 1: w1 = 2^d (the centre).
  * Integral estimate I7 = (V / 2^d) sum_k w7_k S_k, with S_k the sum of f over class k and V the
- * region's volume; error estimate E = |I7 - I5|; split axis: the largest fourth divided
+ * region's volume. Error estimate from the differences of successive degrees,
+ *   D7 = |R7 - R5|, D5 = max(|R5 - R3a|, |R5 - R3b|), D3 = max(|R3a - R1|, |R3b - R1|):
+ * E = D7 when each difference is at most a quarter of the previous one (D7 <= D5 / 4 and
+ * D5 <= D3 / 4: the rules are in their asymptotic range, where D7, the degree-5 rule's error,
+ * bounds the degree-7 rule's), and E = max(D7, D5, D3) otherwise. Split axis: the largest fourth divided
  * difference |f(l2 e_i) + f(-l2 e_i) - 2 f(0) - (l2/l3)^2 (f(l3 e_i) + f(-l3 e_i) - 2 f(0))|,
  * with ties going to the longest side, then the lowest axis. Two differences tie when they are
  * within 1e-12 of the larger of them and of the largest |f| at the centre and axis points (below
@@ -54,6 +64,10 @@ int orc_gm_count(int d)
 }
 
 /* Rule weights per class 1..5 (index 0..4), degree 7 and degree 5, on [-1, 1]^d. */
+/* The five rules' class weights on [-1, 1]^d: W[r][k] for rule r = R7, R5, R3a, R3b, R1 and
+ * class k = 1..5 (index k - 1). */
+void orc_gm_rules(int d, double *W /* 5 x 5 */);
+
 void orc_gm_weights(int d, double *w7, double *w5)
 {
     const double two_d = ldexp(1.0, d), dd = (double)d;
@@ -67,6 +81,28 @@ void orc_gm_weights(int d, double *w7, double *w5)
     w5[2] = two_d * (265.0 - 100.0 * dd) / 1458.0;
     w5[3] = two_d * 25.0 / 729.0;
     w5[4] = 0.0;
+}
+
+void orc_gm_rules(int d, double *W)
+{
+    const double two_d = ldexp(1.0, d);
+    memset(W, 0, sizeof(double) * 25);
+    orc_gm_weights(d, W, W + 5);
+    W[2 * 5 + 1] = two_d / (6.0 * pg_lambda2(2));
+    W[2 * 5 + 0] = two_d - 2.0 * d * W[2 * 5 + 1];
+    W[3 * 5 + 2] = two_d / (6.0 * pg_lambda2(3));
+    W[3 * 5 + 0] = two_d - 2.0 * d * W[3 * 5 + 2];
+    W[4 * 5 + 0] = two_d;
+}
+
+/* The error estimate from the five rule values R[0..4] = R7, R5, R3a, R3b, R1 (see the header). */
+double orc_pagani_error(const double *R)
+{
+    const double d7 = fabs(R[0] - R[1]);
+    const double d5 = fmax(fabs(R[1] - R[2]), fabs(R[1] - R[3]));
+    const double d3 = fmax(fabs(R[2] - R[4]), fabs(R[3] - R[4]));
+    if (d7 <= 0.25 * d5 && d5 <= 0.25 * d3) return d7;
+    return fmax(d7, fmax(d5, d3));
 }
 
 /* All rule points on [-1, 1]^d in the order centre, class 2 (axis-major, + then -), class 3,
@@ -107,7 +143,36 @@ int orc_gm_points(int d, double *U, int *cls)
     return p == n ? 0 : 1;
 }
 
-/* One region: I (degree-7 estimate), E = |I7 - I5|, the split axis, and (if fourth != NULL) the
+/* The five rule values (R7, R5, R3a, R3b, R1, scaled to the region) of one region. */
+int orc_pagani_rules(int id, int d, const double *par, const double *lo, const double *len, double *Rout)
+{
+    const int n = orc_gm_count(d);
+    if (!n) return 2;
+    double *U = malloc(sizeof(double) * (size_t)n * d);
+    int *cls = malloc(sizeof(int) * (size_t)n);
+    if (!U || !cls || orc_gm_points(d, U, cls)) {
+        free(U);
+        free(cls);
+        return 1;
+    }
+    double x[PG_DMAX], S[5] = {0, 0, 0, 0, 0}, vol = 1.0, W[25];
+    for (int i = 0; i < d; ++i) vol *= len[i];
+    for (int p = 0; p < n; ++p) {
+        for (int i = 0; i < d; ++i) x[i] = lo[i] + 0.5 * len[i] * (1.0 + U[(size_t)p * d + i]);
+        S[cls[p] - 1] += orc_integrand(id, d, par, x, 0);
+    }
+    orc_gm_rules(d, W);
+    for (int r = 0; r < 5; ++r) {
+        Rout[r] = 0.0;
+        for (int k = 0; k < 5; ++k) Rout[r] += W[r * 5 + k] * S[k];
+        Rout[r] *= vol / ldexp(1.0, d);
+    }
+    free(U);
+    free(cls);
+    return 0;
+}
+
+/* One region: I (degree-7 estimate), E (from the five rules), the split axis, and (if fourth != NULL) the
  * d fourth divided differences. Class sums are plain sequential sums in point order. */
 int orc_pagani_evaluate(int id, int d, const double *par, const double *lo, const double *len, double *I,
                         double *E, int *axis, double *fourth)
@@ -130,18 +195,15 @@ int orc_pagani_evaluate(int id, int d, const double *par, const double *lo, cons
         fv[p] = orc_integrand(id, d, par, x, 0);
         S[cls[p] - 1] += fv[p];
     }
-    double w7[5], w5[5];
-    orc_gm_weights(d, w7, w5);
-    double i7 = 0.0, i5 = 0.0;
-    for (int k = 0; k < 5; ++k) {
-        i7 += w7[k] * S[k];
-        i5 += w5[k] * S[k];
-    }
+    double W[25], R[5] = {0, 0, 0, 0, 0};
+    orc_gm_rules(d, W);
     const double scale = vol / ldexp(1.0, d);
-    i7 *= scale;
-    i5 *= scale;
-    *I = i7;
-    *E = fabs(i7 - i5);
+    for (int r = 0; r < 5; ++r) {
+        for (int k = 0; k < 5; ++k) R[r] += W[r * 5 + k] * S[k];
+        R[r] *= scale;
+    }
+    *I = R[0];
+    *E = orc_pagani_error(R);
     /* fourth differences: class-2 points of axis i at 1 + 2i (+), 2 + 2i (-); class 3 at 1 + 2d + 2i, ... */
     const double r = pg_lambda2(2) / pg_lambda2(3), f0 = fv[0];
     /* rounding noise of a fourth difference is a few ulps of the largest |f| it combines: below

@@ -12,7 +12,12 @@
 //   degree-7 weights 2^d (12824 - 9120 d + 400 d^2)/19683, 2^d 980/6561, 2^d (1820 - 400 d)/19683,
 //   2^d 200/19683, 6859/19683; degree-5 weights 2^d (729 - 950 d + 50 d^2)/729, 2^d 245/486,
 //   2^d (265 - 100 d)/1458, 2^d 25/729, 0.
-// I = I7 (scaled by volume / 2^d), E = |I7 - I5|, split axis = the largest fourth divided difference
+// Five rules per region, as the paper's kernel accumulates: R7 and R5 above, and from the moment
+// conditions (exact for 1 and x_i^2) R3a on classes 1, 2 (w2 = 2^d / (6 l2^2), w1 = 2^d - 2d w2),
+// R3b on classes 1, 3 (w3 = 2^d / (6 l3^2), w1 = 2^d - 2d w3) and R1, the centre (w1 = 2^d).
+// I = R7 (scaled by volume / 2^d). E from the differences of successive degrees, D7 = |R7 - R5|,
+// D5 = max(|R5 - R3a|, |R5 - R3b|), D3 = max(|R3a - R1|, |R3b - R1|): E = D7 when D7 <= D5 / 4 and
+// D5 <= D3 / 4 (the asymptotic range), else max(D7, D5, D3). Split axis = the largest fourth divided difference
 // |f(l2 e_i) + f(-l2 e_i) - 2 f(0) - (l2/l3)^2 (f(l3 e_i) + f(-l3 e_i) - 2 f(0))|, ties to the
 // longest side, then the lowest axis; differences within 1e-12 of the larger one and of the
 // largest |f| at the centre and axis points tie (below that they are rounding noise). FP64
@@ -43,7 +48,7 @@ constexpr int kScanBlock = 1024;
 struct PgRule {
     int d, n, base3, base4, base5;
     double l2, l3, l4, l5, r23;
-    double w7[5], w5[5];
+    double w[5][5];   // class weights of the rules R7, R5, R3a, R3b, R1
 };
 
 PgRule make_rule(int d)
@@ -60,16 +65,21 @@ PgRule make_rule(int d)
     R.l5 = std::sqrt(9.0 / 19.0);
     R.r23 = (9.0 / 70.0) / (9.0 / 10.0);
     const double p2 = std::ldexp(1.0, d), dd = (double)d;
-    R.w7[0] = p2 * (12824.0 - 9120.0 * dd + 400.0 * dd * dd) / 19683.0;
-    R.w7[1] = p2 * 980.0 / 6561.0;
-    R.w7[2] = p2 * (1820.0 - 400.0 * dd) / 19683.0;
-    R.w7[3] = p2 * 200.0 / 19683.0;
-    R.w7[4] = 6859.0 / 19683.0;
-    R.w5[0] = p2 * (729.0 - 950.0 * dd + 50.0 * dd * dd) / 729.0;
-    R.w5[1] = p2 * 245.0 / 486.0;
-    R.w5[2] = p2 * (265.0 - 100.0 * dd) / 1458.0;
-    R.w5[3] = p2 * 25.0 / 729.0;
-    R.w5[4] = 0.0;
+    std::memset(R.w, 0, sizeof(R.w));
+    R.w[0][0] = p2 * (12824.0 - 9120.0 * dd + 400.0 * dd * dd) / 19683.0;
+    R.w[0][1] = p2 * 980.0 / 6561.0;
+    R.w[0][2] = p2 * (1820.0 - 400.0 * dd) / 19683.0;
+    R.w[0][3] = p2 * 200.0 / 19683.0;
+    R.w[0][4] = 6859.0 / 19683.0;
+    R.w[1][0] = p2 * (729.0 - 950.0 * dd + 50.0 * dd * dd) / 729.0;
+    R.w[1][1] = p2 * 245.0 / 486.0;
+    R.w[1][2] = p2 * (265.0 - 100.0 * dd) / 1458.0;
+    R.w[1][3] = p2 * 25.0 / 729.0;
+    R.w[2][1] = p2 / (6.0 * (9.0 / 70.0));
+    R.w[2][0] = p2 - 2.0 * dd * R.w[2][1];
+    R.w[3][2] = p2 / (6.0 * (9.0 / 10.0));
+    R.w[3][0] = p2 - 2.0 * dd * R.w[3][2];
+    R.w[4][0] = p2;
     return R;
 }
 
@@ -135,8 +145,8 @@ __device__ double eval64(int fid, int d, const IntegrandParams &ip, const double
     }
 }
 
-// A region's estimates from its class sums S and its centre and axis values fax: I = I7,
-// E = |I7 - I5| and the split axis (largest fourth difference; ties -- within 1e-12 of the
+// A region's estimates from its class sums S and its centre and axis values fax: I = R7, E from
+// the five rules (above) and the split axis (largest fourth difference; ties -- within 1e-12 of the
 // larger difference and of the largest |f| at those points -- to the longest side, then the
 // lowest axis).
 __device__ void finish_region(const PgRule &R, const double (&S)[5], const double *fax, const double *rlen,
@@ -145,16 +155,20 @@ __device__ void finish_region(const PgRule &R, const double (&S)[5], const doubl
     const int d = R.d;
     double vol = 1.0;
     for (int i = 0; i < d; ++i) vol *= rlen[i];
-    double i7 = 0.0, i5 = 0.0;
-    for (int k = 0; k < 5; ++k) {
-        i7 += R.w7[k] * S[k];
-        i5 += R.w5[k] * S[k];
-    }
     const double scale = vol / ldexp(1.0, d);
-    i7 *= scale;
-    i5 *= scale;
-    *I = i7;
-    *E = fabs(i7 - i5);
+    double Q[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        double v = 0.0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v += R.w[r][k] * S[k];
+        Q[r] = v * scale;
+    }
+    *I = Q[0];
+    const double d7 = fabs(Q[0] - Q[1]);
+    const double d5 = fmax(fabs(Q[1] - Q[2]), fabs(Q[1] - Q[3]));
+    const double d3 = fmax(fabs(Q[2] - Q[4]), fabs(Q[3] - Q[4]));
+    *E = (d7 <= 0.25 * d5 && d5 <= 0.25 * d3) ? d7 : fmax(d7, fmax(d5, d3));
     const double f0 = fax[0];
     double fscale = fabs(f0);   // the rounding-noise scale of the fourth differences
     for (int p = 1; p < R.base4; ++p) fscale = fmax(fscale, fabs(fax[p]));
