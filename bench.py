@@ -61,6 +61,27 @@ def sm_peak_ops(sm_mhz: float) -> float:
     return SMS * LANES_PER_SM * sm_mhz * 1e6
 
 
+def pipe_bounds(rates: dict, fams, d: int, kinds: dict, sm_mhz: float) -> dict:
+    """Pipe-level roofline of the V-Sample kernels: per launch kind, the SM clocks a sample needs on
+    each pipe at the measured unit rates (mcubes_unit_rates) -- Philox calls on the integer
+    multiply pipe, the shared-memory pipe (table gathers, plus the histogram's u32 atomics when
+    adjusting: both use it) and instruction issue of the algorithmic operations -- their maximum
+    (the bound, every pipe overlapped), and the measured clocks a sample against it."""
+    out = {}
+    for name, adj in (("adjusting", True), ("frozen", False)):
+        ops = float(np.mean([algorithmic_ops_per_sample(f, d, adj, True) for f in fams]))
+        t = {"philox": math.ceil(d / 4) / rates["philox_calls"],
+             "shared_memory": d / rates["shared_gather8_lanes"] +
+             (d / rates["shared_atomic_u32x8_lanes"] if adj else 0.0),
+             "issue": ops / LANES_PER_SM}
+        bound = max(t.values())
+        measured = SMS * sm_mhz * 1e6 / kinds[name]["samples_per_s"]
+        out[name] = {"clk_per_sample_by_pipe": t, "bound_clk_per_sample": bound,
+                     "binding_pipe": max(t, key=t.get), "measured_clk_per_sample": measured,
+                     "frac_of_pipe_bound": bound / measured}
+    return out
+
+
 # ------------------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -353,6 +374,7 @@ def main():
     ap.add_argument("--pagani-only", action="store_true", help="only the PAGANI leg (profiling runs)")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling runs)")
     ap.add_argument("--train-steps", type=int, default=2000, help="flow training steps in the learned leg")
+    ap.add_argument("--unit-rates", action="store_true", help="only the unit-rate microbenchmarks")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -374,6 +396,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
+    if args.unit_rates:
+        if rank == 0:
+            print(json.dumps({"unit_rates_per_sm_clock": capi.unit_rates()}), flush=True)
+        return
     if args.learned_only:
         if rank == 0:
             print(json.dumps({"learned": learned_leg(capi, W, args.train_steps)}), flush=True)
@@ -528,6 +554,12 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---- pipe-level roofline of the same launches, from the device's measured unit rates (after the
+    # timed region)
+    unit = capi.unit_rates()
+    pipes = dict(pipe_bounds(unit, fams, D, kinds, sm_mhz), unit_rates_per_sm_clock=unit,
+                 basis="mcubes_unit_rates microbenchmarks on this device; bound = the slowest pipe, all overlapped")
+
     # ---- plain FP64 arm (same steps)
     f64_steps = 3
     total64, _, res64 = timed(capi.FP64, f64_steps, 3)
@@ -658,7 +690,8 @@ def main():
                          "kernel": "vsample_kernel<8, fid, FP32, HK> (adjusting launches: HK = 2, fixed-point "
                                    "histogram, 152 x 1024; frozen launches: HK = 0, 608 x 256)",
                          "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_kms, "by_kind": kinds,
-                         "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})"},
+                         "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})",
+                         "pipes": pipes},
             "cpu_baseline": cpu,
             "time_to_1e-3": tta,
             "batch": batch,

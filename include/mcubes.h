@@ -468,6 +468,18 @@ int mcubes_last_cuda_error(void);
 /* Release the calling thread's cached device workspace and stream. */
 void mcubes_shutdown(void);
 
+/* Unit rates of the current device, measured by microbenchmarks (about 50 ms): the per-SM
+ * throughput of the operations the V-Sample kernels are built from, per SM clock at the
+ * device's maximum SM clock (cudaDevAttrClockRate). out[0..min(n_out, 7) - 1] receives:
+ *   0: FP32 fused multiply-adds (lanes); 1: FP64 fused multiply-adds (lanes);
+ *   2: exp2f (lanes); 3: Philox4x32-10 calls;
+ *   4: random 8-byte shared-memory gathers from an 8 x 500 table (lanes);
+ *   5: random FP32 shared atomics into an 8 x 500 histogram (lanes);
+ *   6: random u32 shared atomics with their old value into 8 lane-interleaved copies of an
+ *      8 x 500 histogram, carry into a high word (lanes; one 1024-thread block an SM).
+ * Errors: INVALID_ARG (NULL out, n_out < 1), ALLOC, CUDA. Synchronous. */
+int mcubes_unit_rates(double *out, int n_out);
+
 /* Allocation fault hook (for testing the error paths). After mcubes_fail_alloc(n) with n >= 1,
  * the n-th device or pinned-host allocation the library makes from then on (any thread) fails as
  * if out of memory: the call that needed it returns MCUBES_ERR_ALLOC, having released what it

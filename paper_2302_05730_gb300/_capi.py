@@ -135,6 +135,7 @@ def _load():
         "mcubes_last_cuda_error": (i32, []),
         "mcubes_shutdown": (None, []),
         "mcubes_checked_violations": (i64, [i32, ctypes.POINTER(i64)]),
+        "mcubes_unit_rates": (i32, [dp, i32]),
         "mcubes_fail_alloc": (i64, [i64]),
     }
     for name, (res, args) in sig.items():
@@ -518,6 +519,17 @@ def checked_violations(reset: bool = True):
     first = ctypes.c_int64(0)
     n = int(_lib.mcubes_checked_violations(1 if reset else 0, ctypes.byref(first)))
     return None if n < 0 else (n, int(first.value))
+
+
+UNIT_RATE_NAMES = ("ffma_lanes", "dfma_lanes", "exp2f_lanes", "philox_calls", "shared_gather8_lanes",
+                   "shared_atomic_f32_lanes", "shared_atomic_u32x8_lanes")
+
+
+def unit_rates() -> dict:
+    """Per-SM, per-clock throughput of the V-Sample building blocks on the current device."""
+    out = np.zeros(len(UNIT_RATE_NAMES))
+    _check(_lib.mcubes_unit_rates(_hptr(out), len(out)), "unit_rates")
+    return dict(zip(UNIT_RATE_NAMES, (float(v) for v in out)))
 
 
 def fail_alloc(n: int) -> int:
