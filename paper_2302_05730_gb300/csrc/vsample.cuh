@@ -339,8 +339,9 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
                             yn = __fmul_rn(__fadd_rn(cm1[i], f), R);
                             yn = fminf(yn, ycap);
                         } else {
+                            // the cap min(yn, largest double below nd) is applied below, on the rare
+                            // floor >= nd (yn < nd already lies at or below the cap)
                             yn = __dmul_rn(__dadd_rn(cm1[i], f), R);
-                            yn = fmin(yn, ycap);
                         }
                         // floor(yn) for 0 <= yn < 2^23 (2^52): add the magic number rounding down
                         T kb;
@@ -359,6 +360,11 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
                         } else {
                             kb = __dadd_rd(yn, magic);
                             int k = __double2loint(kb);
+                            if (k >= kNB) {   // yn rounded up to nd: cap it, as min(yn, ycap) would
+                                yn = ycap;
+                                kb = __dadd_rd(yn, magic);
+                                k = __double2loint(kb);
+                            }
                             if (!mc_check(P.chk, k, kNB, 1)) k = 0;
                             bw = tab[i * kNB + k];
                             kofs[i] = i * kNB + k;
