@@ -186,9 +186,10 @@ __device__ __forceinline__ unsigned long long round_to_u64(float v)
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Resident blocks per SM the FP32-eval kernels are compiled for (register budget 65536 /
-// (256 x blocks)): as many as the shared memory of an adjusting block allows, at most 4. The
-// kernel is bound by shared-memory latency and throughput, so more resident warps keep more
-// requests in flight. FP64 kernels are bound by the FP64 pipe and keep the default budget.
+// (256 x blocks)): for the frozen and batched kernels, as many 256-thread blocks as the shared
+// memory of a block with a one-copy histogram allows, at most 4 (64 registers: fewer, with
+// spills, measured slower); the fixed-point adjusting kernel runs one 1024-thread block per SM
+// (64 registers as well). FP64 kernels are bound by the FP64 pipe and keep the default budget.
 #ifndef MCUBES_MAX_MIN_BLOCKS
 #define MCUBES_MAX_MIN_BLOCKS 4
 #endif

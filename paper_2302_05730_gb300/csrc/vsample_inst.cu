@@ -66,7 +66,7 @@ int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     if (bps <= 0) {
         bps = info.occ;
         // occupancy was computed for the default block size; smaller blocks fit proportionally
-        // more, up to the shared memory (one block per SM whatever its size when replicated)
+        // more, up to the shared memory (the fixed-point histogram: one block per SM whatever its size)
         if (!kRepl && threads < kDefThreads) bps = bps * (kDefThreads / threads);
     }
     uint64_t blocks = (uint64_t)req.num_sms * (uint64_t)bps;
