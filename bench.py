@@ -1,10 +1,14 @@
 """Benchmark of the m-Cubes hot path (V-Sample + Rebin) on GB300.
 
 Workload: the six Genz families at d = 8 with 1e8 samples per iteration (g = 9, m = 9^8 sub-cubes,
-p = 2), a_i ~ U[5, 15], u_i ~ U[0.2, 0.8] (seed 0). One step = one grid-adjusting iteration of
-every family: V-Sample (bin contributions on) then Rebin, on device-resident grids that keep
-adapting across steps. The headline arm is FP32-eval (point and integrand in single precision,
-FP64 sums and Rebin). The plain FP64 arm runs the same steps and is reported beside it.
+p = 2), a_i ~ U[5, 15], u_i ~ U[0.2, 0.8] (seed 0). One step = one whole m-Cubes integration of
+every family from the uniform grid: 10 iterations, the first 5 adjusting (V-Sample with bin
+contributions, then Rebin), the rest frozen, with every iteration's sums read back to the host
+and combined. The headline arm is FP32-eval (point and integrand in single precision, FP64 sums
+and Rebin); the plain FP64 arm runs the same steps. The same line reports the end-to-end rate
+through the host call, the roofline (FP32 issue, and pipe by pipe from measured unit rates), the
+oracle on the host cores, times to a relative error of 1e-3, the batched path, the learned
+proposal and PAGANI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -12,8 +16,8 @@ Under torchrun (N > 1) every rank runs an independent replica (its own Philox jo
 has no exchange step, so there is no collective on the data path. `value` is the samples of all
 ranks over the slowest rank's time.
 
-`--impl reference` times the CPU oracle (plain C, FP64, one core) on a bounded sample of the same
-workload: the paper publishes no GPU number for it.
+`--impl reference` times the CPU oracle (plain C, FP64, threads over sub-cube ranges on every
+host core) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -557,6 +561,15 @@ def main():
             dist.destroy_process_group()
         return
 
+    # ---- each estimate against the family's closed form (the last timed step of each precision)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from closed_forms import exact as closed_form
+
+    def vs_exact(fid, r):
+        ex = closed_form(fid, pars[fid][:D], pars[fid][D:])
+        return {"exact": ex, "true_rel_err": abs(r["estimate"] / ex - 1.0),
+                "z": (r["estimate"] - ex) / max(r["error"], 1e-300)}
+
     # ---- pipe-level roofline of the same launches, from the device's measured unit rates (after the
     # timed region)
     unit = capi.unit_rates()
@@ -676,11 +689,11 @@ def main():
                                "adjusting (V-Sample with bin contributions + Rebin), the rest frozen; sums to the "
                                "host and the combination", "precision": "FP32-eval, FP64 sums/Rebin",
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-            "estimates": {W.NAMES[f]: {"estimate": res32[f]["estimate"], "error": res32[f]["error"],
-                                       "chi2_dof": res32[f]["chi2_dof"]} for f in fams},
+            "estimates": {W.NAMES[f]: dict({"estimate": res32[f]["estimate"], "error": res32[f]["error"],
+                                            "chi2_dof": res32[f]["chi2_dof"]}, **vs_exact(f, res32[f])) for f in fams},
             "fp64": {"value": value64, "unit": "samples/s", "steps": f64_steps,
-                     "estimates": {W.NAMES[f]: {"estimate": res64[f]["estimate"], "error": res64[f]["error"]}
-                                   for f in fams}},
+                     "estimates": {W.NAMES[f]: dict({"estimate": res64[f]["estimate"], "error": res64[f]["error"]},
+                                                   **vs_exact(f, res64[f])) for f in fams}},
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "call": f"mcubes_integrate_ex per family ({ITMAX} iterations, {ADJ} adjusting), host results"},
             "gpu_launches": n_launch,
