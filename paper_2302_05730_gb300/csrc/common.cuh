@@ -42,6 +42,75 @@ __host__ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c
     return Words4{c0, c1, c2, c3};
 }
 
+// Philox4x32-10 over the sampler's counters (t, q, s_j = ctr2_hi | j, job), with the work that
+// does not depend on the draw hoisted out. The result is bit-identical to philox4x32_10.
+//   Round 0 maps (t, q, s_j, job) to (a_j ^ q, b_j, hi(M0 t) ^ job ^ key1, lo(M0 t)) with
+//   a_j = hi(M1 s_j) ^ key0 and b_j = lo(M1 s_j): a_j and b_j are launch constants, and
+//   words 2 and 3 are constant over a sub-cube's draws.
+//   Round 1 then multiplies word 2 by M1: hi and lo of that product are per-sub-cube values
+//   too, and b_j ^ key0_1 (kept as bk_j) is a launch constant.
+// The round keys key0 + r W0 and key1 + r W1 are stored, so the kernels read them as operands.
+// Per draw that leaves 17 of the 20 64-bit products and no key additions.
+constexpr int kPhiloxPreWords = 8;   // draw words j per sample (FP64 path at d = 16)
+struct PhiloxPre {
+    uint32_t k0[10], k1[10];         // round keys
+    uint32_t a[kPhiloxPreWords];     // hi(M1 (ctr2_hi | j)) ^ key0
+    uint32_t bk[kPhiloxPreWords];    // lo(M1 (ctr2_hi | j)) ^ (key0 + W0)
+    uint32_t c;                      // job ^ key1
+};
+struct PhiloxCube {
+    uint32_t x3;    // lo(M0 t): word 3 after round 0
+    uint32_t h;     // hi(M1 x2), x2 = hi(M0 t) ^ job ^ key1: enters word 0 after round 1
+    uint32_t y1;    // lo(M1 x2): word 1 after round 1
+};
+
+__host__ __device__ __forceinline__ void philox_prepare(PhiloxPre &pp, uint32_t key0, uint32_t key1,
+                                                        uint32_t ctr2_hi, uint32_t job)
+{
+    for (int r = 0; r < 10; ++r) {
+        pp.k0[r] = key0 + (uint32_t)r * kPhiloxW0;
+        pp.k1[r] = key1 + (uint32_t)r * kPhiloxW1;
+    }
+    for (int j = 0; j < kPhiloxPreWords; ++j) {
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)(ctr2_hi | (uint32_t)j);
+        pp.a[j] = (uint32_t)(p1 >> 32) ^ pp.k0[0];
+        pp.bk[j] = (uint32_t)p1 ^ pp.k0[1];
+    }
+    pp.c = job ^ pp.k1[0];
+}
+
+__host__ __device__ __forceinline__ PhiloxCube philox_cube(uint32_t t, const PhiloxPre &pp)
+{
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)t;
+    const uint32_t x2 = (uint32_t)(p0 >> 32) ^ pp.c;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)x2;
+    return PhiloxCube{(uint32_t)p0, (uint32_t)(p1 >> 32), (uint32_t)p1};
+}
+
+// Philox4x32-10 of counter (t, q, ctr2_hi | j, job) from the prepared constants and t's cube state.
+__host__ __device__ __forceinline__ Words4 philox_draw(uint32_t q, int j, const PhiloxCube &cb, const PhiloxPre &pp)
+{
+    // after round 1
+    const uint32_t x0 = pp.a[j] ^ q;
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)x0;
+    uint32_t c0 = cb.h ^ pp.bk[j];
+    uint32_t c1 = cb.y1;
+    uint32_t c2 = (uint32_t)(p0 >> 32) ^ cb.x3 ^ pp.k1[1];
+    uint32_t c3 = (uint32_t)p0;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint64_t m0 = (uint64_t)kPhiloxM0 * (uint64_t)c0;
+        const uint64_t m1 = (uint64_t)kPhiloxM1 * (uint64_t)c2;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ pp.k0[r];
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ pp.k1[r];
+        c1 = (uint32_t)m1;
+        c3 = (uint32_t)m0;
+        c0 = n0;
+        c2 = n2;
+    }
+    return Words4{c0, c1, c2, c3};
+}
+
 // Bounds checks of bounds-checked builds (-DMCUBES_CHECKED=1). mc_check(chk, i, n, site) is true
 // when 0 <= i < n; otherwise it counts the failure in chk[0], records the first as
 // site << 48 | index in chk[1], and returns false so that the caller skips the access. In normal
@@ -107,6 +176,7 @@ struct VsampleParams {
     double fscale;           // FP32 path: f = fscale * (kernel's scaled integrand)
     double log_fscale;       // log(fscale), or 0
     unsigned long long *chk; // bounds-checked builds: [0] failed checks, [1] the first one (else null)
+    PhiloxPre ph;            // philox_prepare(key0, key1, ctr2_hi, job), filled at launch
     IntegrandParams ip;
 };
 

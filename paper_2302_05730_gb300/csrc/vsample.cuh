@@ -254,7 +254,7 @@ __device__ __forceinline__ float histogram_scale(const VsampleParams &P)
 // block's histogram (0: none, 1: one shared copy `hist`, 2: the fixed-point histogram `ih`).
 // kPilot: evaluate only sample q = 0 of sub-cube t and return its contribution (w sigma)^2,
 // touching nothing else.
-template <int D, int FID, bool F32, bool kGlobalHist, int HK, bool kPilot = false>
+template <int D, int FID, bool F32, bool kGlobalHist, int HK, bool kPre, bool kPilot = false>
 __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t, const uint32_t t_end,
                                               const typename Prec<F32>::T2 *tab, typename Prec<F32>::T *hist,
                                               const IntHist &ih, const float hsig, ThreadSums &acc)
@@ -310,6 +310,8 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
     for (; t < t_end; ++t) {
         if (!mc_check(P.chk, t, P.m, 3)) break;
         T S1 = T(0), S2 = T(0), w0 = T(0);   // FP64: plain sums; FP32: w0 and shifted sums
+        PhiloxCube cube{0u, 0u, 0u};
+        if constexpr (kPre) cube = philox_cube(t, P.ph);
 
         for (uint32_t q = 0; q < p; ++q) {
             Integrand64<FID, D> f64;
@@ -322,7 +324,12 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
             constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
 #pragma unroll
             for (int j = 0; j < kCalls; ++j) {
-                const Words4 r = philox4x32_10(t, q, P.ctr2_hi | (uint32_t)j, P.job, P.key0, P.key1);
+                Words4 r;
+                if constexpr (kPre) {
+                    r = philox_draw(q, j, cube, P.ph);
+                } else {
+                    r = philox4x32_10(t, q, P.ctr2_hi | (uint32_t)j, P.job, P.key0, P.key1);
+                }
                 const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
                 for (int h = 0; h < kDimsPerCall; ++h) {
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__((HK == 2 ? kReplThreads : kMaxBlockThreads), (
             // the positive ones' mean log2)
             double lg = 0.0, npos = 0.0, nall = t < t_end ? 1.0 : 0.0;
             if (t < t_end) {
-                const float hp = sample_cubes<D, FID, F32, false, HK, true>(P, t, t + 1, tab, hist, ih, hsig, acc);
+                const float hp = sample_cubes<D, FID, F32, false, HK, true, true>(P, t, t + 1, tab, hist, ih, hsig, acc);
                 if (hp > 0.0f && hp <= 3.0e38f) {
                     lg = (double)log2f(fmaxf(hp, 1.17549435e-38f));
                     npos = 1.0;
@@ -643,7 +650,7 @@ __global__ void __launch_bounds__((HK == 2 ? kReplThreads : kMaxBlockThreads), (
             ih.vmax = pilot_vmax;
         }
     }
-    sample_cubes<D, FID, F32, false, HK>(P, t, t_end, tab, hist, ih, hsig, acc);
+    sample_cubes<D, FID, F32, false, HK, true>(P, t, t_end, tab, hist, ih, hsig, acc);
     finish_block<D, F32, HK>(P, acc, hist, ih, adjust, hsig, red_scratch);
 }
 
@@ -713,7 +720,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (min_blocks_per_sm<D, F32>()
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
-        sample_cubes<D, FID, F32, kGlobalHist, 1>(P, t, t_end, tab, hist, kNoIntHist, hsig, acc);
+        sample_cubes<D, FID, F32, kGlobalHist, 1, false>(P, t, t_end, tab, hist, kNoIntHist, hsig, acc);
     }
     if (cur >= 0) finish_block<D, F32, 1>(P, acc, hist, kNoIntHist, shared_hist, hsig, red_scratch);
 }

@@ -86,6 +86,7 @@ int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     int lg = 0;
     while ((1ull << lg) < spb) ++lg;
     Q.ih_vmax_exp = 63 - lg < 44 ? 63 - lg : 44;
+    philox_prepare(Q.ph, Q.key0, Q.key1, Q.ctr2_hi, Q.job);
     kern<<<(unsigned)blocks, threads, smem, s>>>(Q);
     return (int)cudaGetLastError();
 }
