@@ -68,16 +68,23 @@ def sm_peak_ops(sm_mhz: float) -> float:
     return SMS * LANES_PER_SM * sm_mhz * 1e6
 
 
-def pipe_bounds(rates: dict, fams, d: int, kinds: dict, sm_mhz: float) -> dict:
+PHILOX_PRODUCTS_PER_CALL = 20      # two 32 x 32 -> 64-bit products a round, ten rounds
+PHILOX_PRODUCTS_PER_DRAW = 17      # the sampler's hoisted form: rounds 2-9 and one product of round 1
+PHILOX_PRODUCTS_PER_CUBE = 2       # ... plus round 0's and round 1's products of the sub-cube index
+
+
+def pipe_bounds(rates: dict, fams, d: int, kinds: dict, sm_mhz: float, p: int = 2) -> dict:
     """Pipe-level roofline of the V-Sample kernels: per launch kind, the SM clocks a sample needs on
-    each pipe at the measured unit rates (mcubes_unit_rates) -- Philox calls on the integer
-    multiply pipe, the shared-memory pipe (table gathers, plus the histogram's u32 atomics when
-    adjusting: both use it) and instruction issue of the algorithmic operations -- their maximum
-    (the bound, every pipe overlapped), and the measured clocks a sample against it."""
+    each pipe at the measured unit rates (mcubes_unit_rates) -- Philox's 64-bit integer products
+    (17 a draw plus 2 a sub-cube of p samples, at 20 a measured Philox call), the shared-memory
+    pipe (table gathers, plus the histogram's u32 atomics when adjusting: both use it) and
+    instruction issue of the algorithmic operations -- their maximum (the bound, every pipe
+    overlapped), and the measured clocks a sample against it."""
     out = {}
+    products = math.ceil(d / 4) * PHILOX_PRODUCTS_PER_DRAW + PHILOX_PRODUCTS_PER_CUBE / p
     for name, adj in (("adjusting", True), ("frozen", False)):
         ops = float(np.mean([algorithmic_ops_per_sample(f, d, adj, True) for f in fams]))
-        t = {"philox": math.ceil(d / 4) / rates["philox_calls"],
+        t = {"philox": products / (PHILOX_PRODUCTS_PER_CALL * rates["philox_calls"]),
              "shared_memory": d / rates["shared_gather8_lanes"] +
              (d / rates["shared_atomic_u32x8_lanes"] if adj else 0.0),
              "issue": ops / LANES_PER_SM}
@@ -573,7 +580,7 @@ def main():
     # ---- pipe-level roofline of the same launches, from the device's measured unit rates (after the
     # timed region)
     unit = capi.unit_rates()
-    pipes = dict(pipe_bounds(unit, fams, D, kinds, sm_mhz), unit_rates_per_sm_clock=unit,
+    pipes = dict(pipe_bounds(unit, fams, D, kinds, sm_mhz, p), unit_rates_per_sm_clock=unit,
                  basis="mcubes_unit_rates microbenchmarks on this device; bound = the slowest pipe, all overlapped")
 
     # ---- plain FP64 arm (same steps)

@@ -1,5 +1,6 @@
 """The bench's pipe-level roofline arithmetic (pipe_bounds) on made-up unit rates: each pipe's
-clocks a sample, the binding pipe, and the measured clocks a sample against the bound."""
+clocks a sample (Philox counted in 64-bit products: 17 a draw, 2 a sub-cube, 20 a call), the
+binding pipe, and the measured clocks a sample against the bound."""
 import math
 import os
 import sys
@@ -20,7 +21,11 @@ def test_pipe_bounds_arithmetic():
     kinds = {"adjusting": {"samples_per_s": sps(4.0)}, "frozen": {"samples_per_s": sps(3.0)}}
     out = bench.pipe_bounds(rates, fams, d, kinds, sm_mhz)
     adj, frz = out["adjusting"], out["frozen"]
-    assert math.isclose(adj["clk_per_sample_by_pipe"]["philox"], 1.0)           # 2 calls / 2 per clock
+    # 2 draws of 17 products and 2 products a sub-cube of 2 samples: 35 products, 40 a clock
+    assert math.isclose(adj["clk_per_sample_by_pipe"]["philox"], 35.0 / 40.0)
+    # a sub-cube's products spread over more samples
+    wide = bench.pipe_bounds(rates, fams, d, kinds, sm_mhz, p=8)
+    assert math.isclose(wide["frozen"]["clk_per_sample_by_pipe"]["philox"], 34.25 / 40.0)
     assert math.isclose(adj["clk_per_sample_by_pipe"]["shared_memory"], 3.0)    # 8/4 gathers + 8/8 atomics
     assert math.isclose(frz["clk_per_sample_by_pipe"]["shared_memory"], 2.0)    # gathers only
     ops = sum(bench.algorithmic_ops_per_sample(f, d, True, True) for f in fams) / len(fams)
