@@ -43,8 +43,8 @@ METRIC = "m-Cubes samples/s; time to 1e-3 rel err, plain vs learned/FP32 (1 GB30
 # DRAM bytes (read + write) per vsample_kernel<8, oscillatory, FP32-eval> launch at d = 8, 1e8 samples
 # per iteration, from one ncu capture of this kernel as it stands: the mean over the 5 adjusting and
 # 5 frozen launches of one integration, and each kind's own mean.
-VSAMPLE_DRAM_BYTES = 157619
-VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 188108, "frozen": 127129}
+VSAMPLE_DRAM_BYTES = 102553
+VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 137625, "frozen": 67481}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts: 152 SMs, 4 SM sub-partitions x 32 lanes issue one instruction per clock.
