@@ -111,6 +111,18 @@ __host__ __device__ __forceinline__ Words4 philox_draw(uint32_t q, int j, const 
     return Words4{c0, c1, c2, c3};
 }
 
+// The FP32 layout's uniforms of axes 4j .. 4j + 3 for sample (t, q): the four words of Philox call
+// (t, q, ctr2_hi | j, job), low 23 bits each, times 2^-23.
+__device__ __forceinline__ void uniforms_f32x4(uint32_t t, uint32_t q, uint32_t ctr2_hi, uint32_t job, uint32_t k0,
+                                               uint32_t k1, int j, float u[4])
+{
+    const Words4 r = philox4x32_10(t, q, ctr2_hi | (uint32_t)j, job, k0, k1);
+    u[0] = (float)(r.x & 0x7FFFFFu) * 1.1920928955078125e-7f;
+    u[1] = (float)(r.y & 0x7FFFFFu) * 1.1920928955078125e-7f;
+    u[2] = (float)(r.z & 0x7FFFFFu) * 1.1920928955078125e-7f;
+    u[3] = (float)(r.w & 0x7FFFFFu) * 1.1920928955078125e-7f;
+}
+
 // Bounds checks of bounds-checked builds (-DMCUBES_CHECKED=1). mc_check(chk, i, n, site) is true
 // when 0 <= i < n; otherwise it counts the failure in chk[0], records the first as
 // site << 48 | index in chk[1], and returns false so that the caller skips the access. In normal

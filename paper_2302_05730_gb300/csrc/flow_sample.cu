@@ -104,14 +104,6 @@ __device__ __forceinline__ void digits(uint32_t t, uint32_t g, int d, uint32_t *
     }
 }
 
-// FP32-layout uniform of axis i for sample (t, q): Philox call i / 4, word i % 4, low 23 bits.
-__device__ __forceinline__ float uniform32(uint32_t t, uint32_t q, uint32_t ctr2_hi, uint32_t job, uint32_t k0,
-                                           uint32_t k1, int i)
-{
-    const Words4 r = philox4x32_10(t, q, ctr2_hi | (uint32_t)(i >> 2), job, k0, k1);
-    const uint32_t w = (i & 3) == 0 ? r.x : (i & 3) == 1 ? r.y : (i & 3) == 2 ? r.z : r.w;
-    return (float)(w & 0x7FFFFFu) * 1.1920928955078125e-7f;   // 2^-23
-}
 
 struct SampleSpec {
     uint32_t m, p, g, key0, key1, ctr2_hi, job;
@@ -130,16 +122,22 @@ __global__ void vegas_export_kernel(const SampleSpec S, const IntegrandParams ip
         digits(t, S.g, S.d, c);
         float xs[kDMax];
         float J = 1.f;
-        for (int a = 0; a < S.d; ++a) {
-            const float u = uniform32(t, q, S.ctr2_hi, S.job, S.key0, S.key1, a);
-            float yn = ((float)c[a] + u) * R;
-            yn = fminf(yn, 499.999969f);
-            const int k = min((int)yn, kNB - 1);
-            const double b0 = grid[a * kGS + k], b1 = grid[a * kGS + k + 1];
-            const float wd = (float)(b1 - b0);
-            xs[a] = fmaf(wd, yn - (float)k, (float)b0);
-            J *= (float)kNB * wd;
-            x[i * S.d + a] = xs[a];
+        for (int j = 0; 4 * j < S.d; ++j) {   // one Philox call per four axes
+            float u[4];
+            uniforms_f32x4(t, q, S.ctr2_hi, S.job, S.key0, S.key1, j, u);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int a = 4 * j + h;
+                if (a >= S.d) break;
+                float yn = ((float)c[a] + u[h]) * R;
+                yn = fminf(yn, 499.999969f);
+                const int k = min((int)yn, kNB - 1);
+                const double b0 = grid[a * kGS + k], b1 = grid[a * kGS + k + 1];
+                const float wd = (float)(b1 - b0);
+                xs[a] = fmaf(wd, yn - (float)k, (float)b0);
+                J *= (float)kNB * wd;
+                x[i * S.d + a] = xs[a];
+            }
         }
         w[i] = eval32(S.fid, S.d, ip, xs) * J;
     }
@@ -154,9 +152,15 @@ __global__ void latent_kernel(const SampleSpec S, long long i0, long long n, flo
         const uint32_t t = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
         uint32_t c[kDMax];
         digits(t, S.g, S.d, c);
-        for (int a = 0; a < S.d; ++a) {
-            const float u = uniform32(t, q, S.ctr2_hi, S.job, S.key0, S.key1, a);
-            z[j * S.d + a] = fminf(((float)c[a] + u) * ig, 0.99999994f);
+        for (int jc = 0; 4 * jc < S.d; ++jc) {   // one Philox call per four axes
+            float u[4];
+            uniforms_f32x4(t, q, S.ctr2_hi, S.job, S.key0, S.key1, jc, u);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int a = 4 * jc + h;
+                if (a >= S.d) break;
+                z[j * S.d + a] = fminf(((float)c[a] + u[h]) * ig, 0.99999994f);
+            }
         }
     }
 }
@@ -309,9 +313,15 @@ __global__ void __launch_bounds__(kFThreads, fused_min_blocks<H, K>())
                 const uint32_t tc = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
                 uint32_t c[kDMax];
                 digits(tc, S.g, d, c);
-                for (int a = 0; a < d; ++a) {
-                    const float u = uniform32(tc, q, S.ctr2_hi, S.job, S.key0, S.key1, a);
-                    hr[a] = fminf(((float)c[a] + u) * ig, 0.99999994f);
+                for (int jc = 0; 4 * jc < d; ++jc) {   // one Philox call per four axes
+                    float u[4];
+                    uniforms_f32x4(tc, q, S.ctr2_hi, S.job, S.key0, S.key1, jc, u);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int a = 4 * jc + h;
+                        if (a >= d) break;
+                        hr[a] = fminf(((float)c[a] + u[h]) * ig, 0.99999994f);
+                    }
                 }
             } else {
                 for (int a = 0; a < d; ++a) hr[a] = 0.5f;

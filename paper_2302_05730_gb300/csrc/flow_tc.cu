@@ -293,13 +293,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const long long i = i0 + jr;
                 const uint32_t tc = (uint32_t)(i / S.p), q = (uint32_t)(i % S.p);
                 uint32_t t = tc;
-                for (int a = 0; a < d; ++a) {
-                    const uint32_t c = t % S.g;
-                    t /= S.g;
-                    const Words4 r = philox4x32_10(tc, q, S.ctr2_hi | (uint32_t)(a >> 2), S.job, S.key0, S.key1);
-                    const uint32_t w = (a & 3) == 0 ? r.x : (a & 3) == 1 ? r.y : (a & 3) == 2 ? r.z : r.w;
-                    const float u = (float)(w & 0x7FFFFFu) * 1.1920928955078125e-7f;
-                    hr[a] = fminf(((float)c + u) * ig, 0.99999994f);
+                for (int jc = 0; 4 * jc < d; ++jc) {   // one Philox call per four axes
+                    float u[4];
+                    uniforms_f32x4(tc, q, S.ctr2_hi, S.job, S.key0, S.key1, jc, u);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        if (4 * jc + h >= d) break;
+                        const uint32_t c = t % S.g;
+                        t /= S.g;
+                        hr[4 * jc + h] = fminf(((float)c + u[h]) * ig, 0.99999994f);
+                    }
                 }
             } else {
                 for (int a = 0; a < d; ++a) hr[a] = 0.5f;
