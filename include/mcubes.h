@@ -453,12 +453,14 @@ int mcubes_flow_integrate(int integrand_id, const double *params, int d, const m
 
 /* Philox4x32-10 on the device, for checking the generator. out[4j..4j+3] = Philox(ctr[4j..4j+3],
  * key = (seed mod 2^32, seed >> 32)) for j < n.
- *   impl 0: the library's own generator (the batched and flow samplers use it).
+ *   impl 0: the library's own generator (the flow samplers use it).
  *   impl 1: the CUDA toolkit's cuRAND device function curand_Philox4x32_10.
  *   impl 2: the library's hoisted form (round 0 and part of round 1 precomputed per launch and
  *           per sub-cube), as the single-job V-Sample kernels draw; counter word 2 is split into
  *           its top 29 bits (the launch constant) and its low 3 bits (the draw word j).
- * Errors: INVALID_ARG (NULL pointers, impl not 0, 1 or 2), CUDA. */
+ *   impl 3: the hoisted form with its constants in registers, as the batched V-Sample kernel
+ *           draws; the same split of counter word 2.
+ * Errors: INVALID_ARG (NULL pointers, impl not 0-3), CUDA. */
 int mcubes_philox_dev(const uint32_t *d_ctr, uint64_t n, uint64_t seed, int impl,
                       uint32_t *d_out, void *stream);
 

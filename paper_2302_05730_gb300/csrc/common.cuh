@@ -79,36 +79,68 @@ __host__ __device__ __forceinline__ void philox_prepare(PhiloxPre &pp, uint32_t 
     pp.c = job ^ pp.k1[0];
 }
 
-__host__ __device__ __forceinline__ PhiloxCube philox_cube(uint32_t t, const PhiloxPre &pp)
+
+// The cube state of sub-cube t (rounds 0 and 1's products of t), given job ^ key1.
+__host__ __device__ __forceinline__ PhiloxCube philox_cube_k(uint32_t t, uint32_t job_xor_key1)
 {
     const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)t;
-    const uint32_t x2 = (uint32_t)(p0 >> 32) ^ pp.c;
+    const uint32_t x2 = (uint32_t)(p0 >> 32) ^ job_xor_key1;
     const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)x2;
     return PhiloxCube{(uint32_t)p0, (uint32_t)(p1 >> 32), (uint32_t)p1};
 }
-
-// Philox4x32-10 of counter (t, q, ctr2_hi | j, job) from the prepared constants and t's cube state.
-__host__ __device__ __forceinline__ Words4 philox_draw(uint32_t q, int j, const PhiloxCube &cb, const PhiloxPre &pp)
+__host__ __device__ __forceinline__ PhiloxCube philox_cube(uint32_t t, const PhiloxPre &pp)
 {
-    // after round 1
-    const uint32_t x0 = pp.a[j] ^ q;
+    return philox_cube_k(t, pp.c);
+}
+
+// Rounds 1-9 of a draw: x0 = a_j ^ q (word 0 after round 0), bk_j, the cube state, and the round
+// keys k0r(r), k1r(r).
+template <class K0, class K1>
+__host__ __device__ __forceinline__ Words4 philox_rounds_1_9(uint32_t x0, uint32_t bk, const PhiloxCube &cb, K0 k0r,
+                                                             K1 k1r)
+{
     const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)x0;
-    uint32_t c0 = cb.h ^ pp.bk[j];
+    uint32_t c0 = cb.h ^ bk;
     uint32_t c1 = cb.y1;
-    uint32_t c2 = (uint32_t)(p0 >> 32) ^ cb.x3 ^ pp.k1[1];
+    uint32_t c2 = (uint32_t)(p0 >> 32) ^ cb.x3 ^ k1r(1);
     uint32_t c3 = (uint32_t)p0;
 #pragma unroll
     for (int r = 2; r < 10; ++r) {
         const uint64_t m0 = (uint64_t)kPhiloxM0 * (uint64_t)c0;
         const uint64_t m1 = (uint64_t)kPhiloxM1 * (uint64_t)c2;
-        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ pp.k0[r];
-        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ pp.k1[r];
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0r(r);
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1r(r);
         c1 = (uint32_t)m1;
         c3 = (uint32_t)m0;
         c0 = n0;
         c2 = n2;
     }
     return Words4{c0, c1, c2, c3};
+}
+
+// Philox4x32-10 of counter (t, q, ctr2_hi | j, job) from the prepared constants and t's cube state.
+__host__ __device__ __forceinline__ Words4 philox_draw(uint32_t q, int j, const PhiloxCube &cb, const PhiloxPre &pp)
+{
+    return philox_rounds_1_9(
+        pp.a[j] ^ q, pp.bk[j], cb, [&](int r) { return pp.k0[r]; }, [&](int r) { return pp.k1[r]; });
+}
+
+// The same from values a kernel keeps in registers (the batched kernel, whose per-job parameters
+// are not launch constants): a_j and bk_j from philox_draw_consts, and the key itself, the round
+// keys formed as the rounds need them.
+__host__ __device__ __forceinline__ void philox_draw_consts(uint32_t key0, uint32_t ctr2_hi, int j, uint32_t &a_j,
+                                                            uint32_t &bk_j)
+{
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)(ctr2_hi | (uint32_t)j);
+    a_j = (uint32_t)(p1 >> 32) ^ key0;
+    bk_j = (uint32_t)p1 ^ (key0 + kPhiloxW0);
+}
+__host__ __device__ __forceinline__ Words4 philox_draw_k(uint32_t q, uint32_t a_j, uint32_t bk_j, const PhiloxCube &cb,
+                                                         uint32_t key0, uint32_t key1)
+{
+    return philox_rounds_1_9(
+        a_j ^ q, bk_j, cb, [=](int r) { return key0 + (uint32_t)r * kPhiloxW0; },
+        [=](int r) { return key1 + (uint32_t)r * kPhiloxW1; });
 }
 
 // The FP32 layout's uniforms of axes 4j .. 4j + 3 for sample (t, q): the four words of Philox call

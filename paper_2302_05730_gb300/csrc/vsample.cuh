@@ -307,11 +307,27 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
         }
     }
 
+    // Philox draws: kPre reads the launch's prepared constants (P.ph); otherwise the per-call
+    // constants and job ^ key1 are formed here, once, and kept in registers
+    constexpr int kDimsPerCall = F32 ? 4 : 2;
+    constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
+    uint32_t pa[kCalls], pbk[kCalls];
+    uint32_t job_key1 = 0u;
+    if constexpr (!kPre) {
+#pragma unroll
+        for (int j = 0; j < kCalls; ++j) philox_draw_consts(P.key0, P.ctr2_hi, j, pa[j], pbk[j]);
+        job_key1 = P.job ^ P.key1;
+    }
+
     for (; t < t_end; ++t) {
         if (!mc_check(P.chk, t, P.m, 3)) break;
         T S1 = T(0), S2 = T(0), w0 = T(0);   // FP64: plain sums; FP32: w0 and shifted sums
-        PhiloxCube cube{0u, 0u, 0u};
-        if constexpr (kPre) cube = philox_cube(t, P.ph);
+        PhiloxCube cube;
+        if constexpr (kPre) {
+            cube = philox_cube(t, P.ph);
+        } else {
+            cube = philox_cube_k(t, job_key1);
+        }
 
         for (uint32_t q = 0; q < p; ++q) {
             Integrand64<FID, D> f64;
@@ -320,15 +336,13 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
             int kofs[D];        // bin index i nd + k (FP64 path, global histogram)
             uint32_t kbb[D];    // bit pattern of yn + 2^23 rounded down: 0x4B000000 + k (FP32 path)
 
-            constexpr int kDimsPerCall = F32 ? 4 : 2;
-            constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
 #pragma unroll
             for (int j = 0; j < kCalls; ++j) {
                 Words4 r;
                 if constexpr (kPre) {
                     r = philox_draw(q, j, cube, P.ph);
                 } else {
-                    r = philox4x32_10(t, q, P.ctr2_hi | (uint32_t)j, P.job, P.key0, P.key1);
+                    r = philox_draw_k(q, pa[j], pbk[j], cube, P.key0, P.key1);
                 }
                 const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll

@@ -116,15 +116,18 @@ def test_philox_matches_curand_device_function_and_oracle(capi):
         own = torch.empty_like(d_ctr)
         ref = torch.empty_like(d_ctr)
         hoisted = torch.empty_like(d_ctr)
+        hoisted_reg = torch.empty_like(d_ctr)
         capi.philox_dev(d_ctr, n, seed, 0, own)
         capi.philox_dev(d_ctr, n, seed, 1, ref)
         capi.philox_dev(d_ctr, n, seed, 2, hoisted)
+        capi.philox_dev(d_ctr, n, seed, 3, hoisted_reg)
         torch.cuda.synchronize()
         a = own.cpu().numpy().view(np.uint32)
         b = ref.cpu().numpy().view(np.uint32)
         assert np.array_equal(a, b)
-        # the hoisted form the single-job sampler draws with, bit for bit
+        # the hoisted forms the single-job and batched samplers draw with, bit for bit
         assert np.array_equal(hoisted.cpu().numpy().view(np.uint32), b)
+        assert np.array_equal(hoisted_reg.cpu().numpy().view(np.uint32), b)
         key = [seed & 0xFFFFFFFF, seed >> 32]
         for j in list(range(4)) + list(rng.integers(0, n, 40)):
             assert oracle.philox(ctr[j], key) == [int(v) for v in a[j]]
