@@ -27,6 +27,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -102,10 +103,12 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
+        """Samples `nvidia-smi` every 50 ms into `path` (default: a file in the system temp directory);
+        stop() summarises the samples for the bench line."""
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"mcubes_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -252,7 +255,7 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
         g = json.load(open(gold))
         exact = {"double_gaussian": g["double_gaussian"], "rotated_gaussian": g["rotated_gaussian_seed0"]}
 
-    def judge(name, est, err):
+    def assess(name, est, err):
         if name not in exact:
             return {}
         z = (est - exact[name]) / max(err, 1e-300)
@@ -280,16 +283,16 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
         t32 = (time.perf_counter() - t0) / 9
         c32 = capi.combine(p32["iters"], skip=5)
         k32 = int(math.ceil(float(np.mean(p32["iters"][5:, 1])) / target))
-        j32 = judge(name, c32["estimate"], c32["error"])
-        j64 = judge(name, c64["estimate"], c64["error"])
+        j32 = assess(name, c32["estimate"], c32["error"])
+        j64 = assess(name, c64["estimate"], c64["error"])
         per_seed = []
         for seed in seeds:
             r = capi.flow_integrate(fid, par, 8, layers=4, hidden=64, bins=16, loss="variance", vegas_iters=5,
                                     flow_iters=4, train_steps=train_steps, batch=1 << 14, lr=1e-3, ncall=n_it,
                                     train_samples=1 << 20, seed=seed)
             k_flow = int(math.ceil(r["flow_var_per_sample"] / (m8 * p8) / target))
-            jf = judge(name, r["flow"]["estimate"], r["flow"]["error"])
-            jg = judge(name, r["vegas"]["estimate"], r["vegas"]["error"])
+            jf = assess(name, r["flow"]["estimate"], r["flow"]["error"])
+            jg = assess(name, r["vegas"]["estimate"], r["vegas"]["error"])
             per_seed.append({
                 "seed": seed, "flow": dict(r["flow"], **jf), "grid_same_budget": dict(r["vegas"], **jg),
                 "variance_gain_per_sample": r["vegas_var_per_sample"] / r["flow_var_per_sample"],
@@ -389,6 +392,8 @@ def main():
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling runs)")
     ap.add_argument("--train-steps", type=int, default=2000, help="flow training steps in the learned leg")
     ap.add_argument("--unit-rates", action="store_true", help="only the unit-rate microbenchmarks")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="where to keep the raw nvidia-smi clock samples ({rank} is replaced); default: temp dir")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -524,7 +529,7 @@ def main():
         return total_ms, state, res
 
     # ---- headline: FP32-eval
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(local)) if args.clocks_csv else None)
     clocks.start()
     kern_ev = []
     total_ms, state32, res32 = timed(capi.FP32_EVAL, args.steps, args.warmup, kern_ev)
