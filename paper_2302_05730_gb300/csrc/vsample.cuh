@@ -161,16 +161,18 @@ __device__ __forceinline__ uint32_t atom_add_u32(uint32_t a, uint32_t v)
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v));
     return old;
 }
-__device__ __forceinline__ void red_add_u32(uint32_t a, uint32_t v)
+// The high-word update of a fixed-point bin: c = hi + the carry out of old + lo (add with
+// carry-out, add with carry-in), added to the high word at `a` when non-zero. One predicated
+// reduction, no branch.
+__device__ __forceinline__ void add_high(uint32_t a, uint32_t old, uint32_t lo, uint32_t hi)
 {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
-}
-// hi + the carry out of old + lo (two integer adds: add with carry-out, add with carry-in)
-__device__ __forceinline__ uint32_t add_carry(uint32_t old, uint32_t lo, uint32_t hi)
-{
-    uint32_t sum, c;
-    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;" : "=r"(sum), "=r"(c) : "r"(old), "r"(lo), "r"(hi));
-    return c;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .u32 s, c;\n\t"
+        "add.cc.u32 s, %1, %2;\n\t"
+        "addc.u32 c, %3, 0;\n\t"
+        "setp.ne.u32 p, c, 0;\n\t"
+        "@p red.shared.add.u32 [%0], c;\n\t}" ::"r"(a), "r"(old), "r"(lo), "r"(hi)
+        : "memory");
 }
 // round(v) for a float 2^14 <= v < 2^44, from its bits with integer operations (a 64-bit float
 // conversion would run on the FP64 pipe): v = M 2^s with the 24-bit significand M and
@@ -469,8 +471,7 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
 #pragma unroll
                         for (int i = 0; i < D; ++i) {
                             const uint32_t old = atom_add_u32(kbb[i] * (4u * kR) + (lo_adj + (uint32_t)(i * kNB * 4 * kR)), vlo);
-                            const uint32_t c = add_carry(old, vlo, vhi);
-                            if (c != 0u) red_add_u32(kbb[i] * 4u + (hi_adj + (uint32_t)(i * kNB * 4)), c);
+                            add_high(kbb[i] * 4u + (hi_adj + (uint32_t)(i * kNB * 4)), old, vlo, vhi);
                         }
                     } else if (h != 0.0f) {   // outside the range, infinite or NaN
 #pragma unroll
