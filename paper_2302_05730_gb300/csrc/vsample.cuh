@@ -1,7 +1,8 @@
 // The m-Cubes V-Sample kernel (paper Sec. 3.2, Algorithm 2), written for sm_103a.
 //
-// Work decomposition. A persistent grid (blocks = SMs x resident blocks). Thread j of the
-// whole grid owns the contiguous sub-cube range [j m / N, (j+1) m / N) (N threads). Its
+// Work decomposition. A persistent grid (blocks = SMs x resident blocks, N threads). The
+// sub-cubes [0, m) are cut into N equal contiguous ranges; thread j owns range
+// r = (j perm_mul) mod N, a permutation that scatters a warp's ranges over [0, m). A thread's
 // strata digits are decomposed once and then advanced by +1 with carry.
 //
 // Per sample (Algorithm 2's inner loop):
@@ -31,8 +32,13 @@
 // FP32 path: the same sequence in single precision, with u on 23 bits, so that the bin and
 // the point match a CPU single-precision evaluation bit for bit. Then:
 //   - the scaled integrand f/F (fast SFU math);
-//   - per sub-cube shifted sums (w - w_0), combined per sub-cube in FP64;
-//   - the histogram in single precision, holding (w sigma)^2 with sigma = F / |I_prev|.
+//   - per sub-cube mean and variance from shifted sums (w - w_0) in single precision, summed per
+//     thread with compensation and widened to FP64 once per thread;
+//   - the bin contributions (w sigma)^2 with sigma = F / |I_prev|, in the fixed-point histogram
+//     (IntHist) on adjusting iterations.
+// The single-job kernels draw Philox in the hoisted form (philox_prepare / philox_cube /
+// philox_draw: launch constants, then per-sub-cube products), the batched kernel in its
+// register form; both are bit-identical to philox4x32_10.
 #pragma once
 
 #include <type_traits>
