@@ -7,8 +7,9 @@ contributions, then Rebin), the rest frozen, with every iteration's sums read ba
 and combined. The headline arm is FP32-eval (point and integrand in single precision, FP64 sums
 and Rebin); the plain FP64 arm runs the same steps. The same line reports the end-to-end rate
 through the host call, the roofline (FP32 issue, and pipe by pipe from measured unit rates), the
-oracle on the host cores, times to a relative error of 1e-3, the batched path, the learned
-proposal and PAGANI.
+oracle on the host cores, times to a relative error of 1e-3, the same integration of the
+paper's own fixed-parameter f1..f6 (per-family launch times and errors), the batched path, the
+learned proposal and PAGANI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -386,6 +387,7 @@ def main():
                     help="only the FP32-eval device-resident leg (profiling runs)")
     ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (4096-job) leg")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's fixed-parameter f1..f6 leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
     ap.add_argument("--no-pagani", action="store_true", help="skip the PAGANI leg")
     ap.add_argument("--pagani-only", action="store_true", help="only the PAGANI leg (profiling runs)")
@@ -611,6 +613,33 @@ def main():
     h2d = n_fam * 16                       # the previous-estimate slot
     d2h = n_fam * 2 * (ITMAX + 1) * 8      # every iteration's (sum I_t, sum V_t)
 
+    # ---- the paper's own fixed-parameter f1..f6 at d = 8 (Sec. 5, Eq. 1-6) through the same integration:
+    # mean V-Sample launch times per family beside the estimates' errors against the closed forms. This
+    # is context for the paper's per-family kernel timings (Sec. 5), which state no sample count.
+    def paper_leg():
+        saved = dict(pars)
+        pars.update({fid: W.paper_params(fid, D) for fid in fams})
+        out = {}
+        try:
+            for name, prec, steps in (("fp32_eval", capi.FP32_EVAL, 3), ("fp64", capi.FP64, 2)):
+                ev = []
+                tot, _, res = timed(prec, steps, 2, ev)
+                fam = {}
+                for fid in fams:
+                    ka = [e0.elapsed_time(e1) for (f, a_, e0, e1) in ev if f == fid and a_]
+                    kf = [e0.elapsed_time(e1) for (f, a_, e0, e1) in ev if f == fid and not a_]
+                    fam[W.NAMES[fid]] = dict({"vsample_ms_adjusting": statistics.mean(ka),
+                                              "vsample_ms_frozen": statistics.mean(kf),
+                                              "estimate": res[fid]["estimate"], "error": res[fid]["error"]},
+                                             **vs_exact(fid, res[fid]))
+                out[name] = {"samples_per_s": samples * n_fam * ITMAX * steps * world / (tot * 1e-3), "families": fam}
+        finally:
+            pars.clear()
+            pars.update(saved)
+        return out
+
+    paper = None if args.no_paper else paper_leg()
+
     # ---- time to 1e-3 relative error (full mcubes_integrate runs, host buffers)
     tta = None
     if not args.no_tta and rank == 0:
@@ -722,6 +751,7 @@ def main():
                          "pipes": pipes},
             "cpu_baseline": cpu,
             "time_to_1e-3": tta,
+            "paper_f1_f6_d8": paper,
             "batch": batch,
             "learned": learned,
             "pagani": pagani,
