@@ -278,6 +278,26 @@ def test_config1_gaussian_full_run(capi):
     assert abs(g["estimate"] - exact) < 4 * g["error"]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_paper_f1_f6_d8_against_closed_forms(capi, precision):
+    """The paper's own fixed-parameter f1..f6 at d = 8 (Sec. 5, Eq. 1-6), whole runs of 10
+    iterations (5 adjusting) at 1e7 samples per iteration, seed 0, in both precisions: every
+    estimate lies within 4.5 sigma of its closed form, and sigma is below 1e-3 of the integral for
+    all but f1 (whose integral, 3.4e-5, is small against |f| ~ 1)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from closed_forms import exact
+    d = 8
+    for fid in W.GENZ6:
+        par = W.paper_params(fid, d)
+        r = capi.integrate(fid, par, d, 10 ** 7, 10, 5, 0, precision=precision)
+        ex = exact(fid, par[:d], par[d:])
+        assert abs(r["estimate"] - ex) < 4.5 * r["error"], (fid, precision, r, ex)
+        if fid != W.OSCILLATORY:
+            assert r["error"] < 1e-3 * abs(ex), (fid, precision, r, ex)
+
+
 # ------------------------------------------------------------------------------ device API
 def test_device_iteration_matches_host_call(capi):
     d, n, fid = 6, 300000, W.C0
