@@ -319,6 +319,7 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
     // constants and job ^ key1 are formed here, once, and kept in registers
     constexpr int kDimsPerCall = F32 ? 4 : 2;
     constexpr int kCalls = (D + kDimsPerCall - 1) / kDimsPerCall;
+    static_assert(kCalls <= kPhiloxPreWords, "the prepared constants cover every draw word of a sample");
     uint32_t pa[kCalls], pbk[kCalls];
     uint32_t job_key1 = 0u;
     if constexpr (!kPre) {
