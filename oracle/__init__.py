@@ -59,6 +59,8 @@ def lib():
             L.orc_vsample.argtypes = [i32, i32, dp, i64, u64, i32, u32, i32, i32, dp, i64, i64,
                                       dp, dp, dp, dp, dp, dp]
             L.orc_rebin.argtypes = [i32, dp, dp, ctypes.c_double, dp]
+            L.orc_damp.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_damp.restype = ctypes.c_double
             L.orc_uniform_grid.argtypes = [i32, dp]
             L.orc_integrate.argtypes = [i32, i32, dp, i64, i32, i32, u64, u32, i32, dp, dp, dp, dp]
             L.orc_adapted_grid.argtypes = [i32, i32, dp, i64, i32, u64, u32, i32, dp]
@@ -179,6 +181,11 @@ def rebin(B, C, alpha: float = 1.5) -> np.ndarray:
     out = np.empty_like(B)
     lib().orc_rebin(d, _dp(B), _dp(C), alpha, _dp(out))
     return out
+
+
+def damp(rho: float, alpha: float = 1.5) -> float:
+    """Rebin's damped weight of a bin holding the fraction rho of the smoothed contributions."""
+    return float(lib().orc_damp(float(rho), float(alpha)))
 
 
 def integrate(fid, d, params, n, itmax, iter_adjust, seed, job=0, mode=0, B=None):

@@ -341,6 +341,13 @@ int orc_vsample(int id, int d, const double *par, int64_t n, uint64_t seed, int 
 /*              B'_l = B_k + Delta_k (l S/nd - R_k) / r_k with R_k <= l S/nd < R_{k+1}.      */
 /*     B'_0 = 0, B'_nd = 1.                                                                 */
 /* ------------------------------------------------------------------------------------ */
+/* Step 3's damped weight of one bin with mass fraction 0 < rho <= 1 (1 at rho = 1). */
+double orc_damp(double rho, double alpha)
+{
+    if (rho == 1.0) return 1.0;
+    return pow((1.0 - rho) / (-log(rho)), alpha);
+}
+
 void orc_rebin(int d, const double *B, const double *C, double alpha, double *Bout)
 {
     const int nd = ORC_ND;
@@ -362,9 +369,7 @@ void orc_rebin(int d, const double *B, const double *C, double alpha, double *Bo
         }
         for (int k = 0; k < nd; ++k) {
             double rho = dsm[k] / D;
-            if (dsm[k] == 0.0) r[k] = 0.0;
-            else if (rho == 1.0) r[k] = 1.0;
-            else r[k] = pow((1.0 - rho) / (-log(rho)), alpha);
+            r[k] = dsm[k] == 0.0 ? 0.0 : orc_damp(rho, alpha);
         }
         Rc[0] = 0.0;
         for (int k = 0; k < nd; ++k) Rc[k + 1] = Rc[k] + r[k];

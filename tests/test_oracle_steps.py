@@ -234,6 +234,51 @@ def test_rebin_monotone_endpoints_and_concentration():
     assert Bn[0, 1] >= 249 / ND - 1e-15 and Bn[0, -2] <= 252 / ND + 1e-15
 
 
+def test_damping_asymptotic_laws_pin_alpha():
+    """The damped weight r(rho) = ((1 - rho) / ln(1/rho))^alpha against two laws the mathematics
+    fixes, with no re-typing of the formula: near rho = 1, with eps = 1 - rho, ln(1/rho) =
+    eps + eps^2/2 + ..., so r = 1 - alpha eps / 2 + O(eps^2); for rho -> 0, (1 - rho) -> 1 and
+    r ln(1/rho)^alpha -> 1. A wrong exponent (alpha = 1), ln(rho) for ln(1/rho) or a missing
+    (1 - rho) fails one of them."""
+    for eps in (1e-4, 1e-5):
+        slope = (1.0 - oracle.damp(1.0 - eps)) / eps
+        assert abs(slope - 0.75) < 2 * eps, (eps, slope)        # alpha / 2 = 0.75
+    assert oracle.damp(1.0) == 1.0
+    for rho in (1e-30, 1e-60, 1e-120):
+        law = math.log(1.0 / rho) ** -1.5
+        assert abs(oracle.damp(rho) / law - 1.0) < 1e-12, rho
+    # the (1 - rho) factor at a moderate rho: r^(1/alpha) ln(1/rho) = 1 - rho
+    for rho in (0.1, 0.5, 0.9):
+        assert abs(oracle.damp(rho) ** (1 / 1.5) * math.log(1 / rho) - (1 - rho)) < 1e-14
+
+
+def test_rebin_spacing_ratio_measures_alpha():
+    """Through the whole Rebin on one axis with a uniform grid: contributions C = 1 on bins
+    0..199, 2e-8 on 200..349 and 2e-18 on 350..499 (smoothed mass fractions about 1e-10 and
+    1e-20 inside the two small groups). Inside a group of constant damped weight r the new
+    boundaries are equally spaced by (1/nd) (S/nd) / r, so the ratio of the two groups' new
+    spacings is r_1 / r_2, and by the small-rho law r ~ ln(1/rho)^-alpha it measures
+    alpha = ln(spacing_2 / spacing_1) / ln(ln(1/rho_2) / ln(1/rho_1)), to the O(rho) size of the
+    law's correction."""
+    C = np.concatenate([np.ones(200), np.full(150, 2e-8), np.full(150, 2e-18)])[None, :]
+    B = oracle.uniform_grid(1)
+    Bn = oracle.rebin(B, C)[0]
+    D = 200.0   # the smoothed total, up to terms of order 1e-8 (set by the small groups)
+
+    def spacing(lo, hi):
+        inside = Bn[(Bn > lo + 0.02) & (Bn < hi - 0.02)]
+        assert inside.size >= 6
+        sp = np.diff(inside)
+        assert np.allclose(sp, sp.mean(), rtol=1e-9, atol=0)
+        return sp.mean()
+
+    s1, s2 = spacing(0.4, 0.7), spacing(0.7, 1.0)
+    rho1, rho2 = 2e-8 / D, 2e-18 / D
+    alpha = math.log(s2 / s1) / math.log(math.log(1 / rho2) / math.log(1 / rho1))
+    # the relative errors of rho (about 1e-8) enter through ln(1/rho) ~ 20-46: below 1e-9 in alpha
+    assert abs(alpha - 1.5) < 1e-8, alpha
+
+
 def test_rebin_empty_contributions_keep_grid():
     d = 2
     B = _random_grid(d, 9)
