@@ -85,8 +85,10 @@ def test_batch_fp32_matches_oracle(capi):
         # one combined standard deviation
         assert abs(g["estimate"] - est) <= sig + 1e-5 * cond, (k, g["estimate"], est, sig)
     # the same batch with another launch shape: the global histogram sums in FP64 where the
-    # block histogram sums in FP32, so the bin contributions differ at single-precision rounding
-    # and the refined grids by far less than a bin; the estimates agree to 1e-6
+    # block histogram sums in FP32 (in an order the atomics leave open), so the bin contributions
+    # differ at single-precision rounding and the refined grids by far less than a bin. The two
+    # runs then sample slightly different grids with the same draws: their estimates agree to a
+    # small fraction of the statistical error (1e-3 sigma) and to 1e-5 of the estimate.
     tune = capi.BatchTuning()
     for d in range(1, 17):
         tune.block_threads[d] = 128
@@ -94,7 +96,7 @@ def test_batch_fp32_matches_oracle(capi):
         tune.hist_mode[d] = 1
     again = capi.integrate_batch(jobs, itmax, adjust, precision=1, tune=tune)
     for k, (g, h) in enumerate(zip(got, again)):
-        assert abs(g["estimate"] - h["estimate"]) <= 1e-6 * max(abs(g["estimate"]), g["error"]), k
+        assert abs(g["estimate"] - h["estimate"]) <= 1e-3 * g["error"] + 1e-5 * abs(g["estimate"]), k
 
 
 def test_autotuner_shapes_and_results(capi):
