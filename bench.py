@@ -1,17 +1,29 @@
 """Benchmark of the m-Cubes hot path (V-Sample + Rebin) on GB300.
 
-Workload: the six Genz families at d = 8 with 1e8 samples per iteration (g = 9, m = 9^8 sub-cubes,
-p = 2), a_i ~ U[5, 15], u_i ~ U[0.2, 0.8] (seed 0). One step = one whole m-Cubes integration of
-every family from the uniform grid: 10 iterations, the first 5 adjusting (V-Sample with bin
-contributions, then Rebin), the rest frozen, with every iteration's sums read back to the host
-and combined. The headline arm is FP32-eval (point and integrand in single precision, FP64 sums
-and Rebin); the plain FP64 arm runs the same steps. The same line reports the end-to-end rate
-through the host call, the roofline (FP32 issue, and pipe by pipe from measured unit rates), the
-oracle on the host cores, times to a relative error of 1e-3, the same integration of the
-paper's own fixed-parameter f1..f6 (per-family launch times and errors), the batched path, the
-learned proposal and PAGANI.
+Headline workload: the six Genz families at d = 8 with 1e8 samples per iteration (g = 9, m = 9^8
+sub-cubes, p = 2), a_i ~ U[5, 15], u_i ~ U[0.2, 0.8] (seed 0), in plain FP64 (the paper's
+precision). One step = one whole m-Cubes integration of every family from the uniform grid: 10
+iterations, the first 5 adjusting (V-Sample with bin contributions, then Rebin), the rest frozen,
+with every iteration's sums read back to the host and combined.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Output: every secondary leg first, one JSON line each ({"leg": name, ...}); the last line is the
+compact headline (plain FP64 samples/s with its roofline, the end-to-end rate through the host
+call, the oracle on the host cores, the clocks, and the FP32-eval variant's own rate and roofline).
+The legs:
+  estimates   each family's FP64 and FP32-eval estimate against its closed form
+  pipes       unit-rate microbenchmarks and the FP32-eval V-Sample's pipe-level bounds
+  config2     d = 5 and 6 at 1e8 samples per iteration, both precisions: samples/s, V-Sample
+              launch times and true errors per family
+  tta         time to a relative error of 1e-3 (sigma / |I| <= 1e-3, with the true error beside it)
+              at 1e6, 1e7 and 1e8 samples per iteration, both precisions
+  paper       the paper's own fixed-parameter f1..f6 at d = 8 (context for its per-family timings)
+  config5     d = 10 product peak and C0 at 1e9 samples per iteration, 20 iterations, both
+              precisions; and the learned proposal (6 layers, width 128) at d = 10
+  batch       4096 independent Gaussian integrations in one graph launch
+  learned     the learned proposal at d = 8 (double and rotated Gaussians)
+  pagani      the paper's other workload (off unless --pagani)
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--headline-only]
 
 Under torchrun (N > 1) every rank runs an independent replica (its own Philox job id): the method
 has no exchange step, so there is no collective on the data path. `value` is the samples of all
@@ -39,20 +51,37 @@ sys.path.insert(0, ROOT)
 
 D = 8
 NCALL = 10 ** 8
+ITMAX, ADJ = 10, 5   # one m-Cubes integration: 10 iterations, the first 5 adjust the grid
+WORKLOAD = "genz6-d8-n1e8-fp64"
 # the headline metric as named for this workload: samples/s is the value; the times to a relative
-# error of 1e-3 (plain, FP32-eval, learned) are in the line's time_to_1e-3 and learned blocks
+# error of 1e-3 (plain, FP32-eval, learned) are in the tta, config5 and learned legs
 METRIC = "m-Cubes samples/s; time to 1e-3 rel err, plain vs learned/FP32 (1 GB300)"
-# DRAM bytes (read + write) per vsample_kernel<8, oscillatory, FP32-eval> launch at d = 8, 1e8 samples
-# per iteration, from one ncu capture of this kernel as it stands: the mean over the 5 adjusting and
-# 5 frozen launches of one integration, and each kind's own mean.
-VSAMPLE_DRAM_BYTES = 102553
-VSAMPLE_DRAM_BYTES_BY_KIND = {"adjusting": 137625, "frozen": 67481}
+# DRAM bytes (read + write) per vsample_kernel<8, fid, FP64> launch at d = 8, 1e8 samples per
+# iteration, from one ncu capture of the kernel as it stands (None: not captured for it).
+VSAMPLE64_DRAM_BYTES_BY_KIND = {"adjusting": None, "frozen": None}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# GB300 unit counts: 152 SMs, 4 SM sub-partitions x 32 lanes issue one instruction per clock.
+# GB300 unit counts: 152 SMs; 4 SM sub-partitions x 32 lanes issue one instruction per clock;
+# dense FP64 at 1.25 TFLOP/s nominal is 2 FP64 FMA lanes per SM per clock at the 2070 MHz maximum.
 SMS = 152
 LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2
 FALLBACK_SM_MHZ = 2070.0
+
+
+# ------------------------------------------------------------------------------ operation counts
+# FP64 operations of the definition (Algorithm 2 with the VEGAS map), per sample, for the FP64
+# V-Sample: per axis the map (c + u, times R, floor, yn - k, the point's fma, the Jacobian's
+# product) and the family's per-axis terms; per sample the family's closing function counted at the
+# FP64 operations of a table-driven evaluation to full precision (exp 9, cos 13, a reciprocal 5),
+# w = f J and the two sub-cube sums; per sub-cube the mean, the variance (fma, clamp) and the two
+# thread sums; on adjusting iterations the contribution (w F)^2 and one histogram add per axis.
+FP64_AXIS_TERMS = {0: 1, 1: 3, 2: 1, 3: 3, 4: 2, 5: 2, 6: 1, 7: 0}
+FP64_FINISH = {0: 13, 1: 5, 2: 9, 3: 9, 4: 9, 5: 9, 6: 0, 7: 0}
+
+
+def fp64_ops_per_sample(fid: int, d: int, adjust: bool, p: int = 2) -> float:
+    return d * (6 + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 3 + 5.0 / p + ((2 + d) if adjust else 0)
 
 
 def algorithmic_ops_per_sample(fid: int, d: int, adjust: bool, f32: bool) -> float:
@@ -70,17 +99,21 @@ def sm_peak_ops(sm_mhz: float) -> float:
     return SMS * LANES_PER_SM * sm_mhz * 1e6
 
 
+def fp64_peak_ops(sm_mhz: float) -> float:
+    return SMS * FP64_LANES_PER_SM * sm_mhz * 1e6
+
+
 PHILOX_PRODUCTS_PER_CALL = 20      # two 32 x 32 -> 64-bit products a round, ten rounds
 PHILOX_PRODUCTS_PER_DRAW = 17      # the sampler's hoisted form: rounds 2-9 and one product of round 1
 PHILOX_PRODUCTS_PER_CUBE = 2       # ... plus round 0's and round 1's products of the sub-cube index
 
 
 def pipe_bounds(rates: dict, fams, d: int, kinds: dict, sm_mhz: float, p: int = 2) -> dict:
-    """Pipe-level roofline of the V-Sample kernels: per launch kind, the SM clocks a sample needs on
-    each pipe at the measured unit rates (mcubes_unit_rates) -- Philox's 64-bit integer products
-    (17 a draw plus 2 a sub-cube of p samples, at 20 a measured Philox call), the shared-memory
-    pipe (table gathers, plus the histogram's u32 atomics when adjusting: both use it) and
-    instruction issue of the algorithmic operations -- their maximum (the bound, every pipe
+    """Pipe-level roofline of the FP32-eval V-Sample kernels: per launch kind, the SM clocks a
+    sample needs on each pipe at the measured unit rates (mcubes_unit_rates) -- Philox's 64-bit
+    integer products (17 a draw plus 2 a sub-cube of p samples, at 20 a measured Philox call), the
+    shared-memory pipe (table gathers, plus the histogram's u32 atomics when adjusting: both use
+    it) and instruction issue of the algorithmic operations -- their maximum (the bound, every pipe
     overlapped), and the measured clocks a sample against it."""
     out = {}
     products = math.ceil(d / 4) * PHILOX_PRODUCTS_PER_DRAW + PHILOX_PRODUCTS_PER_CUBE / p
@@ -96,6 +129,28 @@ def pipe_bounds(rates: dict, fams, d: int, kinds: dict, sm_mhz: float, p: int = 
                      "binding_pipe": max(t, key=t.get), "measured_clk_per_sample": measured,
                      "frac_of_pipe_bound": bound / measured}
     return out
+
+
+def kind_roofline(kern_ev, samples: int, d: int, ops_fn, peak: float, p: int) -> dict:
+    """Per launch kind (adjusting, frozen) and over all V-Sample launches of a timed region: the
+    launches, their mean CUDA-event duration, samples/s, and algorithmic operations per second
+    against `peak` (operations/s)."""
+    out = {}
+    tot_ops = tot_ms = 0.0
+    for adj in (True, False):
+        ev = [(fid, e0.elapsed_time(e1)) for (fid, a_, e0, e1) in kern_ev if a_ == adj]
+        if not ev:
+            continue
+        ops = sum(ops_fn(fid, d, adj, p) * samples for fid, _ in ev)
+        ms = sum(t for _, t in ev)
+        tot_ops += ops
+        tot_ms += ms
+        out["adjusting" if adj else "frozen"] = {
+            "launches": len(ev), "avg_launch_ms": ms / len(ev), "samples_per_s": samples * len(ev) / (ms * 1e-3),
+            "achieved": ops / (ms * 1e-3) / 1e12, "frac": ops / (ms * 1e-3) / peak}
+    n = len(kern_ev)
+    return {"by_kind": out, "achieved": tot_ops / (tot_ms * 1e-3) / 1e12, "frac": tot_ops / (tot_ms * 1e-3) / peak,
+            "avg_launch_ms": tot_ms / max(n, 1), "ops_per_launch": tot_ops / max(n, 1)}
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -165,6 +220,11 @@ def replica_job(rank: int) -> int:
     return rank
 
 
+def emit(leg: str, obj) -> None:
+    """One secondary leg as its own JSON line (before the headline line)."""
+    print(json.dumps({"leg": leg, **obj}), flush=True)
+
+
 # ------------------------------------------------------------------------------ oracle timing
 def host_threads() -> int:
     try:
@@ -173,10 +233,10 @@ def host_threads() -> int:
         return max(1, os.cpu_count() or 1)
 
 
-def oracle_vsample_ranges(fams, pars, grids, ncall, starts, cubes, threads, it=1):
-    """The oracle's V-Sample over [t0, t0 + cubes) of each family, split into `threads` equal
-    sub-ranges run side by side (the oracle holds no global state and ctypes releases the
-    interpreter lock during the call). Returns the samples processed."""
+def oracle_vsample_ranges(fams, pars, grids, ncall, starts, cubes, threads, it=1, mode=0):
+    """The oracle's V-Sample (adjusting, point layout of `mode`) over [t0, t0 + cubes) of each
+    family, split into `threads` equal sub-ranges run side by side (the oracle holds no global state
+    and ctypes releases the interpreter lock during the call). Returns the samples processed."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     g, m, p = oracle.stratify(D, ncall)
@@ -189,7 +249,7 @@ def oracle_vsample_ranges(fams, pars, grids, ncall, starts, cubes, threads, it=1
 
     def one(job):
         fid, a, b = job
-        oracle.vsample(fid, D, pars[fid], ncall, 0, it=it, mode=1, adjust=1, B=grids[fid], t0=a, t1=b)
+        oracle.vsample(fid, D, pars[fid], ncall, 0, it=it, mode=mode, adjust=1, B=grids[fid], t0=a, t1=b)
         return (b - a) * p
 
     if threads == 1:
@@ -200,7 +260,7 @@ def oracle_vsample_ranges(fams, pars, grids, ncall, starts, cubes, threads, it=1
 
 # ------------------------------------------------------------------------------ reference arm
 def run_reference(args, rank):
-    """The CPU oracle on a bounded sample of the workload (sub-cube ranges of each family)."""
+    """The CPU oracle (FP64) on a bounded sample of the workload (sub-cube ranges of each family)."""
     if rank != 0:
         return
     import oracle
@@ -215,7 +275,7 @@ def run_reference(args, rank):
 
     def step(k):
         starts = {fid: (k * 7919 * cubes) % (m - cubes) for fid in W.GENZ6}
-        return oracle_vsample_ranges(W.GENZ6, pars, grids, NCALL, starts, cubes, threads, it=k % 65536)
+        return oracle_vsample_ranges(W.GENZ6, pars, grids, NCALL, starts, cubes, threads, it=k % 65536, mode=0)
 
     for k in range(args.warmup):
         step(k)
@@ -229,13 +289,175 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "genz6-d8-n1e8-fp32eval", "d": D, "ncall": NCALL,
+            "config": {"workload": WORKLOAD, "d": D, "ncall": NCALL,
                        "families": [W.NAMES[f] for f in W.GENZ6], "sample_cubes_per_family_step": cubes},
             "cpu_baseline": {"value": v, "unit": "samples/s", "cores": threads, "kind": "oracle",
                              "sample": f"{cubes} sub-cubes ({cubes * p} samples) of each of the 6 families per step, "
-                                       f"FP32-eval point layout, {threads} threads over equal sub-cube ranges"},
+                                       f"FP64, {threads} threads over equal sub-cube ranges"},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ the timed step
+class Harness:
+    """Whole m-Cubes integrations of a set of families on the device, launch by launch through the
+    C ABI's device calls (mcubes_vsample_dev, mcubes_rebin_dev) on one stream, with every
+    iteration's sums read back to the host once per step and combined there (mcubes_combine)."""
+
+    def __init__(self, capi, torch, dev, stream, d, ncall, fams, pars, itmax, adj, job, dist):
+        self.capi, self.torch, self.dev, self.stream = capi, torch, dev, stream
+        self.d, self.ncall, self.fams, self.pars = d, ncall, list(fams), pars
+        self.itmax, self.adj, self.job, self.dist = itmax, adj, job, dist
+        self.g, self.m, self.p = capi.stratify(d, ncall)
+        self.samples = self.m * self.p
+        self.uni = torch.from_numpy(np.tile(np.arange(NB + 1, dtype=np.float64) / NB, (d, 1))).to(dev)
+        nf = len(self.fams)
+        self.sums = torch.zeros((nf, itmax, 2), dtype=torch.float64, device=dev)
+        self.sums_host = torch.zeros((nf, itmax, 2), dtype=torch.float64).pin_memory()
+        self.counter = 0
+        self.launches = 0
+
+    def fresh_state(self):
+        t = self.torch
+        return {fid: dict(grid=[self.uni.clone(), t.empty_like(self.uni)], cur=0,
+                          C=t.zeros(self.d * NB, dtype=t.float64, device=self.dev)) for fid in self.fams}
+
+    def step(self, state, prec, kernel_events=None):
+        """One whole integration of each family (all hot-path rows): uniform grid, itmax V-Sample
+        passes (the first adj accumulate bin contributions and rebin), the sums of every iteration to
+        the host in one copy; the host combination follows the step."""
+        capi, t = self.capi, self.torch
+        seed = self.counter
+        self.counter += 1
+        self.sums.zero_()
+        for f, fid in enumerate(self.fams):
+            s = state[fid]
+            s["grid"][0].copy_(self.uni)
+            s["cur"] = 0
+            for it in range(self.itmax):
+                adjust = it < self.adj
+                if adjust:
+                    s["C"].zero_()
+                gin, gout = s["grid"][s["cur"]], s["grid"][1 - s["cur"]]
+                if kernel_events is not None:
+                    e0 = t.cuda.Event(enable_timing=True)
+                    e1 = t.cuda.Event(enable_timing=True)
+                    e0.record(self.stream)
+                capi.vsample_dev(fid, self.pars[fid], self.d, self.ncall, seed, it, self.job, int(adjust), prec, gin,
+                                 s["C"] if adjust else None, self.sums[f, it], stream=self.stream)
+                if kernel_events is not None:
+                    e1.record(self.stream)
+                    kernel_events.append((fid, adjust, e0, e1))
+                self.launches += 1
+                if adjust and it + 1 < self.itmax:
+                    capi.rebin_dev(self.d, gin, s["C"], gout, stream=self.stream)
+                    self.launches += 1
+                    s["cur"] = 1 - s["cur"]
+        self.sums_host.copy_(self.sums, non_blocking=True)
+
+    def combine_all(self):
+        out = {}
+        m = float(self.m)
+        for f, fid in enumerate(self.fams):
+            it = self.sums_host[f].numpy().copy()
+            it[:, 0] /= m
+            it[:, 1] /= m * m
+            out[fid] = self.capi.combine(it)
+        return out
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        self.torch.cuda.synchronize(self.dev)
+
+    def timed(self, prec, steps, warmup, kern=None, flush=None):
+        """`warmup` untimed steps, then `steps` steps each bracketed by CUDA events on the stream
+        (L2 flushed before each, outside the events). Returns (total ms over ranks, state, last
+        step's combined results)."""
+        t = self.torch
+        state = self.fresh_state()
+        with t.cuda.stream(self.stream):
+            for _ in range(warmup):
+                self.step(state, prec)
+        self.barrier()
+        self.launches = 0
+        step_ms = []
+        res = None
+        for _ in range(steps):
+            if flush is not None:
+                flush.add_(1.0)   # evict L2 between timed steps (outside the timed events)
+            t.cuda.synchronize(self.dev)
+            a = t.cuda.Event(enable_timing=True)
+            b = t.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            with t.cuda.stream(self.stream):
+                self.step(state, prec, kern)
+            b.record(self.stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            res = self.combine_all()
+        self.barrier()
+        total_ms = max_over_ranks(sum(step_ms), self.dist, self.dev)
+        for fid in self.fams:   # sanity: the last step's estimates are finite
+            assert math.isfinite(res[fid]["estimate"]) and math.isfinite(res[fid]["error"]), (fid, res[fid])
+        return total_ms, state, res
+
+
+def closed_form_fn():
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from closed_forms import exact
+    return exact
+
+
+def vs_exact(exact, fid, par, d, r):
+    ex = exact(fid, par[:d], par[d:])
+    return {"exact": ex, "true_rel_err": abs(r["estimate"] / ex - 1.0),
+            "z": (r["estimate"] - ex) / max(r["error"], 1e-300)}
+
+
+# ------------------------------------------------------------------------------ time to 1e-3
+def time_to_target(capi, fid, par, d, ncall, prec, kmax, adjust, exact=None, target=1e-3):
+    """Time to a relative error of `target`, one definition for every entry: the wall time of the
+    shortest whole run (in iterations, the first min(k, adjust) adjusting) whose combined estimate
+    has sigma <= target |I|, measured by running it again through mcubes_integrate_ex; beside it the
+    true relative error |I - I_exact| / |I_exact| and z = (I - I_exact) / sigma. A run of k
+    iterations equals the first k iterations of a longer run with the same seed (the draws are
+    indexed by iteration and the grid only depends on earlier iterations), so the k is read off one
+    run of kmax iterations."""
+    r = capi.integrate(fid, par, d, ncall, kmax, min(kmax, adjust), 0, precision=prec, return_iters=True)
+    iters = r["iters"]
+    k_hit = None
+    for k in range(1, kmax + 1):
+        c = capi.combine(iters[:k])
+        if c["error"] <= target * abs(c["estimate"]):
+            k_hit = k
+            break
+    out = {"kmax": kmax}
+    if k_hit is None:
+        c = capi.combine(iters)
+        out.update(reached=False, iters=kmax, rel_sigma=c["error"] / max(abs(c["estimate"]), 1e-300))
+        res = c
+    else:
+        t0 = time.perf_counter()
+        res = capi.integrate(fid, par, d, ncall, k_hit, min(k_hit, adjust), 0, precision=prec)
+        el = time.perf_counter() - t0
+        out.update(reached=True, iters=k_hit, seconds=el, rel_sigma=res["error"] / max(abs(res["estimate"]), 1e-300))
+    if exact is not None:
+        ex = exact(fid, par[:d], par[d:])
+        out.update(true_rel_err=abs(res["estimate"] / ex - 1.0), z=(res["estimate"] - ex) / max(res["error"], 1e-300))
+    return out
+
+
+def tta_leg(capi, W, d, pars, exact):
+    out = {}
+    budgets = {10 ** 6: 60, 10 ** 7: 30, 10 ** 8: 12}
+    for prec, name in ((capi.FP64, "fp64"), (capi.FP32_EVAL, "fp32_eval")):
+        for nb, kmax in budgets.items():
+            out[f"{name}_n{nb:.0e}"] = {W.NAMES[f]: time_to_target(capi, f, pars[f], d, nb, prec, kmax, ADJ, exact)
+                                       for f in W.GENZ6}
+    return {"d": d, "definition": "shortest whole run with sigma <= 1e-3 |I| (first min(k, 5) iterations "
+                                  "adjusting), timed through mcubes_integrate_ex; true error beside it",
+            "by_budget": out}
 
 
 # ------------------------------------------------------------------------------ learned proposal
@@ -245,11 +467,12 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
     p1 = 0.25 1, p2 = 0.75 1, and on a rotated anisotropic Gaussian (random orthogonal Q,
     eigenvalues 1..400), d = 8. Per training seed: the variance per sample against the adapted grid
     at the same budget; each method's estimate against the closed form (z-score, true relative
-    error); and the time to a relative error of 1e-3 for the learned proposal, the FP32-eval grid
-    and the plain FP64 grid: warm-up plus the iterations the measured per-iteration variance needs,
-    or null when the method's estimate disagrees with the closed form (|z| > 4), since then more
-    iterations shrink its error bar but not its error. Training differs from seed to seed, so the
-    leg reports every seed and the medians."""
+    error); and the time to a relative error of 1e-3 (sigma <= 1e-3 |I|) for the learned proposal,
+    the FP32-eval grid and the plain FP64 grid: warm-up plus the iterations the measured
+    per-iteration variance needs, with the true error beside it, or null when the method's
+    estimate disagrees with the closed form (|z| > 4), since then more iterations shrink its error
+    bar but not its error. Training differs from seed to seed, so the leg reports every seed and
+    the medians."""
     exact = {}
     gold = os.path.join(ROOT, "tests", "golden", "learned_exact_d8.json")
     if os.path.exists(gold):
@@ -270,9 +493,7 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
     for name, fid, par in cases:
         I = abs(exact.get(name, 1.0))
         target = (1e-3 * I) ** 2
-        # plain m-Cubes on the same integrand: per-iteration time and variance after adaptation (after
-        # one untimed call of each precision, which sets up the kernels' launch attributes)
-        for prec in (capi.FP64, capi.FP32_EVAL):
+        for prec in (capi.FP64, capi.FP32_EVAL):   # one untimed call of each precision (launch attributes)
             capi.integrate(fid, par, 8, n_it, 2, 1, 0, precision=prec)
         t0 = time.perf_counter()
         pl = capi.integrate(fid, par, 8, n_it, 9, 5, 0, precision=capi.FP64, return_iters=True)
@@ -318,6 +539,104 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
     return out
 
 
+# ------------------------------------------------------------------------------ config 5
+def config5_leg(capi, W, exact, flow_steps: int, with_flow: bool = True):
+    """d = 10 product peak and C0 (a_i ~ U[5, 15], u_i ~ U[0.2, 0.8], seed 0) at 1e9 samples per
+    iteration (g = 7, m = 7^10, p = 3), 20 iterations with the first 10 adjusting, FP32-eval and
+    FP64: samples/s of the whole run through mcubes_integrate_ex, the estimate against the closed
+    form, and the time to 1e-3 (sigma <= 1e-3 |I|, the tta definition). Then the learned proposal
+    at d = 10 (6 coupling layers, width 128, 16 bins) trained on 2^22-sample batches of m-Cubes'
+    own samples, on the same two integrands: variance gain per sample over the adapted grid and its
+    time to 1e-3 against plain FP64."""
+    d, n, itmax, adj = 10, 10 ** 9, 20, 10
+    g, m, p = capi.stratify(d, n)
+    out = {"d": d, "ncall": n, "m": m, "p": p, "iters": itmax, "iter_adjust": adj}
+    for fid in (W.PRODUCT_PEAK, W.C0):
+        par = W.genz_params(fid, d, seed=0)
+        fam = {}
+        for prec, name in ((capi.FP32_EVAL, "fp32_eval"), (capi.FP64, "fp64")):
+            capi.integrate(fid, par, d, n, 1, 1, 0, precision=prec)          # warm-up
+            t0 = time.perf_counter()
+            r = capi.integrate(fid, par, d, n, itmax, adj, 0, precision=prec, return_iters=True)
+            el = time.perf_counter() - t0
+            k_hit = None
+            for k in range(1, itmax + 1):
+                c = capi.combine(r["iters"][:k])
+                if c["error"] <= 1e-3 * abs(c["estimate"]):
+                    k_hit = k
+                    break
+            tt = None
+            if k_hit is not None:
+                t0 = time.perf_counter()
+                capi.integrate(fid, par, d, n, k_hit, min(k_hit, adj), 0, precision=prec)
+                tt = time.perf_counter() - t0
+            fam[name] = dict({"samples_per_s": m * p * itmax / el, "seconds": el, "estimate": r["estimate"],
+                              "error": r["error"], "iters_to_1e-3": k_hit, "time_to_1e-3_s": tt},
+                             **vs_exact(exact, fid, par, d, r))
+        if with_flow:
+            try:
+                t0 = time.perf_counter()
+                fr = capi.flow_integrate(fid, par, d, layers=6, hidden=128, bins=16, loss="variance", vegas_iters=5,
+                                         flow_iters=4, train_steps=flow_steps, batch=1 << 14, lr=1e-3,
+                                         ncall=1 << 22, train_samples=1 << 22, seed=0)
+                el = time.perf_counter() - t0
+                n_it = fr["flow"].get("samples_per_iter") or (1 << 22)
+                ex = exact(fid, par[:d], par[d:])
+                k_flow = int(math.ceil(fr["flow_var_per_sample"] / n_it / (1e-3 * ex) ** 2))
+                fam["learned_w128_l6"] = {
+                    "variance_gain_per_sample": fr["vegas_var_per_sample"] / fr["flow_var_per_sample"],
+                    "estimate": fr["flow"]["estimate"], "error": fr["flow"]["error"],
+                    "true_rel_err": abs(fr["flow"]["estimate"] / ex - 1.0),
+                    "z": (fr["flow"]["estimate"] - ex) / max(fr["flow"]["error"], 1e-300),
+                    "train_seconds": fr["seconds_train"], "seconds_total": el,
+                    "flow_samples_per_s": 4 * n_it / max(fr["seconds_flow"], 1e-9), "iters_to_1e-3": k_flow,
+                    "time_to_1e-3_s": fr["seconds_vegas"] + fr["seconds_train"] + k_flow * fr["seconds_flow"] / 4}
+            except Exception as e:   # reported, not hidden: the leg says what failed
+                fam["learned_w128_l6"] = {"error": f"{type(e).__name__}: {e}"}
+        out[W.NAMES[fid]] = fam
+    return out
+
+
+# ------------------------------------------------------------------------------ batch
+def batch_leg(capi, W):
+    """4096 independent Gaussian integrations, d ~ U{2..8}, a_i ~ U[5, 25], u_i ~ U[0.2, 0.8],
+    samples/iteration log-uniform in [1e4, 1e7], 8 iterations (4 adjust), one graph launch per
+    precision; plain FP64 one job at a time on a sample of the jobs. Jobs at 1e-3 use the tta
+    definition (sigma <= 1e-3 |I|) on the whole run."""
+    bjobs = W.batch_jobs(4096, seed=0)
+    for jb in bjobs:
+        jb["seed"] = 0
+    per_job = [int(np.prod(capi.stratify(jb["d"], jb["ncall"])[1:])) for jb in bjobs]
+    tot = sum(per_job)
+    t0 = time.perf_counter()
+    tune = capi.tune_batch(bjobs, precision=capi.FP32_EVAL)
+    tune_s = time.perf_counter() - t0
+    capi.integrate_batch(bjobs[:32], 2, 1, precision=capi.FP32_EVAL, tune=tune)
+    out = {"jobs": len(bjobs), "samples_per_iter": tot, "iters": 8, "iter_adjust": 4, "autotune_s": tune_s,
+           "autotuned": {str(k): v for k, v in tune.as_dict().items()}}
+    exact = closed_form_fn()
+    for prec, name in ((capi.FP32_EVAL, "fp32_eval"), (capi.FP64, "fp64")):
+        t0 = time.perf_counter()
+        res = capi.integrate_batch(bjobs, 8, 4, precision=prec, tune=tune, raise_on_error=False)
+        el = time.perf_counter() - t0
+        rel = np.array([r["error"] / abs(r["estimate"]) if r["estimate"] else np.inf for r in res])
+        true = np.array([abs(r["estimate"] / exact(jb["fid"], jb["params"][:jb["d"]], jb["params"][jb["d"]:]) - 1.0)
+                         for r, jb in zip(res, bjobs)])
+        out[name] = {"seconds": el, "samples_per_s": 8 * tot / el, "jobs_sigma_1e-3": int(np.sum(rel <= 1e-3)),
+                     "median_rel_sigma": float(np.median(rel)), "median_true_rel_err": float(np.median(true)),
+                     "jobs_true_1e-3": int(np.sum(true <= 1e-3))}
+    sample = list(range(0, len(bjobs), 16))
+    t0 = time.perf_counter()
+    for k in sample:
+        jb = bjobs[k]
+        capi.integrate(jb["fid"], jb["params"], jb["d"], jb["ncall"], 8, 4, 0, precision=capi.FP64)
+    el = time.perf_counter() - t0
+    frac = sum(per_job[k] for k in sample) / tot
+    out["plain_fp64_sequential"] = {"seconds_sampled": el, "jobs_sampled": len(sample),
+                                    "seconds_scaled": el / frac, "samples_per_s": 8 * tot * frac / el}
+    return out
+
+
 # ------------------------------------------------------------------------------ PAGANI
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, NVIDIA's figure (no measured FP64 peak is recorded)
 
@@ -325,14 +644,11 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, NVIDIA's figure (no measured FP
 def pagani_leg(capi, W, torch, dev, pars, mcubes64):
     """The paper's other workload (Sec. 3.1): the PAGANI region-evaluation kernel on 2^18 random
     regions of [0,1]^8 for each Genz family (regions/s, integrand evaluations/s, and the FP64 rate
-    a direct evaluation would need, 6 d + 2 FP64 operations a point -- the map to the region, the
-    family's per-axis arithmetic, the class sum, the exp -- against the nominal FP64 peak; the
-    kernel itself tabulates the separable families per axis and does less), and the
-    adaptive driver to a relative error of 1e-3 per family with up to 2^24 regions (wall time,
-    regions, status, its estimate's true relative error against the family's closed form, and its
-    distance from the m-Cubes FP64 estimate of the same run)."""
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from closed_forms import exact as closed_form
+    a direct evaluation would need, 6 d + 2 FP64 operations a point, against the nominal FP64
+    peak), and the adaptive driver to a relative error of 1e-3 per family with up to 2^24 regions
+    (wall time, regions, status, its estimate's true relative error against the family's closed
+    form, and its distance from the m-Cubes FP64 estimate of the same run)."""
+    closed_form = closed_form_fn()
     d = 8
     n = 1 << 18
     rng = np.random.default_rng(0)
@@ -378,21 +694,27 @@ def pagani_leg(capi, W, torch, dev, pars, mcubes64):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the timed FP64 and FP32-eval steps and the headline line (profiling runs)")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32"],
+                    help="with --headline-only: which timed region to run (profiling runs)")
+    ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
+    ap.add_argument("--fp32-steps", type=int, default=None, help="timed FP32-eval steps (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tta", action="store_true", help="skip the time-to-1e-3 leg")
-    ap.add_argument("--headline-only", action="store_true",
-                    help="only the FP32-eval device-resident leg (profiling runs)")
-    ap.add_argument("--ncall", type=float, default=NCALL, help="samples per iteration (profiling runs)")
+    ap.add_argument("--no-config2", action="store_true", help="skip the d = 5, 6 leg")
+    ap.add_argument("--no-config5", action="store_true", help="skip the d = 10, 1e9 leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (4096-job) leg")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's fixed-parameter f1..f6 leg")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal leg")
-    ap.add_argument("--no-pagani", action="store_true", help="skip the PAGANI leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal legs")
+    ap.add_argument("--pagani", action="store_true", help="run the PAGANI leg")
     ap.add_argument("--pagani-only", action="store_true", help="only the PAGANI leg (profiling runs)")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling runs)")
-    ap.add_argument("--train-steps", type=int, default=2000, help="flow training steps in the learned leg")
+    ap.add_argument("--config5-only", action="store_true", help="only the d = 10, 1e9 leg")
+    ap.add_argument("--train-steps", type=int, default=2000, help="flow training steps in the learned legs")
     ap.add_argument("--unit-rates", action="store_true", help="only the unit-rate microbenchmarks")
     ap.add_argument("--clocks-csv", default=None,
                     help="where to keep the raw nvidia-smi clock samples ({rank} is replaced); default: temp dir")
@@ -423,207 +745,155 @@ def main():
         return
     if args.learned_only:
         if rank == 0:
-            print(json.dumps({"learned": learned_leg(capi, W, args.train_steps)}), flush=True)
+            emit("learned", learned_leg(capi, W, args.train_steps))
         return
     if args.pagani_only:
         if rank == 0:
             pars0 = {fid: W.genz_params(fid, D, seed=0) for fid in W.GENZ6}
-            print(json.dumps({"pagani": pagani_leg(capi, W, torch, dev, pars0, {})}), flush=True)
+            emit("pagani", pagani_leg(capi, W, torch, dev, pars0, {}))
+        return
+    if args.config5_only:
+        if rank == 0:
+            emit("config5", config5_leg(capi, W, closed_form_fn(), args.train_steps, not args.no_learned))
         return
 
     stream = torch.cuda.Stream(device=dev)
     job = replica_job(rank)
     ncall = int(args.ncall)
-    g, m, p = capi.stratify(D, ncall)
-    samples = m * p
     fams = list(W.GENZ6)
     pars = {fid: W.genz_params(fid, D, seed=0) for fid in fams}
-    uni = torch.from_numpy(np.tile(np.arange(NB + 1, dtype=np.float64) / NB, (D, 1))).to(dev)
-
-    ITMAX, ADJ = 10, 5   # one m-Cubes integration: 10 iterations, the first 5 adjust the grid
+    H = Harness(capi, torch, dev, stream, D, ncall, fams, pars, ITMAX, ADJ, job, dist)
+    samples, m, p = H.samples, H.m, H.p
     n_fam = len(fams)
-    sums_all = torch.zeros((n_fam, ITMAX, 2), dtype=torch.float64, device=dev)
-    sums_host = torch.zeros((n_fam, ITMAX, 2), dtype=torch.float64).pin_memory()
-
-    def fresh_state():
-        st = {}
-        for fid in fams:
-            st[fid] = dict(grid=[uni.clone(), torch.empty_like(uni)], cur=0,
-                           C=torch.zeros(D * NB, dtype=torch.float64, device=dev))
-        return st
-
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
-    run_counter = [0]
-    launches = [0]
 
-    def step(state, prec, kernel_events=None):
-        """One whole integration of each family (all hot-path rows): uniform grid, ITMAX
-        V-Sample passes (the first ADJ accumulate bin contributions and rebin), the sums of every
-        iteration to the host in one copy; the host combination follows the step."""
-        seed = run_counter[0]
-        run_counter[0] += 1
-        sums_all.zero_()
-        for f, fid in enumerate(fams):
-            s = state[fid]
-            s["grid"][0].copy_(uni)
-            s["cur"] = 0
-            for it in range(ITMAX):
-                adjust = it < ADJ
-                if adjust:
-                    s["C"].zero_()
-                gin, gout = s["grid"][s["cur"]], s["grid"][1 - s["cur"]]
-                if kernel_events is not None:
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                capi.vsample_dev(fid, pars[fid], D, ncall, seed, it, job, int(adjust), prec, gin,
-                                 s["C"] if adjust else None, sums_all[f, it], stream=stream)
-                if kernel_events is not None:
-                    e1.record(stream)
-                    kernel_events.append((fid, adjust, e0, e1))
-                launches[0] += 1
-                if adjust and it + 1 < ITMAX:
-                    capi.rebin_dev(D, gin, s["C"], gout, stream=stream)
-                    launches[0] += 1
-                    s["cur"] = 1 - s["cur"]
-        sums_host.copy_(sums_all, non_blocking=True)
-
-    def combine_all():
-        """The combination (mcubes_combine) of every family's iterations after a step."""
-        out = {}
-        for f, fid in enumerate(fams):
-            it = sums_host[f].numpy().copy()
-            it[:, 0] /= m
-            it[:, 1] /= float(m) * float(m)
-            out[fid] = capi.combine(it)
-        return out
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def timed(prec, steps, warmup, kern=None):
-        state = fresh_state()
-        with torch.cuda.stream(stream):
-            for _ in range(warmup):
-                step(state, prec)
-        barrier()
-        launches[0] = 0
-        step_ms = []
-        res = None
-        for _ in range(steps):
-            flush.add_(1.0)   # evict L2 between timed steps (outside the timed events)
-            torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            with torch.cuda.stream(stream):
-                step(state, prec, kern)
-            b.record(stream)
-            b.synchronize()
-            step_ms.append(a.elapsed_time(b))
-            res = combine_all()
-        barrier()
-        total_ms = max_over_ranks(sum(step_ms), dist, dev)
-        for fid in fams:   # sanity: the last step's estimates are finite
-            assert math.isfinite(res[fid]["estimate"]) and math.isfinite(res[fid]["error"]), (fid, res[fid])
-        return total_ms, state, res
-
-    # ---- headline: FP32-eval
-    clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(local)) if args.clocks_csv else None)
-    clocks.start()
-    kern_ev = []
-    total_ms, state32, res32 = timed(capi.FP32_EVAL, args.steps, args.warmup, kern_ev)
-    clk = clocks.stop()
-    n_launch = launches[0]
-    ms_step = total_ms / args.steps
-    value = samples * n_fam * ITMAX * args.steps * world / (total_ms * 1e-3)
-
-    # dominant kernel: the V-Sample launches inside the timed region (adjusting and frozen)
     sm_mhz = FALLBACK_SM_MHZ
-    peak_src = "fallback (2070 MHz max SM clock)"
+    peak_src = "fallback 2070 MHz"
     if os.path.exists(PEAKS_FILE):
         try:
             sm_mhz = float(json.load(open(PEAKS_FILE)).get("sm_max_mhz", FALLBACK_SM_MHZ))
             peak_src = "MEASURED_PEAKS.json sm_max_mhz"
         except (ValueError, OSError):
             pass
-    peak = sm_peak_ops(sm_mhz) / 1e12
-    kinds = {}
-    for adj in (True, False):
-        ev = [(fid, e0.elapsed_time(e1)) for (fid, a_, e0, e1) in kern_ev if a_ == adj]
-        ops_k = sum(algorithmic_ops_per_sample(fid, D, adj, True) * samples for fid, _ in ev)
-        ms_k = sum(t for _, t in ev)
-        name = "adjusting" if adj else "frozen"
-        kinds[name] = {
-            "launches": len(ev), "avg_launch_ms": ms_k / len(ev), "samples_per_s": samples * len(ev) / (ms_k * 1e-3),
-            "achieved": ops_k / (ms_k * 1e-3) / 1e12, "frac": ops_k / (ms_k * 1e-3) / 1e12 / peak,
-            "traffic": VSAMPLE_DRAM_BYTES_BY_KIND[name] if ncall == NCALL else None}
-    all_ms = sum(e0.elapsed_time(e1) for (_, _, e0, e1) in kern_ev)
-    ops = sum(algorithmic_ops_per_sample(fid, D, a_, True) * samples for (fid, a_, _, _) in kern_ev)
-    avg_kms = all_ms / len(kern_ev)
-    achieved = ops / (all_ms * 1e-3) / 1e12
-    ops_per_launch = ops / len(kern_ev)
+
+    # ---- timed regions: plain FP64 (headline), then FP32-eval, with the clocks sampled throughout
+    clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(local)) if args.clocks_csv else None)
+    clocks.start()
+    run64 = args.precision in ("both", "fp64")
+    run32 = args.precision in ("both", "fp32")
+    kern64, kern32 = [], []
+    total64 = total32 = None
+    res64 = res32 = None
+    if run64:
+        total64, _, res64 = H.timed(capi.FP64, args.steps, args.warmup, kern64, flush)
+        n_launch = H.launches
+    steps32 = args.fp32_steps or args.steps
+    if run32:
+        total32, state32, res32 = H.timed(capi.FP32_EVAL, steps32, args.warmup, kern32, flush)
+        if not run64:
+            n_launch = H.launches
+    clk = clocks.stop()
+
+    peak64 = fp64_peak_ops(sm_mhz)
+    peak32 = sm_peak_ops(sm_mhz)
+    roof64 = kind_roofline(kern64, samples, D, fp64_ops_per_sample, peak64, p) if run64 else None
+    roof32 = kind_roofline(kern32, samples, D, lambda f, d, a, p_: algorithmic_ops_per_sample(f, d, a, True),
+                           peak32, p) if run32 else None
+    if run64:
+        for kname, v in roof64["by_kind"].items():
+            v["traffic"] = VSAMPLE64_DRAM_BYTES_BY_KIND[kname] if ncall == NCALL else None
+    value64 = samples * n_fam * ITMAX * args.steps * world / (total64 * 1e-3) if run64 else None
+    value32 = samples * n_fam * ITMAX * steps32 * world / (total32 * 1e-3) if run32 else None
+
+    def fp32_obj():
+        if not run32:
+            return None
+        return {"value": value32, "unit": "samples/s", "steps": steps32, "ms_per_step": total32 / steps32,
+                "dtype": "f32 point/integrand, f64 sums/Rebin",
+                "roofline": {"bound": "alu", "pipe": "fp32 issue", "unit": "T lane-ops/s", "peak": peak32 / 1e12,
+                             "achieved": roof32["achieved"], "frac": roof32["frac"],
+                             "by_kind": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4), "frac": round(v["frac"], 4)}
+                                         for k, v in roof32["by_kind"].items()}}}
+
+    def headline(extra):
+        v = value64 if run64 else value32
+        tot = total64 if run64 else total32
+        st = args.steps if run64 else steps32
+        line = {"metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world, "steps": st,
+                "warmup": args.warmup, "ms_per_step": tot / st, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if run64 else "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD if run64 else "genz6-d8-n1e8-fp32eval", "d": D, "ncall": ncall,
+                           "m": m, "p": p, "iters": ITMAX, "iter_adjust": ADJ, "families": n_fam,
+                           "params": "a~U[5,15],u~U[0.2,0.8],seed 0",
+                           "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                "gpu_launches": n_launch}
+        if run64:
+            line["roofline"] = {
+                "bound": "alu", "pipe": "fp64", "unit": "T fp64-ops/s", "peak": peak64 / 1e12,
+                "achieved": roof64["achieved"], "frac": roof64["frac"],
+                "traffic": None if ncall != NCALL or None in VSAMPLE64_DRAM_BYTES_BY_KIND.values() else
+                float(np.mean(list(VSAMPLE64_DRAM_BYTES_BY_KIND.values()))),
+                "kernel": "vsample_kernel<8,fid,FP64,HK>",
+                "avg_launch_ms": round(roof64["avg_launch_ms"], 4),
+                "by_kind": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4), "frac": round(v["frac"], 4),
+                                "traffic": v["traffic"]} for k, v in roof64["by_kind"].items()},
+                "peak_basis": f"152 SMs x 2 FP64 lanes x {sm_mhz:.0f} MHz ({peak_src}; 1.25 TFLOP/s nominal)"}
+        line.update(extra)
+        line["fp32_eval"] = fp32_obj()
+        line["clocks"] = clk
+        return line
 
     if args.headline_only:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "samples/s",
-                              "ms_per_step": ms_step, "ncall": ncall, "avg_launch_ms": avg_kms,
-                              "by_kind": kinds, "gpu_launches": n_launch, "clocks": clk}), flush=True)
+            print(json.dumps(headline({})), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    # ---- each estimate against the family's closed form (the last timed step of each precision)
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from closed_forms import exact as closed_form
+    exact = closed_form_fn()
+    if rank == 0:
+        emit("estimates", {
+            "fp64": {W.NAMES[f]: dict({"estimate": res64[f]["estimate"], "error": res64[f]["error"],
+                                       "chi2_dof": res64[f]["chi2_dof"]}, **vs_exact(exact, f, pars[f], D, res64[f]))
+                     for f in fams} if run64 else None,
+            "fp32_eval": {W.NAMES[f]: dict({"estimate": res32[f]["estimate"], "error": res32[f]["error"],
+                                            "chi2_dof": res32[f]["chi2_dof"]},
+                                           **vs_exact(exact, f, pars[f], D, res32[f])) for f in fams} if run32 else None,
+            "fp64_roofline_by_kind": roof64["by_kind"] if run64 else None,
+            "fp32_roofline_by_kind": roof32["by_kind"] if run32 else None})
+        if run32:
+            unit = capi.unit_rates()
+            emit("pipes", dict(pipe_bounds(unit, fams, D, roof32["by_kind"], sm_mhz, p), unit_rates_per_sm_clock=unit,
+                               basis="mcubes_unit_rates microbenchmarks on this device; bound = the slowest pipe, "
+                                     "all overlapped (FP32-eval V-Sample)"))
 
-    def vs_exact(fid, r):
-        ex = closed_form(fid, pars[fid][:D], pars[fid][D:])
-        return {"exact": ex, "true_rel_err": abs(r["estimate"] / ex - 1.0),
-                "z": (r["estimate"] - ex) / max(r["error"], 1e-300)}
-
-    # ---- pipe-level roofline of the same launches, from the device's measured unit rates (after the
-    # timed region)
-    unit = capi.unit_rates()
-    pipes = dict(pipe_bounds(unit, fams, D, kinds, sm_mhz, p), unit_rates_per_sm_clock=unit,
-                 basis="mcubes_unit_rates microbenchmarks on this device; bound = the slowest pipe, all overlapped")
-
-    # ---- plain FP64 arm (same steps)
-    f64_steps = 3
-    total64, _, res64 = timed(capi.FP64, f64_steps, 3)
-    value64 = samples * n_fam * ITMAX * f64_steps * world / (total64 * 1e-3)
-
-    # ---- end to end through the public host call (mcubes_integrate_ex: parameters in, per-iteration
+    # ---- end to end through the public host call (mcubes_integrate_ex, FP64: parameters in, per-iteration
     # results and the combined estimate out; the call uploads the previous-estimate slot and reads back
     # every iteration's sums)
+    prec_e2e = capi.FP64 if run64 else capi.FP32_EVAL
     for fid in fams:   # warm-up
-        capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 0, precision=capi.FP32_EVAL)
-    barrier()
-    e2e_steps = 3
+        capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 0, precision=prec_e2e)
+    H.barrier()
+    e2e_steps = 2
     t = time.perf_counter()
-    e2e_res = {}
     for k in range(e2e_steps):
         for fid in fams:
-            e2e_res[fid] = capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 1 + k, precision=capi.FP32_EVAL,
-                                          return_iters=True)
+            capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 1 + k, precision=prec_e2e, return_iters=True)
     e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
-    e2e_value = samples * n_fam * ITMAX * e2e_steps * world / e2e_s
-    h2d = n_fam * 16                       # the previous-estimate slot
-    d2h = n_fam * 2 * (ITMAX + 1) * 8      # every iteration's (sum I_t, sum V_t)
+    e2e = {"value": samples * n_fam * ITMAX * e2e_steps * world / e2e_s, "unit": "samples/s",
+           "h2d_bytes_per_step": n_fam * 16, "d2h_bytes_per_step": n_fam * 2 * (ITMAX + 1) * 8,
+           "call": "mcubes_integrate_ex per family, host results"}
 
-    # ---- the paper's own fixed-parameter f1..f6 at d = 8 (Sec. 5, Eq. 1-6) through the same integration:
-    # mean V-Sample launch times per family beside the estimates' errors against the closed forms. This
-    # is context for the paper's per-family kernel timings (Sec. 5), which state no sample count.
-    def paper_leg():
-        saved = dict(pars)
-        pars.update({fid: W.paper_params(fid, D) for fid in fams})
-        out = {}
-        try:
-            for name, prec, steps in (("fp32_eval", capi.FP32_EVAL, 3), ("fp64", capi.FP64, 2)):
+    # ---- secondary legs (rank 0)
+    if rank == 0 and not args.no_config2:
+        sweep = {}
+        for d in (5, 6):
+            pd = {fid: W.genz_params(fid, d, seed=0) for fid in fams}
+            Hd = Harness(capi, torch, dev, stream, d, ncall, fams, pd, ITMAX, ADJ, job, None)
+            entry = {"ncall": ncall, "m": Hd.m, "p": Hd.p}
+            for prec, name, st in ((capi.FP64, "fp64", 2), (capi.FP32_EVAL, "fp32_eval", 3)):
                 ev = []
-                tot, _, res = timed(prec, steps, 2, ev)
+                tot, _, res = Hd.timed(prec, st, 1, ev, flush)
                 fam = {}
                 for fid in fams:
                     ka = [e0.elapsed_time(e1) for (f, a_, e0, e1) in ev if f == fid and a_]
@@ -631,133 +901,71 @@ def main():
                     fam[W.NAMES[fid]] = dict({"vsample_ms_adjusting": statistics.mean(ka),
                                               "vsample_ms_frozen": statistics.mean(kf),
                                               "estimate": res[fid]["estimate"], "error": res[fid]["error"]},
-                                             **vs_exact(fid, res[fid]))
-                out[name] = {"samples_per_s": samples * n_fam * ITMAX * steps * world / (tot * 1e-3), "families": fam}
-        finally:
-            pars.clear()
-            pars.update(saved)
-        return out
+                                             **vs_exact(exact, fid, pd[fid], d, res[fid]))
+                entry[name] = {"samples_per_s": Hd.samples * n_fam * ITMAX * st / (tot * 1e-3), "families": fam}
+            sweep[f"d{d}"] = entry
+        emit("config2", sweep)
 
-    paper = None if args.no_paper else paper_leg()
+    if rank == 0 and not args.no_tta:
+        emit("tta", tta_leg(capi, W, D, pars, exact))
 
-    # ---- time to 1e-3 relative error (full mcubes_integrate runs, host buffers)
-    tta = None
-    if not args.no_tta and rank == 0:
-        tta = {}
-        for prec, name in ((capi.FP64, "fp64"), (capi.FP32_EVAL, "fp32_eval")):
-            per = {}
+    if rank == 0 and not args.no_paper:
+        pp = {fid: W.paper_params(fid, D) for fid in fams}
+        Hp = Harness(capi, torch, dev, stream, D, ncall, fams, pp, ITMAX, ADJ, job, None)
+        out = {}
+        for name, prec, steps in (("fp32_eval", capi.FP32_EVAL, 3), ("fp64", capi.FP64, 2)):
+            ev = []
+            tot, _, res = Hp.timed(prec, steps, 1, ev, flush)
+            fam = {}
             for fid in fams:
-                k_hit = None
-                for k in range(1, 11):
-                    t0 = time.perf_counter()
-                    r = capi.integrate(fid, pars[fid], D, ncall, k, min(k, 5), 0, precision=prec)
-                    el = time.perf_counter() - t0
-                    if r["error"] <= 1e-3 * abs(r["estimate"]):
-                        k_hit = (k, el)
-                        break
-                per[W.NAMES[fid]] = {"iters": k_hit[0], "seconds": k_hit[1]} if k_hit else None
-            tta[name] = per
+                ka = [e0.elapsed_time(e1) for (f, a_, e0, e1) in ev if f == fid and a_]
+                kf = [e0.elapsed_time(e1) for (f, a_, e0, e1) in ev if f == fid and not a_]
+                fam[W.NAMES[fid]] = dict({"vsample_ms_adjusting": statistics.mean(ka),
+                                          "vsample_ms_frozen": statistics.mean(kf),
+                                          "estimate": res[fid]["estimate"], "error": res[fid]["error"]},
+                                         **vs_exact(exact, fid, pp[fid], D, res[fid]))
+            out[name] = {"samples_per_s": Hp.samples * n_fam * ITMAX * steps / (tot * 1e-3), "families": fam}
+        emit("paper", out)
 
-    # ---- batched form: 4096 independent Gaussian integrations, d ~ U{2..8}, a_i ~ U[5, 25],
-    # u_i ~ U[0.2, 0.8], samples/iteration log-uniform in [1e4, 1e7], 8 iterations (4 adjust),
-    # one graph launch per precision; plain FP64 one job at a time on a sample of the jobs
-    batch = None
-    if not args.no_batch and rank == 0:
-        bjobs = W.batch_jobs(4096, seed=0)
-        for k, jb in enumerate(bjobs):
-            jb["seed"] = 0
-        per_job = [int(np.prod(capi.stratify(jb["d"], jb["ncall"])[1:])) for jb in bjobs]
-        tot = sum(per_job)
-        t0 = time.perf_counter()
-        tune = capi.tune_batch(bjobs, precision=capi.FP32_EVAL)
-        tune_s = time.perf_counter() - t0
-        capi.integrate_batch(bjobs[:32], 2, 1, precision=capi.FP32_EVAL, tune=tune)
-        batch = {"jobs": len(bjobs), "samples_per_iter": tot, "iters": 8, "iter_adjust": 4, "autotune_s": tune_s,
-                 "autotuned": {str(k): v for k, v in tune.as_dict().items()}}
-        for prec, name in ((capi.FP32_EVAL, "fp32_eval"), (capi.FP64, "fp64")):
-            t0 = time.perf_counter()
-            res = capi.integrate_batch(bjobs, 8, 4, precision=prec, tune=tune, raise_on_error=False)
-            el = time.perf_counter() - t0
-            rel = np.array([r["error"] / abs(r["estimate"]) if r["estimate"] else np.inf for r in res])
-            batch[name] = {"seconds": el, "samples_per_s": 8 * tot / el,
-                           "jobs_at_1e-3": int(np.sum(rel <= 1e-3)), "median_rel_err": float(np.median(rel))}
-        # plain FP64 m-Cubes, one job at a time, on every 16th job; scaled to the whole batch
-        sample = list(range(0, len(bjobs), 16))
-        t0 = time.perf_counter()
-        for k in sample:
-            jb = bjobs[k]
-            capi.integrate(jb["fid"], jb["params"], jb["d"], jb["ncall"], 8, 4, 0, precision=capi.FP64)
-        el = time.perf_counter() - t0
-        frac = sum(per_job[k] for k in sample) / tot
-        batch["plain_fp64_sequential"] = {"seconds_sampled": el, "jobs_sampled": len(sample),
-                                          "seconds_scaled": el / frac, "samples_per_s": 8 * tot * frac / el}
+    if rank == 0 and not args.no_config5:
+        emit("config5", config5_leg(capi, W, exact, args.train_steps, not args.no_learned))
 
-    learned = None
-    if not args.no_learned and rank == 0:
-        learned = learned_leg(capi, W, args.train_steps)
+    if rank == 0 and not args.no_batch:
+        emit("batch", batch_leg(capi, W))
 
-    pagani = None
-    if not args.no_pagani and rank == 0:
-        pagani = pagani_leg(capi, W, torch, dev, pars, res64)
+    if rank == 0 and not args.no_learned:
+        emit("learned", learned_leg(capi, W, args.train_steps))
 
-    # ---- CPU baseline: the oracle on a bounded sample of the same workload (rank 0, N = 1)
+    if rank == 0 and args.pagani:
+        emit("pagani", pagani_leg(capi, W, torch, dev, pars, res64 or {}))
+
+    # ---- CPU baseline: the oracle (FP64) on a bounded sample of the same workload (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = host_threads()
-        grids = {fid: state32[fid]["grid"][state32[fid]["cur"]].cpu().numpy() for fid in fams}   # adapted
+        grids = {fid: np.tile(np.arange(NB + 1, dtype=np.float64) / NB, (D, 1)) for fid in fams}
         starts = {fid: 0 for fid in fams}
-        c1 = min(1 << 20, m)
+        c1 = min(1 << 18, m)
         t0 = time.perf_counter()
-        n1 = oracle_vsample_ranges(fams, pars, grids, ncall, starts, c1, 1)
+        n1 = oracle_vsample_ranges(fams, pars, grids, ncall, starts, c1, 1, mode=0)
         el1 = time.perf_counter() - t0
-        cn = min((1 << 19) * threads, m)
+        cn = min((1 << 18) * threads, m)
         t0 = time.perf_counter()
-        nn = oracle_vsample_ranges(fams, pars, grids, ncall, starts, cn, threads)
+        nn = oracle_vsample_ranges(fams, pars, grids, ncall, starts, cn, threads, mode=0)
         el = time.perf_counter() - t0
         cpu = {"value": nn / el, "unit": "samples/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {cn} sub-cubes ({cn * p} samples) of each of the 6 families on the adapted "
-                         f"grids, FP32-eval point layout, {threads} threads over equal sub-cube ranges ({el:.1f} s)",
-               "single_thread": {"value": n1 / el1, "sample": f"first {c1} sub-cubes of each family ({el1:.1f} s)"}}
+               "sample": f"first {cn} sub-cubes of each of 6 families, FP64, adjusting, {threads} threads ({el:.1f} s)",
+               "single_thread": n1 / el1}
 
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "genz6-d8-n1e8-fp32eval", "d": D, "ncall": ncall, "g": g, "m": m, "p": p,
-                       "families": [W.NAMES[f] for f in fams], "params": "a_i~U[5,15], u_i~U[0.2,0.8], seed 0",
-                       "step": f"one whole m-Cubes integration of each family: {ITMAX} iterations, the first {ADJ} "
-                               "adjusting (V-Sample with bin contributions + Rebin), the rest frozen; sums to the "
-                               "host and the combination", "precision": "FP32-eval, FP64 sums/Rebin",
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
-            "estimates": {W.NAMES[f]: dict({"estimate": res32[f]["estimate"], "error": res32[f]["error"],
-                                            "chi2_dof": res32[f]["chi2_dof"]}, **vs_exact(f, res32[f])) for f in fams},
-            "fp64": {"value": value64, "unit": "samples/s", "steps": f64_steps,
-                     "estimates": {W.NAMES[f]: dict({"estimate": res64[f]["estimate"], "error": res64[f]["error"]},
-                                                   **vs_exact(f, res64[f])) for f in fams}},
-            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "call": f"mcubes_integrate_ex per family ({ITMAX} iterations, {ADJ} adjusting), host results"},
-            "gpu_launches": n_launch,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
-                         "frac": achieved / peak,
-                         "traffic": VSAMPLE_DRAM_BYTES if ncall == NCALL else None,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the 10 "
-                                           "launches of one full-size integration "
-                                           "(profiles/vsample_fp32_d8_genz6_n1e8_launches.md)",
-                         "kernel": "vsample_kernel<8, fid, FP32, HK> (adjusting launches: HK = 2, fixed-point "
-                                   "histogram, 152 x 1024; frozen launches: HK = 0, 608 x 256)",
-                         "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_kms, "by_kind": kinds,
-                         "peak_basis": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_src})",
-                         "pipes": pipes},
-            "cpu_baseline": cpu,
-            "time_to_1e-3": tta,
-            "paper_f1_f6_d8": paper,
-            "batch": batch,
-            "learned": learned,
-            "pagani": pagani,
-            "clocks": clk,
-        }
-        print(json.dumps(line), flush=True)
+        line = headline({"e2e": e2e, "cpu_baseline": cpu})
+        s = json.dumps(line)
+        if len(s) > 2048:   # keep the headline line compact: drop the descriptive strings first
+            for obj, key in ((line.get("cpu_baseline") or {}, "sample"), (line["e2e"], "call"),
+                             (line["config"], "params"), (line.get("roofline") or {}, "peak_basis")):
+                obj.pop(key, None)
+            s = json.dumps(line)
+        print(s, flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
