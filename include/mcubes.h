@@ -104,7 +104,11 @@ typedef struct mcubes_tuning {
                                  1024 for FP32 adjusting iterations, whose one block per SM holds the
                                  fixed-point histogram */
     int32_t blocks_per_sm;    /* resident blocks per SM to launch (persistent grid); default: occupancy */
-    int32_t reserved[6];
+    int32_t fp64_plain;       /* FP64 precision, single-job V-Sample: 0 (default) takes the FP64 kernel with
+                                 integer bin extraction and per-bin folded integrand tables for the six Genz
+                                 families (the same quantities to FP64 rounding, bins bit-identical);
+                                 1 forces the plain FP64 kernel, which evaluates the definition step by step */
+    int32_t reserved[5];
 } mcubes_tuning;
 
 /* Stratification (Sec. 3.2: m sub-cubes so that a 2-point MC estimate runs in each while about

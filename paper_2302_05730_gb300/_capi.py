@@ -47,7 +47,7 @@ class Result(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("fp64_plain", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class PaganiResult(ctypes.Structure):
@@ -221,6 +221,7 @@ def _tune(tune):
     t = Tuning()
     t.block_threads = int(tune.get("block_threads", 0))
     t.blocks_per_sm = int(tune.get("blocks_per_sm", 0))
+    t.fp64_plain = int(tune.get("fp64_plain", 0))
     return ctypes.byref(t)
 
 

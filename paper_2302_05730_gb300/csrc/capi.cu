@@ -295,7 +295,10 @@ int make_req(const mcubes_tuning *tune, LaunchReq &req)
     req.threads = kMaxBlockThreads;
     req.user_threads = 0;
     req.blocks_per_sm = 0;
+    req.plain64 = 0;
     if (tune) {
+        if (tune->fp64_plain != 0 && tune->fp64_plain != 1) return MCUBES_ERR_INVALID_ARG;
+        req.plain64 = tune->fp64_plain;
         if (tune->block_threads) {
             if (tune->block_threads < 64 || tune->block_threads > kMaxBlockThreads || tune->block_threads % 32)
                 return MCUBES_ERR_INVALID_ARG;

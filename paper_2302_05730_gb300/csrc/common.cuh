@@ -204,6 +204,7 @@ struct VsampleParams {
     uint32_t perm_mul;       // odd multiplier, coprime with the launch's thread count
     int ih_vmax_exp;         // fixed-point histogram: contributions below 2^ih_vmax_exp units take the
                              // integer path (set per launch so no bin's 64-bit sum can overflow)
+    int fix_shift;           // fast FP64 kernel: fraction bits of its fixed-point table sums
     uint32_t m;              // sub-cubes
     uint32_t p;              // samples per sub-cube
     uint32_t g;              // strata per axis

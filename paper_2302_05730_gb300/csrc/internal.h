@@ -37,6 +37,7 @@ struct LaunchReq {
     int user_threads;     // 1: threads was requested (else each kernel takes its default size)
     int blocks_per_sm;    // 0: as many as fit (occupancy)
     int num_sms;          // SMs of the device
+    int plain64;          // 1: the plain FP64 V-Sample kernel even where the fast one serves the family
 };
 
 }  // namespace mcubes

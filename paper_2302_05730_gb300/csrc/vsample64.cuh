@@ -1,0 +1,366 @@
+// The FP64 V-Sample kernel for the six Genz families (paper Sec. 3.2, Algorithm 2; Eq. 1-6),
+// arranged for GB300's FP64 pipe, which issues about 1/64 of the FP32 rate. Each FP64 operation
+// the definition does not need is moved off that pipe, while every step keeps FP64 accuracy and
+// the bin index stays bit-identical to the definition's:
+//   - c + u rounded to FP64 (nearest even, as an FP64 addition rounds) is built from the integers
+//     c 2^52 + bits with integer operations, and yn = (c + u) R is one FP64 product, exactly as
+//     defined (the bin depends on its rounding);
+//   - the bin k = floor(yn) and the offset in the bin come from the bits of yn with integer
+//     operations: for yn >= 1, G = 1 + (yn - k) is exact and is built by shifting the fraction
+//     bits of yn under the exponent of 1; for yn < 1 (bin 0) G is 1 + yn cut to 52 fraction bits
+//     (an error below 2^-52 of the bin's width);
+//   - the family's per-axis linear term is folded into the block's grid table: per bin
+//     P_k = a Delta_k and Q_k = (a (B_k - u) or a B_k) - P_k, so that a (x - u) (or a x) is one
+//     fma(P_k, G, Q_k) -- the same value as the definition's up to the rounding of the table
+//     entries (a few ulps of a Delta_k and a B_k); for the families that only need the sum
+//     sum_i a_i x_i (oscillatory, corner peak, discontinuous) the constant parts Q_k are held as
+//     64-bit fixed-point integers and summed exactly with integer additions, so each axis costs
+//     one FP64 fma into the sum;
+//   - the Jacobian prod_i nd Delta_k is taken as prod_i P_k, its constant factor nd^d / prod a
+//     (times prod a^2 for the product peak) folded into the launch's scale fscale;
+//   - exp and cos are table-driven (2^(j/64), cos and sin of 2 pi j / 256, filled per block), with
+//     their reduced arguments' Taylor series to 2^-54 (no library constants or steps);
+//   - the discontinuous family's cut x_i < u_i is decided exactly as defined, by one integer
+//     comparison of the offset's bits with a per-bin threshold the block finds by bisection.
+// The per-cube statistics, the reduction and the bin contributions are the FP64 kernel's own
+// (vsample.cuh): finish_block, the FP64 shared histogram.
+#pragma once
+
+#include "vsample.cuh"
+
+namespace mcubes {
+
+constexpr int kExpTab = 64;      // 2^(j / 64), j = 0..63
+constexpr int kCosTab = 256;     // cos and sin of 2 pi j / 256
+
+// ln 2 / 64 in two parts: the high part has 36 significant bits, so k * hi is exact for |k| < 2^17.
+constexpr double kLn2by64Hi = 0x1.62e42fefa0000p-7;
+constexpr double kLn2by64Lo = 0x1.cf79abc9e3b3ap-46;
+constexpr double k64byLn2 = 0x1.71547652b82fep+6;
+constexpr double kTwoPi64 = 0x1.921fb54442d18p+2;
+constexpr double kRoundMagic = 0x1.8p52;   // 1.5 2^52: adding it rounds to an integer in the low word
+
+// Families the fast FP64 kernel serves, and which per-sample closing function each takes.
+template <int FID>
+struct Fast64 {
+    static constexpr bool kOn = FID >= 0 && FID <= 5;
+    static constexpr bool kExp = FID == kGaussian || FID == kC0 || FID == kDiscontinuous;
+    static constexpr bool kCos = FID == kOscillatory;
+    static constexpr bool kCut = FID == kDiscontinuous;
+    // Q_k = a (B_k - u) - P_k for these, a B_k - P_k otherwise
+    static constexpr bool kCentred = FID == kGaussian || FID == kC0 || FID == kProductPeak;
+    // Q_k as a 64-bit fixed-point integer (2^fix_shift units), summed with integer additions
+    static constexpr bool kFixedQ = !kCentred;
+};
+
+// fl(c + u) for integers 0 <= c < 2^11 and u = bits 2^-52 (bits < 2^52), rounded to nearest even as
+// an FP64 addition rounds, from hi = c 2^20 + (bits >> 32) and lo = the low 32 bits: with N = c 2^52
+// + bits of bit length L, the significand is N shifted to 53 bits (rounded when L > 53) and the
+// exponent is L - 53.
+__device__ __forceinline__ double c_plus_u(uint32_t hi, uint32_t lo)
+{
+    const unsigned long long N = ((unsigned long long)hi << 32) | lo;
+    const int L = 64 - __clzll((long long)N);
+    unsigned long long q;
+    if (L > 53) {
+        const int s = L - 53;
+        q = (N + (1ull << (s - 1)) - 1ull + ((N >> s) & 1ull)) >> s;
+    } else {
+        q = N << (53 - L);
+    }
+    const unsigned long long bits = ((unsigned long long)(969 + L) << 52) + q;
+    return N != 0ull ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the FP64 histogram copy when
+// adjusting, the cut thresholds, and the exp or cos table.
+template <int D, int FID, int HK>
+__host__ __device__ constexpr size_t fast64_smem_bytes()
+{
+    return (size_t)D * kNB * (16 + (HK == 1 ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
+           (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
+}
+
+// exp(x): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(x) = 2^m 2^(j/64) e^r; e^r - 1 from
+// its Taylor series through r^5 (remainder below 4e-17), 2^(j/64) from the block's table, 2^m added
+// to the exponent field. 10 FP64 operations. Outside |x| < 708 (results near or beyond the
+// subnormal range, infinities, NaN) it returns the library's exp.
+__device__ __forceinline__ double exp_tab(double x, const double *T)
+{
+    if ((__double2hiint(x) & 0x7FFFFFFF) >= 0x40862000) return exp(x);   // |x| >= 708
+    const double kd = __fma_rn(x, k64byLn2, kRoundMagic);
+    const int k = __double2loint(kd);
+    const double kf = kd - kRoundMagic;
+    double r = __fma_rn(kf, -kLn2by64Hi, x);
+    r = __fma_rn(kf, -kLn2by64Lo, r);
+    double q = __fma_rn(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = __fma_rn(q, r, 1.0 / 6.0);
+    q = __fma_rn(q, r, 0.5);
+    q = __fma_rn(q, r, 1.0);
+    q = q * r;                                   // e^r - 1
+    const double tj = T[k & (kExpTab - 1)];
+    const double y = __fma_rn(tj, q, tj);        // 2^(j/64) e^r, in [0.99, 2)
+    return __hiloint2double(__double2hiint(y) + ((k >> 6) << 20), __double2loint(y));
+}
+
+// cos(2 pi t) for |t| < 2^40 turns: t = j/256 + r with |r| <= 1/512 exactly, theta = 2 pi r, and
+// cos(2 pi t) = C_j cos(theta) - S_j sin(theta); cos(theta) - 1 through theta^6 and sin(theta)
+// through theta^5 (remainders below 1e-17). 13 FP64 operations. CS holds (C_j, S_j) pairs.
+__device__ __forceinline__ double cos_turns(double t, const double2 *CS)
+{
+    const double kd = __fma_rn(t, 256.0, kRoundMagic);
+    const int k = __double2loint(kd);
+    const double kf = kd - kRoundMagic;
+    const double r = __fma_rn(kf, -1.0 / 256.0, t);   // exact
+    const double th = r * kTwoPi64;
+    const double z = th * th;
+    double c = __fma_rn(z, -1.0 / 720.0, 1.0 / 24.0);
+    c = __fma_rn(c, z, -0.5);
+    c = c * z;                                   // cos(theta) - 1
+    double s = __fma_rn(z, 1.0 / 120.0, -1.0 / 6.0);
+    s = s * z;
+    s = __fma_rn(th, s, th);                     // sin(theta)
+    const double2 cs = CS[k & (kCosTab - 1)];
+    return __fma_rn(-cs.y, s, __fma_rn(cs.x, c, cs.x));
+}
+
+// Bin and offset of 0 <= yn < 512 from its bits (integer operations only): k = floor(yn), and
+// the bits of G = 1 + (yn - k) (exact for yn >= 1; for yn < 1, 1 + yn cut to 52 fraction bits).
+__device__ __forceinline__ int split_bin(unsigned long long yb, unsigned long long &gbits)
+{
+    const int e = (int)(yb >> 52) - 1023;                          // yn >= 0
+    const unsigned long long mant = yb & 0x000FFFFFFFFFFFFFull;
+    const unsigned long long M = mant | 0x0010000000000000ull;
+    unsigned long long frac;
+    int k;
+    if (e >= 0) {
+        frac = (mant << e) & 0x000FFFFFFFFFFFFFull;
+        k = (int)(M >> (52 - e));
+    } else {
+        const int sh = -e < 63 ? -e : 63;
+        frac = M >> sh;
+        k = 0;
+    }
+    gbits = 0x3FF0000000000000ull | frac;
+    return k;
+}
+
+// Stage the fast kernel's tables: per axis and bin (P, Q) (see the header), the discontinuous
+// family's cut thresholds, and the exp or cos table; clear the histogram copy. Block-wide.
+template <int D, int FID>
+__device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *tab, double *hist, int n_hist,
+                                             unsigned long long *thr, double *ftab)
+{
+    const IntegrandParams &ip = P.ip;
+    for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
+        const int i = e / kNB;
+        const int k = e - i * kNB;
+        const double b0 = P.grid[i * (kNB + 1) + k];
+        const double b1 = P.grid[i * (kNB + 1) + k + 1];
+        const double w = b1 - b0;
+        const double a = ip.b[i];   // the fold factor (a, or a / (2 pi) for the oscillatory family)
+        const double pk = a * w;
+        const double base = Fast64<FID>::kCentred ? a * (b0 - ip.u[i]) : a * b0;
+        if constexpr (Fast64<FID>::kFixedQ) {
+            // |base - pk| <= |a|, and the launch's fix_shift keeps d |a|max 2^fix_shift below 2^62
+            const long long qf = __double2ll_rn(ldexp(base - pk, P.fix_shift));
+            tab[e] = make_double2(pk, __longlong_as_double(qf));
+        } else {
+            tab[e] = make_double2(pk, base - pk);
+        }
+        if constexpr (Fast64<FID>::kCut) {
+            // inside iff fma(w, delta, b0) < u; the decision is monotone in the offset, so it is a
+            // threshold on the offset's bit pattern: yn's bits in bin 0, G's bits in the others,
+            // where the offset is a multiple of 2^(e - 52), e the exponent of yn in bin k.
+            const double u = ip.u[i];
+            unsigned long long t;
+            if (k == 0) {
+                // smallest yn in [0, 1) with fma(w, yn, 0) >= u (2^62 bit patterns: bisection)
+                unsigned long long lo = 0ull, hi = 0x3FF0000000000000ull;   // bits(1.0): outside the bin
+                while (lo < hi) {
+                    const unsigned long long mid = lo + ((hi - lo) >> 1);
+                    if (__fma_rn(w, __longlong_as_double((long long)mid), b0) >= u) hi = mid;
+                    else lo = mid + 1;
+                }
+                t = lo;
+            } else {
+                const int ex = 31 - __clz(k);                  // exponent of yn in [k, k + 1)
+                const int sh = 52 - ex;                        // fraction bits of the offset
+                const double step = __longlong_as_double((long long)(1023 - sh) << 52);   // 2^-sh
+                unsigned long long lo = 0ull, hi = 1ull << sh;  // offset j step, j in [0, 2^sh)
+                while (lo < hi) {
+                    const unsigned long long mid = lo + ((hi - lo) >> 1);
+                    if (__fma_rn(w, (double)mid * step, b0) >= u) hi = mid;
+                    else lo = mid + 1;
+                }
+                // G = 1 + j step has fraction bits j << (52 - sh)
+                t = lo >= (1ull << sh) ? 0x4000000000000000ull : (0x3FF0000000000000ull | (lo << (52 - sh)));
+            }
+            thr[e] = t;   // inside iff bits < t
+        }
+    }
+    if constexpr (Fast64<FID>::kExp) {
+        for (int j = threadIdx.x; j < kExpTab; j += blockDim.x) ftab[j] = exp2((double)j / (double)kExpTab);
+    }
+    if constexpr (Fast64<FID>::kCos) {
+        double2 *cs = reinterpret_cast<double2 *>(ftab);
+        for (int j = threadIdx.x; j < kCosTab; j += blockDim.x) {
+            double s, c;
+            sincospi((double)j / (double)(kCosTab / 2), &s, &c);
+            cs[j] = make_double2(c, s);
+        }
+    }
+    for (int e = threadIdx.x; e < n_hist; e += blockDim.x) hist[e] = 0.0;
+    __syncthreads();
+}
+
+// Algorithm 2's loop over sub-cubes [t, t_end) for the fast FP64 kernel.
+template <int D, int FID, int HK>
+__device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, uint32_t t, const uint32_t t_end,
+                                                    const double2 *tab, double *hist,
+                                                    const unsigned long long *thr, const double *ftab,
+                                                    ThreadSums &acc)
+{
+    static_assert(Fast64<FID>::kOn, "the fast FP64 kernel serves the six Genz families");
+    const bool adjust = HK == 1 && P.adjust != 0;
+    // strata digits c_i, held as c_i 2^20 (the high word of c_i 2^52; g <= 2^11)
+    uint32_t dsh[D];
+    {
+        uint32_t rest = t;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            dsh[i] = (rest % P.g) << 20;
+            rest /= P.g;
+        }
+    }
+    const uint32_t gsh = P.g << 20;
+    const double inv_fix = ldexp(1.0, -P.fix_shift);
+    const double R = P.R;
+    const unsigned long long ycap_bits = (unsigned long long)__double_as_longlong(P.ycap);
+    const uint32_t p = P.p;
+    const double s0 = FID == kOscillatory ? P.ip.u[0] : 0.0;   // the phase offset u_1, in turns
+    constexpr int kCalls = (D + 1) / 2;
+
+    for (; t < t_end; ++t) {
+        if (!mc_check(P.chk, t, P.m, 3)) break;
+        double S1 = 0.0, S2 = 0.0;
+        const PhiloxCube cube = philox_cube(t, P.ph);
+        for (uint32_t q = 0; q < p; ++q) {
+            double s = s0, prod = 1.0, J = 1.0;
+            long long sq = 0;   // fixed-point sum of the Q_k (kFixedQ)
+            bool inside = true;
+            int kofs[D];
+#pragma unroll
+            for (int j = 0; j < kCalls; ++j) {
+                const Words4 r = philox_draw(q, j, cube, P.ph);
+                const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = 2 * j + h;
+                    if (i < D) {
+                        const double yn = __dmul_rn(c_plus_u(dsh[i] | (wv[2 * h] & 0xFFFFFu), wv[2 * h + 1]), R);
+                        unsigned long long yb = (unsigned long long)__double_as_longlong(yn);
+                        yb = yb < ycap_bits ? yb : ycap_bits;   // min(yn, largest double below nd)
+                        unsigned long long gb;
+                        int k = split_bin(yb, gb);
+                        if (!mc_check(P.chk, k, kNB, 1)) k = 0;
+                        kofs[i] = i * kNB + k;
+                        const double2 pq = tab[kofs[i]];
+                        const double G = __longlong_as_double((long long)gb);
+                        if constexpr (Fast64<FID>::kFixedQ) {
+                            s = __fma_rn(pq.x, G, s);
+                            sq += __double_as_longlong(pq.y);
+                        } else {
+                            const double v = __fma_rn(pq.x, G, pq.y);
+                            if constexpr (FID == kGaussian) {
+                                s = __fma_rn(v, v, s);
+                            } else if constexpr (FID == kC0) {
+                                s += fabs(v);
+                            } else {   // product peak
+                                prod *= __fma_rn(v, v, 1.0);
+                            }
+                        }
+                        if constexpr (Fast64<FID>::kCut) inside = inside && ((k == 0 ? yb : gb) < thr[kofs[i]]);
+                        J *= pq.x;
+                    }
+                }
+            }
+            if constexpr (Fast64<FID>::kFixedQ) s = __fma_rn(__ll2double_rn(sq), inv_fix, s);
+            double fv;
+            if constexpr (FID == kGaussian || FID == kC0) {
+                fv = exp_tab(-s, ftab);
+            } else if constexpr (FID == kDiscontinuous) {
+                fv = inside ? exp_tab(s, ftab) : 0.0;
+            } else if constexpr (FID == kOscillatory) {
+                fv = cos_turns(s, reinterpret_cast<const double2 *>(ftab));
+            } else if constexpr (FID == kProductPeak) {
+                fv = __drcp_rn(prod);
+            } else {   // corner peak
+                fv = inv_pow<D + 1>(1.0 + s);
+            }
+            const double w = fv * J;   // the weight without the launch's scale fscale
+            S1 += w;
+            S2 = __fma_rn(w, w, S2);
+            if (adjust) {
+                const double wf = w * P.fscale;
+                const double hv = wf * wf;
+#pragma unroll
+                for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], hv);
+            }
+        }
+        const bool probe_this = P.probe != nullptr && (t & P.probe_mask) == 0 &&
+                                mc_check(P.chk, t >> P.probe_shift, (long long)(P.m >> P.probe_shift) + 1, 4);
+        const double It = S1 * P.inv_p;
+        double Vt = __fma_rn(-It, S1, S2);
+        Vt = Vt > 0.0 ? Vt : 0.0;
+        acc.sI += It;
+        acc.sV += Vt;
+        if (probe_this) {
+            P.probe[2 * (size_t)(t >> P.probe_shift)] = It * P.fscale;
+            P.probe[2 * (size_t)(t >> P.probe_shift) + 1] = Vt * P.inv_pp1 * P.fscale * P.fscale;
+        }
+        bool carry = true;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            if (carry) {
+                dsh[i] += 1u << 20;
+                if (dsh[i] < gsh) {
+                    carry = false;
+                } else {
+                    dsh[i] = 0u;
+                }
+            }
+        }
+    }
+}
+
+// One job, persistent grid; HK = 0 frozen, HK = 1 adjusting (FP64 shared histogram).
+template <int D, int FID, int HK>
+__global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(const VsampleParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *tab = reinterpret_cast<double2 *>(smem_raw);
+    unsigned char *next = smem_raw + (size_t)D * kNB * 16;
+    double *hist = reinterpret_cast<double *>(next);
+    if constexpr (HK == 1) next += (size_t)D * kNB * 8;
+    unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
+    if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
+    double *ftab = reinterpret_cast<double *>(next);
+    __shared__ double red_scratch[64];
+
+    const bool adjust = HK == 1 && P.adjust != 0;
+    stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);
+
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t rng = (gtid * (uint64_t)P.perm_mul) % nthreads;
+    const uint32_t t = (uint32_t)((rng * P.m) / nthreads);
+    const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
+
+    ThreadSums acc;
+    sample_cubes_fast64<D, FID, HK>(P, t, t_end, tab, hist, thr, ftab, acc);
+    const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
+    finish_block<D, false, HK>(P, acc, hist, none, adjust, 1.0f, red_scratch);
+}
+
+}  // namespace mcubes

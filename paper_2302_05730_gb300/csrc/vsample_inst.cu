@@ -1,10 +1,12 @@
 // One (precision, integrand) slice of the V-Sample kernel instances, for d = 1..16. Compiled
 // once per slice with -DMCUBES_F32=0|1 -DMCUBES_FID=0..7 so the instances build in parallel.
 #include <atomic>
+#include <cmath>
 #include <numeric>
 
 #include "internal.h"
 #include "vsample.cuh"
+#include "vsample64.cuh"
 
 #ifndef MCUBES_F32
 #error "MCUBES_F32 must be defined"
@@ -34,48 +36,49 @@ namespace {
 constexpr bool kF32 = MCUBES_F32 != 0;
 constexpr int kFid = MCUBES_FID;
 
-// Per-instance launch facts, filled on first use (benign race: every writer stores the same
-// values for the same device).
+// Per-instance launch facts, filled on a device's first use of the instance (benign race: every
+// writer stores the same values for the same device). The shared-memory attribute is a per-device
+// setting, so the facts are kept per device.
+constexpr int kMaxDevices = 64;
 struct InstanceInfo {
-    std::atomic<int> ready{0};
-    int occ;   // resident blocks per SM at the instance's default block size
+    std::atomic<int> ready[kMaxDevices] = {};
+    int occ[kMaxDevices];   // resident blocks per SM at the instance's default block size
 };
 
-// One single-job launch of vsample_kernel<D, fid, precision, HK>: a persistent grid of
-// num_sms x resident blocks (or the requested blocks per SM).
-template <int D, int HK>
-int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
+// The kernel's shared-memory attribute and its residency at `threads` on the current device, set and
+// measured once per device.
+template <typename Kern>
+int instance_occupancy(InstanceInfo &info, Kern kern, int threads, size_t smem, int &occ)
 {
-    static InstanceInfo info;
-    auto kern = vsample_kernel<D, kFid, kF32, HK>;
-    constexpr bool kRepl = HK == 2;   // one 1024-thread block per SM
-    constexpr int kDefThreads = kRepl ? kReplThreads : kMaxBlockThreads;
-    constexpr size_t smem = single_smem_bytes<D, kF32, HK>();
-    cudaError_t e;
-    if (!info.ready.load(std::memory_order_acquire)) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+    if (!info.ready[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kDefThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
         if (e != cudaSuccess) return (int)e;
-        info.occ = nb > 0 ? nb : 1;
-        info.ready.store(1, std::memory_order_release);
+        info.occ[dev] = nb > 0 ? nb : 1;
+        info.ready[dev].store(1, std::memory_order_release);
     }
-    const int threads = req.user_threads ? req.threads : kDefThreads;
-    int bps = req.blocks_per_sm;
-    if (bps <= 0) {
-        bps = info.occ;
-        // occupancy was computed for the default block size; smaller blocks fit proportionally
-        // more, up to the shared memory (the fixed-point histogram: one block per SM whatever its size)
-        if (!kRepl && threads < kDefThreads) bps = bps * (kDefThreads / threads);
-    }
+    occ = info.occ[dev];
+    return (int)cudaSuccess;
+}
+
+// Persistent-grid shape and per-launch constants shared by the single-job kernels: blocks, the range
+// permutation multiplier, the fixed-point histogram's range and the prepared Philox constants.
+inline uint64_t single_launch_shape(VsampleParams &Q, const VsampleParams &P, const LaunchReq &req, int threads,
+                                    int bps)
+{
     uint64_t blocks = (uint64_t)req.num_sms * (uint64_t)bps;
     // at least ~4 sub-cubes per thread so the per-block grid staging stays cheap
     const uint64_t want = ((uint64_t)P.m + (uint64_t)threads * 4 - 1) / ((uint64_t)threads * 4);
     if (want < blocks) blocks = want;
     if (blocks < 1) blocks = 1;
     // range permutation multiplier: near N / 32 * golden ratio, odd, coprime with N
-    VsampleParams Q = P;
+    Q = P;
     const uint64_t n = blocks * (uint64_t)threads;
     uint64_t mul = (uint64_t)((double)n * 0.6180339887498949) | 1u;
     while (std::gcd(mul, n) != 1) mul += 2;
@@ -87,8 +90,100 @@ int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     while ((1ull << lg) < spb) ++lg;
     Q.ih_vmax_exp = 63 - lg < 44 ? 63 - lg : 44;
     philox_prepare(Q.ph, Q.key0, Q.key1, Q.ctr2_hi, Q.job);
+    return blocks;
+}
+
+// One single-job launch of vsample_kernel<D, fid, precision, HK>: a persistent grid of
+// num_sms x resident blocks (or the requested blocks per SM).
+template <int D, int HK>
+int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
+{
+    static InstanceInfo info;
+    auto kern = vsample_kernel<D, kFid, kF32, HK>;
+    constexpr bool kRepl = HK == 2;   // one 1024-thread block per SM
+    constexpr int kDefThreads = kRepl ? kReplThreads : kMaxBlockThreads;
+    constexpr size_t smem = single_smem_bytes<D, kF32, HK>();
+    int occ = 1;
+    int e = instance_occupancy(info, kern, kDefThreads, smem, occ);
+    if (e != (int)cudaSuccess) return e;
+    const int threads = req.user_threads ? req.threads : kDefThreads;
+    int bps = req.blocks_per_sm;
+    if (bps <= 0) {
+        bps = occ;
+        // occupancy was computed for the default block size; smaller blocks fit proportionally
+        // more, up to the shared memory (the fixed-point histogram: one block per SM whatever its size)
+        if (!kRepl && threads < kDefThreads) bps = bps * (kDefThreads / threads);
+    }
+    VsampleParams Q;
+    const uint64_t blocks = single_launch_shape(Q, P, req, threads, bps);
     kern<<<(unsigned)blocks, threads, smem, s>>>(Q);
     return (int)cudaGetLastError();
+}
+
+// The fast FP64 kernel (vsample64.cuh) serves a Genz family when the strata fit its integer
+// c + u (g <= 2^11) and its per-axis fold factors are usable: every a_i finite and non-zero
+// (positive for C0, whose |a (x - u)| must equal a |x - u|) and the folded scale finite and
+// non-zero. The launch's copy of the parameters then carries the fold factors in ip.b, the scale
+// nd^d / prod(fold) (nd^d prod a for the product peak), and the fraction bits of the fixed-point
+// table sums: sum_i |fold_i| 2^fix_shift stays below 2^61.
+template <int FID>
+bool fast64_params(VsampleParams &Q, int d)
+{
+    if constexpr (kF32 || !Fast64<FID>::kOn) {
+        (void)Q; (void)d;
+        return false;
+    } else {
+        constexpr double kTwoPi = 6.283185307179586;
+        if (Q.g > 2048u) return false;
+        double scale = 1.0, fsum = 0.0;
+        for (int i = 0; i < d; ++i) {
+            const double a = Q.ip.a[i];
+            if (!std::isfinite(a) || a == 0.0 || (FID == kC0 && a < 0.0)) return false;
+            const double f = FID == kOscillatory ? a / kTwoPi : a;
+            if (!std::isfinite(f) || f == 0.0) return false;
+            Q.ip.b[i] = f;
+            fsum += std::fabs(f);
+            scale *= (double)kNB;
+            scale = FID == kProductPeak ? scale * f : scale / f;
+        }
+        if (!std::isfinite(scale) || scale == 0.0 || !(fsum < 1e15)) return false;
+        Q.fscale = scale;
+        int e = 0;
+        std::frexp(fsum * 1.0000001 + 1.0, &e);   // fsum + 1 < 2^e
+        Q.fix_shift = 61 - e;
+        return true;
+    }
+}
+
+template <int D, int HK>
+int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, bool &launched)
+{
+    launched = false;
+    if constexpr (kF32 || !Fast64<kFid>::kOn) {
+        (void)P; (void)req; (void)s;
+        return (int)cudaSuccess;
+    } else {
+        VsampleParams F = P;
+        if (!fast64_params<kFid>(F, D)) return (int)cudaSuccess;
+        static InstanceInfo info;
+        auto kern = vsample_fast64_kernel<D, kFid, HK>;
+        constexpr size_t smem = fast64_smem_bytes<D, kFid, HK>();
+        if (smem > (size_t)227 * 1024) return (int)cudaSuccess;
+        int occ = 1;
+        int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
+        if (e != (int)cudaSuccess) return e;
+        const int threads = req.user_threads ? req.threads : kMaxBlockThreads;
+        int bps = req.blocks_per_sm;
+        if (bps <= 0) {
+            bps = occ;
+            if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
+        }
+        VsampleParams Q;
+        const uint64_t blocks = single_launch_shape(Q, F, req, threads, bps);
+        kern<<<(unsigned)blocks, threads, smem, s>>>(Q);
+        launched = true;
+        return (int)cudaGetLastError();
+    }
 }
 
 // Frozen iterations take the histogram-free instance; adjusting ones the FP32 kernel with the
@@ -96,14 +191,19 @@ int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 template <int D>
 int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 {
+    if (!kF32 && !req.plain64) {
+        bool launched = false;
+        const int e = P.adjust == 0 ? launch_fast64<D, 0>(P, req, s, launched) : launch_fast64<D, 1>(P, req, s, launched);
+        if (launched || e != (int)cudaSuccess) return e;
+    }
     if (P.adjust == 0) return launch_hr<D, 0>(P, req, s);
     return launch_hr<D, kF32 ? 2 : 1>(P, req, s);
 }
 
 #if MCUBES_PART == 1
 struct BatchInstanceInfo {
-    std::atomic<int> ready{0};
-    int occ[2];   // resident blocks per SM at 256 threads, [shared histogram]
+    std::atomic<int> ready[kMaxDevices] = {};
+    int occ[kMaxDevices][2];   // resident blocks per SM at 256 threads, [shared histogram]
 };
 
 template <int D, bool kGlobalHist>
@@ -114,8 +214,11 @@ int launch_batch_d(const BatchJob *jobs, const BatchTile *tiles, int n_tiles, in
     auto kern = vsample_batch_kernel<D, kFid, kF32, kGlobalHist>;
     const bool shared_hist = adjust && !kGlobalHist;
     const size_t smem = vsample_smem_bytes<kF32>(D, shared_hist ? 1 : 0);
-    cudaError_t e;
-    if (!info.ready.load(std::memory_order_acquire)) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+    if (!info.ready[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)vsample_smem_bytes<kF32>(D, 1));
         if (e != cudaSuccess) return (int)e;
@@ -124,14 +227,14 @@ int launch_batch_d(const BatchJob *jobs, const BatchTile *tiles, int n_tiles, in
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kMaxBlockThreads,
                                                               vsample_smem_bytes<kF32>(D, a));
             if (e != cudaSuccess) return (int)e;
-            info.occ[a] = nb > 0 ? nb : 1;
+            info.occ[dev][a] = nb > 0 ? nb : 1;
         }
-        info.ready.store(1, std::memory_order_release);
+        info.ready[dev].store(1, std::memory_order_release);
     }
     const int threads = req.threads;
     int bps = req.blocks_per_sm;
     if (bps <= 0) {
-        bps = info.occ[shared_hist ? 1 : 0];
+        bps = info.occ[dev][shared_hist ? 1 : 0];
         if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
     }
     int blocks = req.num_sms * bps;
