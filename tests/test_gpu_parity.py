@@ -87,13 +87,23 @@ def _tols(ref, mode):
     return rel * cI, rel, floor
 
 
-def _compare(gpu, ref, mode, B=None, check_grid=True):
+def _osc_extra(fid, mode, d, par, n, seed, it, job, B):
+    """The oscillatory family's per-bin phase-rounding bound (tests/phase_bounds.py), FP64 only."""
+    if fid != W.OSCILLATORY or mode != 0:
+        return None
+    from phase_bounds import oscillatory_c_bound
+    return oscillatory_c_bound(d, par, n, seed, it, job, oracle.uniform_grid(d) if B is None else B)
+
+
+def _compare(gpu, ref, mode, B=None, check_grid=True, c_extra=None):
     tolI, rel, vfloor = _tols(ref, mode)
     assert abs(gpu["I"] - ref["I"]) <= tolI, ("I", gpu["I"], ref["I"], tolI)
     assert abs(gpu["Var"] - ref["Var"]) <= rel * ref["Var"] + vfloor, ("Var", gpu["Var"], ref["Var"])
     if "C" in gpu:
         crel, cfloor = (1e-12, 1e-14) if mode == 0 else (1e-4, 1e-6)
         tol = crel * ref["C"] + cfloor * ref["C"].mean(axis=1, keepdims=True)
+        if c_extra is not None and mode == 0:
+            tol = tol + c_extra
         err = np.abs(gpu["C"] - ref["C"])
         assert np.all(err <= tol), ("C", float(np.max(err / tol)), float(np.max(err / np.maximum(ref["C"], 1e-300))))
     if check_grid and "grid" in gpu and B is not None:
@@ -153,7 +163,7 @@ def test_vsample_parity(capi, fid, d, n, mode):
     seed, it, job = 12345 + d, 3, 0
     gpu = capi.vsample_once(fid, par, d, n, seed, iteration=it, job=job, adjust=1, precision=mode, grid_in=B)
     ref = oracle.vsample(fid, d, par, n, seed, it=it, job=job, mode=mode, adjust=1, B=B, per_cube=True)
-    _compare(gpu, ref, mode, B)
+    _compare(gpu, ref, mode, B, c_extra=_osc_extra(fid, mode, d, par, n, seed, it, job, B))
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -165,7 +175,7 @@ def test_vsample_parity_adapted_grid(capi, fid, mode):
     B = oracle.adapted_grid(fid, d, par, 20000, 3, seed=1, mode=0)
     gpu = capi.vsample_once(fid, par, d, n, 99, iteration=5, adjust=1, precision=mode, grid_in=B)
     ref = oracle.vsample(fid, d, par, n, 99, it=5, mode=mode, adjust=1, B=B, per_cube=True)
-    _compare(gpu, ref, mode, B)
+    _compare(gpu, ref, mode, B, c_extra=_osc_extra(fid, mode, d, par, n, 99, 5, 0, B))
 
 
 LAUNCH_SHAPES = [None, dict(block_threads=64), dict(block_threads=96, blocks_per_sm=3),
@@ -198,7 +208,8 @@ def test_launch_shapes_match_oracle(capi, fid, d, n, mode):
                 gpu["C"] = C.cpu().numpy().reshape(d, 500)
             else:
                 assert not C.any()
-            _compare(gpu, ref[adjust], mode)
+            _compare(gpu, ref[adjust], mode,
+                     c_extra=_osc_extra(fid, mode, d, par, n, seed, it, 0, B) if adjust else None)
 
 
 @pytest.mark.parametrize("fid,d,n,a,u", [
@@ -325,17 +336,33 @@ def test_device_iteration_matches_host_call(capi):
 F32_MIN = float(np.finfo(np.float32).tiny)
 
 
-def _weight_error_bounds(fid, d, par, x, w, J, mode):
+def _weight_error_bounds(fid, d, par, x, w, J, mode, dk=None):
     """Bound on the rounding error of each sample weight w = f J in the kernel's precision.
     The integrand's argument (the exponent, the oscillatory phase) is a sum of d rounded terms,
     so its absolute error grows with its size, and f's relative error with it; J is a product of
     d rounded bin widths. FP32-eval weights also underflow below FLT_MIN times the integrand's
     scale factor F (the peak value: 1, prod a_i^2 for the product peak, e^{sum a min(u, 1)} for
-    the discontinuous family)."""
+    the discontinuous family).
+    FP64 Genz families (dk: the samples' bin widths, n x d): the kernel forms a (x - u) (or a x)
+    as one fma of per-bin table entries a Delta_k and a (B_k - u) - a Delta_k, each rounded once,
+    so each term carries up to 2 eps a (2 |x - u| + 3 Delta_k) (x for |x - u| in the uncentred
+    families) of absolute error, which the argument's error adds up as below."""
     eps = 2.0 ** -24 if mode == 1 else 2.0 ** -53
     a, u = par[:d], par[d:]
     aw = np.abs(w)
     base = eps * (8 + 2 * d)
+    fold = None
+    if mode == 0 and dk is not None and fid in W.GENZ6:
+        cen = np.abs(x - u) if fid in (W.GAUSSIAN, W.C0, W.PRODUCT_PEAK) else np.abs(x)
+        dv = 2 * eps * np.abs(a) * (2 * cen + 3 * dk)          # per axis, absolute error of a (x - u) or a x
+        if fid == W.GAUSSIAN:
+            fold = aw * np.sum(2 * np.abs(a) * cen * dv + dv * dv, axis=1)
+        elif fid == W.OSCILLATORY:
+            fold = np.abs(J) * np.sum(dv, axis=1)
+        elif fid == W.CORNER_PEAK:
+            fold = aw * (d + 1) * np.sum(dv, axis=1) / (1.0 + x @ a)
+        else:   # C0, product peak (2 |v| / (1 + v^2) <= 1), discontinuous
+            fold = aw * np.sum(dv, axis=1)
     if fid == W.OSCILLATORY:
         t = np.abs(u[0] + x @ a / (2 * np.pi))
         delta = aw * base + np.abs(J) * (2 * np.pi * eps * (d + 4) * (t + 1.0) + 4 * eps)
@@ -356,6 +383,8 @@ def _weight_error_bounds(fid, d, par, x, w, J, mode):
     if mode == 1:
         # f / F below FLT_MIN, and w / F in the subnormal range (spacing 2^-149)
         delta = delta + 4 * F32_MIN * _f32_scale(fid, d, par) * np.abs(J) + 2.0 ** -148 * _f32_scale(fid, d, par)
+    if fold is not None:
+        delta = delta + fold
     return delta
 
 
@@ -385,7 +414,9 @@ def _check_probes(capi, fid, d, n, mode, B, shift, par, seed=3, it=0, job=0):
         ref = oracle.vsample(fid, d, par, n, seed, it=it, job=job, mode=mode, adjust=0, B=B, t0=t, t1=t + 1,
                              per_cube=True)
         sp = oracle.sample_points(fid, d, par, n, seed, it=it, job=job, mode=mode, B=B, t0=t, t1=t + 1)
-        delta = _weight_error_bounds(fid, d, par, sp["x"], sp["w"], sp["J"], mode)
+        dk = np.take_along_axis(np.diff(B, axis=1)[None, :, :].repeat(sp["k"].shape[0], 0),
+                                sp["k"][:, :, None].astype(np.int64), axis=2)[:, :, 0]
+        delta = _weight_error_bounds(fid, d, par, sp["x"], sp["w"], sp["J"], mode, dk)
         rel = 1e-12 if mode == 0 else 1e-6
         I_ref, V_ref = ref["cubeI"][0], ref["cubeV"][0]
         tol_I = rel * abs(I_ref) + delta.sum() / p + 1e-300
