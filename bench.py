@@ -70,18 +70,23 @@ FALLBACK_SM_MHZ = 2070.0
 
 
 # ------------------------------------------------------------------------------ operation counts
-# FP64 operations of the definition (Algorithm 2 with the VEGAS map), per sample, for the FP64
-# V-Sample: per axis the map (c + u, times R, floor, yn - k, the point's fma, the Jacobian's
-# product) and the family's per-axis terms; per sample the family's closing function counted at the
-# FP64 operations of a table-driven evaluation to full precision (exp 9, cos 13, a reciprocal 5),
-# w = f J and the two sub-cube sums; per sub-cube the mean, the variance (fma, clamp) and the two
-# thread sums; on adjusting iterations the contribution (w F)^2 and one histogram add per axis.
-FP64_AXIS_TERMS = {0: 1, 1: 3, 2: 1, 3: 3, 4: 2, 5: 2, 6: 1, 7: 0}
-FP64_FINISH = {0: 13, 1: 5, 2: 9, 3: 9, 4: 9, 5: 9, 6: 0, 7: 0}
+# FP64 operations per sample of the FP64 V-Sample's formulation for the six Genz families (the
+# kernel with integer c + u and bin extraction and folded per-bin tables): per axis the product
+# (c + u) R, the Jacobian's product and the family's terms -- one fma of the folded table entries
+# and its accumulation for the Gaussian and C0 (an fma, an add), three for the product peak (fma,
+# fma, product), one fma into the sum for the families that only need sum a x (their constant parts
+# summed as fixed-point integers, converted and added once a sample: 2); per sample the family's
+# closing function at the FP64 operations of its table-driven evaluation (exp 10, cos 13, a
+# reciprocal 5, the corner peak's 1 + s and ninth power 5 + a reciprocal), w = f J and the two
+# sub-cube sums; per sub-cube the mean, the variance (fma, clamp) and the two thread sums; on
+# adjusting iterations the contribution (w F)^2 and one histogram add per axis. Counted from the
+# formulation, not from compiled code.
+FP64_AXIS_TERMS = {0: 1, 1: 3, 2: 1, 3: 2, 4: 2, 5: 1}
+FP64_FINISH = {0: 15, 1: 5, 2: 12, 3: 10, 4: 10, 5: 12}
 
 
 def fp64_ops_per_sample(fid: int, d: int, adjust: bool, p: int = 2) -> float:
-    return d * (6 + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 3 + 5.0 / p + ((2 + d) if adjust else 0)
+    return d * (2 + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 3 + 5.0 / p + ((2 + d) if adjust else 0)
 
 
 def algorithmic_ops_per_sample(fid: int, d: int, adjust: bool, f32: bool) -> float:
@@ -833,7 +838,7 @@ def main():
                 "achieved": roof64["achieved"], "frac": roof64["frac"],
                 "traffic": None if ncall != NCALL or None in VSAMPLE64_DRAM_BYTES_BY_KIND.values() else
                 float(np.mean(list(VSAMPLE64_DRAM_BYTES_BY_KIND.values()))),
-                "kernel": "vsample_kernel<8,fid,FP64,HK>",
+                "kernel": "vsample_fast64_kernel<8,fid,HK>",
                 "avg_launch_ms": round(roof64["avg_launch_ms"], 4),
                 "by_kind": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4), "frac": round(v["frac"], 4),
                                 "traffic": v["traffic"]} for k, v in roof64["by_kind"].items()},
