@@ -238,6 +238,11 @@ int mcubes_iteration_dev(int integrand_id, const double *params, int d, int64_t 
  *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress, once
  *     per device, with that device current). Make that first call before any stream capture.
+ *   - Under CUDA's default lazy module loading, the first address lookup and the first launch of
+ *     each (precision, integrand, d) kernel can make the CUDA driver load code, which takes device
+ *     memory. A caller whose pool will own the whole device should make one call of every
+ *     configuration it uses before the pool claims the device, or run with
+ *     CUDA_MODULE_LOADING=EAGER.
  *   - Every call shares the one array per device. The call clears it before use, but two calls
  *     whose work overlaps on the GPU (different streams, no ordering) race on it.
  *   - `stream` NULL means the legacy default stream here, not the library's own stream (creating

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -47,17 +48,30 @@ namespace mcubes {
 __device__ unsigned long long g_bounds_chk[2];
 #endif
 
-// The bounds-check words of a checked build (null otherwise): every launch's VsampleParams
-// carries them.
+// The bounds-check words of a checked build on the current device (null otherwise): every
+// launch's VsampleParams carries them. The symbol's device address differs per device, so it is
+// looked up once per device, with that device current.
 unsigned long long *bounds_words()
 {
 #if MCUBES_CHECKED
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_bounds_chk) != cudaSuccess) {
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static unsigned long long *addr[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
         (void)cudaGetLastError();
         return nullptr;
     }
-    return (unsigned long long *)p;
+    std::lock_guard<std::mutex> lock(mu);
+    if (addr[dev] == nullptr) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bounds_chk) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        addr[dev] = (unsigned long long *)p;
+    }
+    return addr[dev];
 #else
     return nullptr;
 #endif
@@ -171,8 +185,7 @@ int prepare(int fid, const double *params, int d, int64_t ncall, uint64_t seed, 
     P.ctr2_hi = (uint32_t)iteration << 16;
     P.job = job;
     P.adjust = adjust ? 1 : 0;
-    static unsigned long long *const chk = bounds_words();
-    P.chk = chk;
+    P.chk = bounds_words();
     P.R = (double)kNB / (double)pb.g;
     P.R32 = (float)P.R;
     P.ycap = std::nextafter((double)kNB, 0.0);

@@ -327,10 +327,11 @@ def test_device_iteration_matches_host_call(capi):
         torch.cuda.synchronize()
         h = capi.vsample_once(fid, par, d, n, 8, iteration=1, adjust=1, precision=mode, grid_in=B)
         r = res.cpu().numpy()
-        # same kernel and inputs; only the order of the floating-point atomics differs
+        # same kernel and inputs; only the order of the floating-point atomics differs (the grid takes
+        # it through C, to the FP64 grid tolerance of the oracle-parity checks)
         assert math.isclose(r[0], h["I"], rel_tol=1e-13 if mode == 0 else 1e-9)
         assert math.isclose(r[1], h["Var"], rel_tol=1e-11 if mode == 0 else 1e-7)
-        assert np.allclose(g_out.cpu().numpy(), h["grid"], rtol=0, atol=1e-14 if mode == 0 else 1e-8)
+        assert np.allclose(g_out.cpu().numpy(), h["grid"], rtol=0, atol=1e-12 if mode == 0 else 1e-8)
 
 
 F32_MIN = float(np.finfo(np.float32).tiny)

@@ -60,10 +60,45 @@ def test_static_scratch_iteration_matches_caller_scratch(capi, mode):
         capi.iteration_dev_static(fid, par, d, n, 5, 2, 0, 1, mode, g_in, out, res, stream=stream)
         torch.cuda.synchronize()
         a, b = ref_res.cpu().numpy(), res.cpu().numpy()
-        # same kernels and inputs; only the order of floating-point atomics differs
+        # same kernels and inputs; only the order of floating-point atomics differs. The refined grid
+        # takes that order through C: where a bin's damped weight is tiny, Rebin places boundaries
+        # from small differences of the running sums, so the grids agree to the FP64 grid tolerance
+        # of the oracle-parity tests (1e-12), not to the last bit.
         assert math.isclose(a[0], b[0], rel_tol=1e-13 if mode == 0 else 1e-9), (a, b)
         assert math.isclose(a[1], b[1], rel_tol=1e-11 if mode == 0 else 1e-7), (a, b)
-        assert np.allclose(ref_out.cpu().numpy(), out.cpu().numpy(), rtol=0, atol=1e-14 if mode == 0 else 1e-8)
+        assert np.allclose(ref_out.cpu().numpy(), out.cpu().numpy(), rtol=0, atol=1e-12 if mode == 0 else 1e-8)
+
+
+def test_static_scratch_null_stream_with_allocation_hook_armed(capi):
+    """With stream NULL (the legacy default stream) and the library's allocation fault hook armed
+    (its next allocation would fail), the call still succeeds: it takes neither the library's
+    workspace nor its own stream, and it matches the caller-scratch call."""
+    from paper_2302_05730_gb300 import workloads as W
+
+    dev = torch.device("cuda")
+    fid, d, n, mode = W.GAUSSIAN, 6, 900_001, 0
+    par = W.genz_params(fid, d, seed=4)
+    g_in = torch.from_numpy(_grid(d, 21)).to(dev)
+    ref_out, out = torch.empty_like(g_in), torch.empty_like(g_in)
+    ref_res = torch.zeros(2, dtype=torch.float64, device=dev)
+    res = torch.zeros(2, dtype=torch.float64, device=dev)
+    nbytes = capi.workspace_bytes(d)
+    ws = torch.empty(nbytes // 8 + 64, dtype=torch.float64, device=dev)
+    aligned = (ws.data_ptr() + 255) // 256 * 256
+    capi.iteration_dev(fid, par, d, n, 7, 1, 0, 1, mode, g_in, ref_out, ref_res, None, aligned, nbytes,
+                       stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    before = capi.fail_alloc(1)
+    try:
+        capi.iteration_dev_static(fid, par, d, n, 7, 1, 0, 1, mode, g_in, out, res, stream=None)
+        torch.cuda.synchronize()
+    finally:
+        after = capi.fail_alloc(0)
+    assert after == before   # the library made no allocation during the call
+    a, b = ref_res.cpu().numpy(), res.cpu().numpy()
+    assert math.isclose(a[0], b[0], rel_tol=1e-13), (a, b)
+    assert math.isclose(a[1], b[1], rel_tol=1e-11), (a, b)
+    assert np.allclose(ref_out.cpu().numpy(), out.cpu().numpy(), rtol=0, atol=1e-12)
 
 
 def test_static_scratch_rejects_out_of_range(capi):
