@@ -393,7 +393,14 @@ int mcubes_flow_inverse_dev(const mcubes_flow_shape *shape, const float *d_param
 /* Loss and gradient on n samples x with weights w (normalised to sum 1 by the caller):
  *   loss_kind 0 (variance, chi^2): L = sum w / q(x)   (w = f^2 J from the grid sampler);
  *   loss_kind 1 (KL):              L = -sum w log q(x) (w = |f| J).
- * d_grad (param_count FP32) and d_loss[0] accumulate; zero them first. Asynchronous. */
+ * d_grad (param_count FP32) and d_loss[0] accumulate; zero them first. Asynchronous.
+ * Kernels: widths 64 and 128 (output GEMM at most 256 wide, K <= 16) run on the tcgen05 training
+ * kernels (tensor-core MMAs with TMEM accumulators), width 32 and shapes beyond those on the fused
+ * mma.sync kernels, and shapes neither fits on the per-layer kernels; the environment variable
+ * MCUBES_FLOW_TRAIN=mma or =chain forces the latter two (for comparisons). The tcgen05 kernels'
+ * waits are bounded: if one expires they set the int at the workspace's last 256 bytes
+ * (mcubes_flow_work_bytes(shape, n) - 256), and the gradient is then invalid; mcubes_flow_integrate
+ * checks that word after training (TIMEOUT). */
 int mcubes_flow_grad_dev(const mcubes_flow_shape *shape, const float *d_params, int64_t n, const float *d_x,
                          const float *d_w, int loss_kind, float *d_grad, float *d_loss, void *d_work,
                          size_t work_bytes, void *stream);

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -603,6 +604,8 @@ struct Work {
     long long part_stride;
     int part_rows;
     unsigned char *mirror;     // fused kernels: the bf16 weight mirror
+    size_t mirror_bytes;
+    int *err;                  // tcgen05 training: bounded-wait error word
 };
 
 // Fused training scratch for n samples: the mirror and the partial-gradient rows (one per
@@ -637,7 +640,7 @@ inline size_t work_bytes(const Shape &S, long long n, int &nout_max)
     fused_extent(S, n, mb, stride, rows);
     return al(sizeof(float) * (size_t)(S.L + 1) * n * S.d) + 2 * al(sizeof(float) * (size_t)n * nout_max) +
            4 * al(sizeof(__nv_bfloat16) * (size_t)n * S.H) + 2 * al(sizeof(float) * (size_t)n * S.d) +
-           2 * al(sizeof(float) * (size_t)n) + al(mb) + al(sizeof(float) * (size_t)stride * rows);
+           2 * al(sizeof(float) * (size_t)n) + al(mb) + al(sizeof(float) * (size_t)stride * rows) + al(sizeof(int));
 }
 
 inline Work carve(const Shape &S, long long n, void *base)
@@ -661,7 +664,9 @@ inline Work carve(const Shape &S, long long n, void *base)
     size_t mb;
     fused_extent(S, n, mb, w.part_stride, w.part_rows);
     w.mirror = (unsigned char *)q; q += al(mb);
-    w.part = (float *)q;
+    w.mirror_bytes = mb;
+    w.part = (float *)q; q += al(sizeof(float) * (size_t)w.part_stride * w.part_rows);
+    w.err = (int *)q;
     return w;
 }
 
@@ -811,11 +816,24 @@ int mcubes_flow_grad_dev(const mcubes_flow_shape *shape, const float *d_params, 
     if (!d_work || work_bytes < flow::work_bytes(S, n, nm) || ((uintptr_t)d_work & 255u)) return MCUBES_ERR_WORKSPACE;
     flow::Work w = flow::carve(S, n, d_work);
     flow::FusedFlow F;
+    // MCUBES_FLOW_TRAIN selects a path for comparisons: "mma" (fused mma.sync kernels), "chain"
+    // (per-layer kernels); by default the tcgen05 kernels where the shape fits them, then the
+    // fused mma.sync kernels, then the per-layer chain
+    const char *path = std::getenv("MCUBES_FLOW_TRAIN");
+    const bool want_tc = !path || (std::strcmp(path, "mma") != 0 && std::strcmp(path, "chain") != 0);
+    const bool want_fused = !path || std::strcmp(path, "chain") != 0;
     if (w.part_rows > 0 && flow::fused_layout(S, F)) {
-        const flow::FusedTrainWork W{w.hs, w.gA, w.gB, w.gl, w.part, w.part_stride, w.part_rows, w.mirror};
-        const int st = flow::fused_grad(F, d_params, n, S.d, d_x, d_w, loss_kind, d_grad, d_loss, W,
-                                        (cudaStream_t)stream);
-        if (st != flow::kFusedUnsupported) return st;
+        const flow::FusedTrainWork W{w.hs, w.gA, w.gB, w.gl, w.part, w.part_stride, w.part_rows, w.mirror, w.err};
+        if (want_tc) {
+            const int st = flow::tc_grad(S, d_params, n, d_x, d_w, loss_kind, d_grad, d_loss, W, w.mirror_bytes,
+                                         (cudaStream_t)stream);
+            if (st != flow::kFusedUnsupported) return st;
+        }
+        if (want_fused) {
+            const int st = flow::fused_grad(F, d_params, n, S.d, d_x, d_w, loss_kind, d_grad, d_loss, W,
+                                            (cudaStream_t)stream);
+            if (st != flow::kFusedUnsupported) return st;
+        }
     }
     const int sms = flow::sms_of_device();
     if (sms <= 0) return cuda_status(cudaErrorNoDevice);

@@ -407,6 +407,7 @@ struct FusedTrainWork {
     long long part_stride;
     int part_rows;
     unsigned char *mirror;    // the bf16 weight mirror
+    int *err;                 // set by a tcgen05 kernel whose bounded wait expired (the step is then invalid)
 };
 constexpr int kFusedPartRowsMax = 1024;
 constexpr int kFusedBwdRows = kFWarps * 16;   // samples per backward block tile
@@ -415,6 +416,15 @@ constexpr int kFusedBwdRows = kFWarps * 16;   // samples per backward block tile
 // Returns kFusedUnsupported when the shape's kernels do not fit the device's shared memory.
 int fused_grad(const FusedFlow &F, const float *params, long long n, int d, const float *x, const float *w, int kind,
                float *grad, float *loss, const FusedTrainWork &W, cudaStream_t s);
+
+// The same on the tcgen05 training kernels (flow_train_tc.cu), for widths 64 and 128 whose output
+// GEMM is at most 256 wide; its mirror (the tcgen05 layout) must fit mirror_bytes. Returns
+// kFusedUnsupported for other shapes.
+int tc_grad(const Shape &S, const float *params, long long n, const float *x, const float *w, int kind, float *grad,
+            float *loss, const FusedTrainWork &W, size_t mirror_bytes, cudaStream_t s);
+
+// grad[e] += sum over rows r < rows of part[r pstride + e], e < npl, in a fixed order.
+int launch_reduce_part(const float *part, int rows, long long pstride, int npl, float *grad, cudaStream_t s);
 
 // One coupling layer on the 16 rows R0..R0+15 of a block's shared row set hs (row stride HS), run
 // by one warp. The three GEMMs of the MLP chain through registers (the accumulator layout of

@@ -754,7 +754,13 @@ extern "C" int mcubes_flow_integrate(int integrand_id, const double *params, int
             out->train_loss_last = l;
         }
     }
-    if ((st = cuda_status(cudaStreamSynchronize(s)))) return finish(st);
+    {   // the tcgen05 training kernels' error word: the workspace's last 256 bytes
+        int h_terr = 0;
+        const int *d_terr = (const int *)((const char *)d_work + mcubes_flow_work_bytes(&sh, batch) - 256);
+        if ((st = cuda_status(cudaMemcpyAsync(&h_terr, d_terr, sizeof(int), cudaMemcpyDeviceToHost, s)))) return finish(st);
+        if ((st = cuda_status(cudaStreamSynchronize(s)))) return finish(st);
+        if (h_terr) return finish(MCUBES_ERR_TIMEOUT);
+    }
     out->seconds_train = seconds_since(t0);
 
     // ---- 4. m-Cubes iterations with the flow as proposal: the fused sampling kernel where the

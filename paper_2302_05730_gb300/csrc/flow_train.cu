@@ -615,6 +615,13 @@ int grad_h(const FusedFlow &F, const unsigned char *mirror, long long n, int d, 
 
 }  // namespace
 
+int launch_reduce_part(const float *part, int rows, long long pstride, int npl, float *grad, cudaStream_t s)
+{
+    if (npl <= 0) return MCUBES_OK;
+    reduce_part_kernel<<<(unsigned)((npl + 31) / 32), 256, 0, s>>>(part, rows, pstride, npl, grad);
+    return cuda_status(cudaGetLastError());
+}
+
 int fused_grad(const FusedFlow &F, const float *params, long long n, int d, const float *x, const float *w, int kind,
                float *grad, float *loss, const FusedTrainWork &W, cudaStream_t s)
 {

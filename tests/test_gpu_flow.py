@@ -367,3 +367,75 @@ def test_learned_proposal_double_gaussian_d8(capi):
     gain = r["vegas_var_per_sample"] / r["flow_var_per_sample"]
     assert abs(r["flow"]["estimate"] - exact) < 4.5 * r["flow"]["error"], (r["flow"], gain)
     assert gain > 10.0, (r["flow"], r["vegas"], gain)
+
+
+def _grad(capi, shape, p, x, w, kind, path=None):
+    """mcubes_flow_grad_dev on one batch, with MCUBES_FLOW_TRAIN set to `path` for the call."""
+    import os
+    n, d = x.shape
+    ws, nb, keep = _work(capi, shape, n)
+    dp = torch.from_numpy(p).cuda()
+    dx = torch.from_numpy(x.astype(np.float32)).cuda()
+    dw = torch.from_numpy(w.astype(np.float32)).cuda()
+    grad = torch.zeros(p.size, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    old = os.environ.pop("MCUBES_FLOW_TRAIN", None)
+    if path is not None:
+        os.environ["MCUBES_FLOW_TRAIN"] = path
+    try:
+        capi.flow_grad_dev(shape, dp, n, dx, dw, kind, grad, loss, ws, nb)
+        torch.cuda.synchronize()
+    finally:
+        os.environ.pop("MCUBES_FLOW_TRAIN", None)
+        if old is not None:
+            os.environ["MCUBES_FLOW_TRAIN"] = old
+    # the tcgen05 kernels' error word: the int at the workspace's last 256 bytes
+    off = (ws - keep.data_ptr() + nb - 256) // 4
+    assert int(keep[off:off + 1].view(torch.int32).item()) == 0
+    return grad.cpu().numpy().astype(np.float64), float(loss.item())
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d,L,H,K,n", [(8, 4, 64, 16, 3000), (8, 2, 128, 16, 1000), (10, 6, 128, 16, 40000),
+                                       (5, 3, 64, 8, 700)])
+def test_tcgen05_training_matches_other_paths(capi, d, L, H, K, n, kind):
+    """The tcgen05 training kernels (default for widths 64 and 128) against the fused mma.sync
+    kernels (width 64) or the per-layer chain (width 128) on the same batch: the same loss and the
+    same gradient up to the bf16 rounding of the MLP operands (the order of the sums differs).
+    40,000 samples make the backward CTAs take several 128-sample tiles each."""
+    p = _params(d, L, H, K, seed=30 + d + H, scale=0.1)
+    rng = np.random.default_rng(31)
+    x = rng.uniform(0.0, 1.0, (n, d))
+    f = np.exp(-np.sum((x - 0.4) ** 2, axis=1) * 6.0)
+    w = f ** 2 if kind == 0 else f
+    w = w / w.sum()
+    shape = capi.flow_shape(d, L, H, K)
+    g_tc, l_tc = _grad(capi, shape, p, x, w, kind)
+    g_ref, l_ref = _grad(capi, shape, p, x, w, kind, "mma" if H == 64 else "chain")
+    assert abs(l_tc - l_ref) <= 1e-5 * abs(l_ref), (l_tc, l_ref)
+    rel = np.linalg.norm(g_tc - g_ref) / np.linalg.norm(g_ref)
+    cos = float(g_tc @ g_ref / (np.linalg.norm(g_tc) * np.linalg.norm(g_ref)))
+    assert rel < 2e-2 and cos > 0.9998, (rel, cos)
+
+
+def test_tcgen05_training_config5_shape_matches_finite_differences(capi):
+    """The d = 10 flow of the large configuration (6 coupling layers, width 128, 16 bins) on the
+    tcgen05 kernels against the oracle's finite-difference gradient on a parameter subset."""
+    d, L, H, K = 10, 6, 128, 16
+    n = 256
+    p = _params(d, L, H, K, seed=44, scale=0.1)
+    rng = np.random.default_rng(45)
+    x = rng.uniform(0.0, 1.0, (n, d))
+    f = np.exp(-np.sum((x - 0.35) ** 2, axis=1) * 8.0)
+    w = f ** 2 / np.sum(f ** 2)
+    shape = capi.flow_shape(d, L, H, K)
+    g, l = _grad(capi, shape, p, x, w, 0)
+    l_ref = F.loss(p.astype(np.float64), x.astype(np.float32).astype(np.float64), w, d, L, H, K, "variance")
+    assert abs(l - l_ref) <= 2e-2 * abs(l_ref)
+    idx = np.random.default_rng(46).choice(p.size, 300, replace=False)
+    g_ref = F.grad_fd(p.astype(np.float64), x.astype(np.float32).astype(np.float64), w, d, L, H, K, "variance",
+                      eps=1e-4, idx=idx)
+    a = g[idx]
+    cos = float(a @ g_ref / (np.linalg.norm(a) * np.linalg.norm(g_ref)))
+    rel = float(np.linalg.norm(a - g_ref) / np.linalg.norm(g_ref))
+    assert cos > 0.998 and rel < 0.05, (cos, rel)
