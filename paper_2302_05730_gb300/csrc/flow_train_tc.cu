@@ -69,6 +69,20 @@ __device__ __forceinline__ void relu_cols(uint32_t taddr, const float *bias, uns
     }
 }
 
+// dst[0..8) = v (first) or dst[0..8) += v, as two 16-byte accesses (dst 16-byte aligned).
+__device__ __forceinline__ void add8(float *dst, const float (&v)[8], bool first)
+{
+    float4 *p = reinterpret_cast<float4 *>(dst);
+    float4 a = make_float4(v[0], v[1], v[2], v[3]), b = make_float4(v[4], v[5], v[6], v[7]);
+    if (!first) {
+        const float4 x = p[0], y = p[1];
+        a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+        b.x += y.x; b.y += y.y; b.z += y.z; b.w += y.w;
+    }
+    p[0] = a;
+    p[1] = b;
+}
+
 // Sum of v over the warp's 32 lanes (rows), added to *dst by lane 0.
 __device__ __forceinline__ void col_sum_add(float v, float *dst)
 {
@@ -135,18 +149,22 @@ __global__ void __launch_bounds__(kTT, 1)
     long long step = 0;
 
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const long long sr = tile * kTcRows + row;
-        if (half == 0)
-            for (int a = 0; a < d; ++a) hr[a] = sr < n ? x[sr * d + a] : 0.5f;
+        const long long r0 = tile * kTcRows, sr = r0 + row;
+        const int rows = (int)(n - r0 < (long long)kTcRows ? n - r0 : (long long)kTcRows);
+        // the tile's rows are contiguous in x: loaded by all threads, coalesced
+        for (int e = tid; e < kTcRows * d; e += kTT) {
+            const int r = e / d, a = e - r * d;
+            hs[r * HS + a] = r < rows ? x[r0 * d + e] : 0.5f;
+        }
         float lq = 0.f;
         for (int l = 0; l < F.L && ok; ++l, ++step) {
             const TcLayer &Y = F.lay[l];
             before_sync();
             __syncthreads();   // hs holds layer l's input; the previous layer's MMAs and reads are done
             after_sync();
-            if (half == 0 && sr < n) {
-                float *hl = hsave + (size_t)l * (size_t)n * d + sr * d;
-                for (int a = 0; a < d; ++a) hl[a] = hr[a];
+            {
+                float *hl = hsave + (size_t)l * (size_t)n * d + r0 * d;
+                for (int e = tid; e < rows * d; e += kTT) hl[e] = hs[(e / d) * HS + e % d];
             }
             const int b = (int)(step % nbuf);
             if (tid == 0) {
@@ -354,11 +372,27 @@ __global__ void __launch_bounds__(kTT, 1)
     const long long ntiles = (n + kTcRows - 1) / kTcRows;
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const bool first = tile == blockIdx.x;
-        const long long sr = tile * kTcRows + row;
+        const long long r0 = tile * kTcRows, sr = r0 + row;
+        const int rows = (int)(n - r0 < (long long)kTcRows ? n - r0 : (long long)kTcRows);
         const bool live = sr < n;
-        if (half == 0) {
-            for (int a = 0; a < d; ++a) hr[a] = live ? hin[sr * d + a] : 0.5f;
-            gls[row] = live ? gl[sr] : 0.f;
+        // the tile's input rows are contiguous: loaded by all threads, coalesced
+        for (int e = tid; e < kTcRows * d; e += kTT) {
+            const int r = e / d, a = e - r * d;
+            hs[r * HS + a] = r < rows ? hin[r0 * d + e] : 0.5f;
+        }
+        if (half == 0) gls[row] = live ? gl[sr] : 0.f;
+        // dL/dh_{l+1} of this row's axes, fetched now so that the loads overlap the recomputation:
+        // this half's transformed axes (j = half, half + 2, ...) and the kept axes c = 8 half .. 8 half + 7
+        float gyB[(kMaxAB + 1) / 2], gyA[8];
+#pragma unroll
+        for (int u = 0; u < (kMaxAB + 1) / 2; ++u) {
+            const int j = half + 2 * u;
+            gyB[u] = (live && gout && j < nB) ? gout[sr * d + Y.B[j]] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = 8 * half + u;
+            gyA[u] = (live && gout && c < nA) ? gout[sr * d + Y.A[c]] : 0.f;
         }
         before_sync();
         __syncthreads();
@@ -402,6 +436,7 @@ __global__ void __launch_bounds__(kTT, 1)
         // ---- coupling backward of this half's axes: dL/do into X (bf16), its column sums into db3,
         // dL/dx of the B axes to gin
         const float glq = gls[row];
+#pragma unroll 1
         for (int j = half; j < nB; j += 2) {
             float raw[SW];
 #pragma unroll
@@ -412,7 +447,10 @@ __global__ void __launch_bounds__(kTT, 1)
                 for (int u = 0; u < 8; ++u) raw[c0 + u] = v[u] + b3[j * SW + c0 + u];
             }
             const int ax = Y.B[j];
-            const float gy = (live && gout) ? gout[sr * d + ax] : 0.f;
+            float gy = 0.f;
+#pragma unroll
+            for (int u = 0; u < (kMaxAB + 1) / 2; ++u)
+                if (half + 2 * u == j) gy = gyB[u];
             const float gx = pq_backward<K>(raw, hr[ax], gy, glq, [&raw](int k, float v) { raw[k] = v; });
 #pragma unroll
             for (int k = 0; k < SW; ++k)
@@ -468,11 +506,7 @@ __global__ void __launch_bounds__(kTT, 1)
             for (int cc = c0h; cc < c1h; cc += 8) {
                 float v[8];
                 tmem_ld8(tb + 256u + (uint32_t)(c * H + cc), v);
-                if (nrow < M3 && k < NO) {
-                    float *dst = prow + pW3 + (j * NO + k) * H + cc;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) dst[u] = first ? v[u] : dst[u] + v[u];
-                }
+                if (nrow < M3 && k < NO) add8(prow + pW3 + (j * NO + k) * H + cc, v, first);
             }
         }
         // ---- dR1 = dZ2 W2 into [0, H); dW2 = dZ2^T R1 into [H, 2H)
@@ -509,11 +543,7 @@ __global__ void __launch_bounds__(kTT, 1)
         for (int cc = c0h; cc < c1h; cc += 8) {
             float v[8];
             tmem_ld8(tb + (uint32_t)(H + cc), v);
-            if (row < H) {
-                float *dst = prow + pW2 + row * H + cc;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) dst[u] = first ? v[u] : dst[u] + v[u];
-            }
+            if (row < H) add8(prow + pW2 + row * H + cc, v, first);
         }
         // ---- dA = dZ1 W1 into [0, 16); dW1 = dZ1^T A1 into [H, H + 16)
         to_mma();
@@ -532,10 +562,7 @@ __global__ void __launch_bounds__(kTT, 1)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int c = 8 * half + u;
-                    if (c < nA) {
-                        const int ax = Y.A[c];
-                        gin[sr * d + ax] = (gout ? gout[sr * d + ax] : 0.f) + v[u];
-                    }
+                    if (c < nA) gin[sr * d + Y.A[c]] = gyA[u] + v[u];
                 }
             tmem_ld8(tb + (uint32_t)(H + 8 * half), v);   // dW1 row h = row, columns [8 half, 8 half + 8)
             if (row < H)
