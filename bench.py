@@ -20,6 +20,7 @@ The legs:
   config5     d = 10 product peak and C0 at 1e9 samples per iteration, 20 iterations, both
               precisions; and the learned proposal (6 layers, width 128) at d = 10
   batch       4096 independent Gaussian integrations in one graph launch
+  train_step  one training step of the flow per shape and kernel path (tcgen05, mma.sync, per layer)
   learned     the learned proposal at d = 8 (double and rotated Gaussians)
   pagani      the paper's other workload (off unless --pagani)
 
@@ -545,6 +546,49 @@ def learned_leg(capi, W, train_steps: int, n_it: int = 1 << 20, seeds=(0, 1, 2))
     return out
 
 
+# ------------------------------------------------------------------------------ training step
+def train_step_leg(capi, torch, steps: int = 20):
+    """One training step (loss and gradient of a 2^14-sample batch, mcubes_flow_grad_dev) per flow
+    shape and per kernel path: the tcgen05 kernels (the default where the shape fits them), the
+    fused mma.sync kernels and the per-layer chain (MCUBES_FLOW_TRAIN); CUDA events on the
+    launching stream after three warm-up steps. A path that does not take a shape falls back, so a
+    timing equal to the next path's means the path does not fit."""
+    out = {}
+    n = 1 << 14
+    for (d, L, H, K) in [(8, 4, 64, 16), (8, 4, 128, 16), (10, 6, 128, 16)]:
+        shape = capi.flow_shape(d, L, H, K)
+        npar = capi.flow_param_count(shape)
+        rng = np.random.default_rng(1)
+        p = torch.from_numpy(rng.normal(0, 0.1, npar).astype(np.float32)).cuda()
+        x = torch.from_numpy(rng.uniform(0, 1, (n, d)).astype(np.float32)).cuda()
+        w = torch.from_numpy((rng.exponential(1.0, n) / n).astype(np.float32)).cuda()
+        nb = capi.flow_work_bytes(shape, n)
+        buf = torch.empty(nb // 4 + 128, dtype=torch.float32, device="cuda")
+        ws = (buf.data_ptr() + 255) // 256 * 256
+        g = torch.zeros(npar, dtype=torch.float32, device="cuda")
+        lo = torch.zeros(1, dtype=torch.float32, device="cuda")
+        st = torch.cuda.current_stream()
+        res = {}
+        for path in ("tc", "mma", "chain"):
+            os.environ.pop("MCUBES_FLOW_TRAIN", None)
+            if path != "tc":
+                os.environ["MCUBES_FLOW_TRAIN"] = path
+            for _ in range(3):
+                capi.flow_grad_dev(shape, p, n, x, w, 0, g, lo, ws, nb, stream=st)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for _ in range(steps):
+                capi.flow_grad_dev(shape, p, n, x, w, 0, g, lo, ws, nb, stream=st)
+            b.record(st)
+            b.synchronize()
+            res[path] = a.elapsed_time(b) / steps
+        os.environ.pop("MCUBES_FLOW_TRAIN", None)
+        out[f"d{d}_L{L}_H{H}_K{K}"] = res
+    return {"batch": n, "ms_per_step": out}
+
+
 # ------------------------------------------------------------------------------ config 5
 def config5_leg(capi, W, exact, flow_steps: int, with_flow: bool = True):
     """d = 10 product peak and C0 (a_i ~ U[5, 15], u_i ~ U[0.2, 0.8], seed 0) at 1e9 samples per
@@ -751,6 +795,7 @@ def main():
         return
     if args.learned_only:
         if rank == 0:
+            emit("train_step", train_step_leg(capi, torch))
             emit("learned", learned_leg(capi, W, args.train_steps))
         return
     if args.pagani_only:
@@ -940,6 +985,7 @@ def main():
         emit("batch", batch_leg(capi, W))
 
     if rank == 0 and not args.no_learned:
+        emit("train_step", train_step_leg(capi, torch))
         emit("learned", learned_leg(capi, W, args.train_steps))
 
     if rank == 0 and args.pagani:
