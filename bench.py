@@ -764,6 +764,7 @@ def main():
     ap.add_argument("--pagani-only", action="store_true", help="only the PAGANI leg (profiling runs)")
     ap.add_argument("--learned-only", action="store_true", help="only the learned-proposal leg (profiling runs)")
     ap.add_argument("--config5-only", action="store_true", help="only the d = 10, 1e9 leg")
+    ap.add_argument("--train-step-only", action="store_true", help="only the training-step leg (profiling runs)")
     ap.add_argument("--train-steps", type=int, default=2000, help="flow training steps in the learned legs")
     ap.add_argument("--unit-rates", action="store_true", help="only the unit-rate microbenchmarks")
     ap.add_argument("--clocks-csv", default=None,
@@ -802,6 +803,10 @@ def main():
         if rank == 0:
             pars0 = {fid: W.genz_params(fid, D, seed=0) for fid in W.GENZ6}
             emit("pagani", pagani_leg(capi, W, torch, dev, pars0, {}))
+        return
+    if args.train_step_only:
+        if rank == 0:
+            emit("train_step", train_step_leg(capi, torch, steps=args.steps))
         return
     if args.config5_only:
         if rank == 0:
