@@ -278,11 +278,16 @@ typedef struct mcubes_job {
  * Zero entries take the defaults (256 threads, 4 sub-cubes per thread per tile, block-private
  * histogram). A tile is block_threads x cubes_per_thread consecutive sub-cubes of one job.
  * hist_mode 0: block-private shared-memory histogram, flushed once per job and block.
- * hist_mode 1: FP64 atomics straight into the job's global bin contributions. */
+ * hist_mode 1: FP64 atomics straight into the job's global bin contributions.
+ * In FP64, the jobs of one (d, Genz family) class take the fast FP64 V-Sample kernel (the one
+ * mcubes_tuning.fp64_plain describes; block-private shared histogram, hist_mode not consulted)
+ * when every job of the class meets its conditions and its shared memory fits; fp64_plain = 1
+ * sends every class to the plain kernels. mcubes_tune_batch leaves it 0. */
 typedef struct mcubes_batch_tuning {
     int32_t block_threads[MCUBES_DMAX + 1];
     int32_t cubes_per_thread[MCUBES_DMAX + 1];
     int32_t hist_mode[MCUBES_DMAX + 1];
+    int32_t fp64_plain;   /* 0 or 1, else INVALID_ARG */
 } mcubes_batch_tuning;
 
 /* Integrate n_jobs independent problems together on the current device.
@@ -491,13 +496,16 @@ void mcubes_shutdown(void);
 
 /* Unit rates of the current device, measured by microbenchmarks (about 50 ms): the per-SM
  * throughput of the operations the V-Sample kernels are built from, per SM clock at the
- * device's maximum SM clock (cudaDevAttrClockRate). out[0..min(n_out, 7) - 1] receives:
+ * device's maximum SM clock (cudaDevAttrClockRate). out[0..min(n_out, 10) - 1] receives:
  *   0: FP32 fused multiply-adds (lanes); 1: FP64 fused multiply-adds (lanes);
  *   2: exp2f (lanes); 3: Philox4x32-10 calls;
  *   4: random 8-byte shared-memory gathers from an 8 x 500 table (lanes);
  *   5: random FP32 shared atomics into an 8 x 500 histogram (lanes);
  *   6: random u32 shared atomics with their old value into 8 lane-interleaved copies of an
- *      8 x 500 histogram, carry into a high word (lanes; one 1024-thread block an SM).
+ *      8 x 500 histogram, carry into a high word (lanes; one 1024-thread block an SM);
+ *   7: random u64 shared reductions (no returned value) into one 8 x 500 histogram (lanes; one
+ *      1024-thread block an SM); 8: the same into 4 lane-interleaved copies;
+ *   9: random u32 shared reductions (no returned value) into 8 lane-interleaved copies.
  * Errors: INVALID_ARG (NULL out, n_out < 1), ALLOC, CUDA. Synchronous. */
 int mcubes_unit_rates(double *out, int n_out);
 

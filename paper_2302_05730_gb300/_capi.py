@@ -68,7 +68,8 @@ class Job(ctypes.Structure):
 class BatchTuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32 * (DMAX + 1)),
                 ("cubes_per_thread", ctypes.c_int32 * (DMAX + 1)),
-                ("hist_mode", ctypes.c_int32 * (DMAX + 1))]
+                ("hist_mode", ctypes.c_int32 * (DMAX + 1)),
+                ("fp64_plain", ctypes.c_int32)]
 
     def as_dict(self):
         return {d: dict(block_threads=self.block_threads[d], cubes_per_thread=self.cubes_per_thread[d],
@@ -523,7 +524,8 @@ def checked_violations(reset: bool = True):
 
 
 UNIT_RATE_NAMES = ("ffma_lanes", "dfma_lanes", "exp2f_lanes", "philox_calls", "shared_gather8_lanes",
-                   "shared_atomic_f32_lanes", "shared_atomic_u32x8_lanes")
+                   "shared_atomic_f32_lanes", "shared_atomic_u32x8_lanes", "shared_red_u64_lanes",
+                   "shared_red_u64x4_lanes", "shared_red_u32x8_lanes")
 
 
 def unit_rates() -> dict:

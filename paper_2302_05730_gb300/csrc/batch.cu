@@ -13,6 +13,7 @@
 #include "../../include/mcubes.h"
 #include "internal.h"
 #include "vsample.cuh"
+#include "vsample64.cuh"
 
 using namespace mcubes;
 
@@ -94,6 +95,7 @@ struct Plan {
     };
     std::vector<Class> classes;
     std::vector<BatchTile> h_tiles_all;   // kept for re-tiling
+    std::map<std::pair<int, int>, bool> fast;   // FP64 (d, family) classes whose jobs all take the fast kernel
 
     ~Plan() { release(); }
     void release()
@@ -105,7 +107,7 @@ struct Plan {
         dmem = nullptr;
     }
 
-    int init(int n, const mcubes_job *jobs, int itmax_, int iter_adjust, int precision)
+    int init(int n, const mcubes_job *jobs, int itmax_, int iter_adjust, int precision, int plain64 = 0)
     {
         n_jobs = n;
         itmax = itmax_;
@@ -146,6 +148,19 @@ struct Plan {
         d_rb_job = (uint32_t *)q; q += b_rb;
         d_rb_axis = (uint32_t *)q; q += b_rb;
 
+        // FP64 classes of the six Genz families take the fast kernel when every job's fold is usable;
+        // their jobs' parameters then carry it
+        fast.clear();
+        if (precision == MCUBES_FP64 && !plain64) {
+            for (int j = 0; j < n; ++j) {
+                const std::pair<int, int> key{pb[j].d, pb[j].fid};
+                VsampleParams Q = pb[j].P;
+                const bool ok = fast64_fold(pb[j].fid, Q, pb[j].d) &&
+                                fast64_smem_bytes_rt(pb[j].d, pb[j].fid, 1) <= (size_t)227 * 1024;
+                auto it = fast.find(key);
+                fast[key] = (it == fast.end() ? true : it->second) && ok;
+            }
+        }
         std::vector<BatchJob> hj(n);
         std::vector<double *> g0(n), g1(n), cp(n);
         std::vector<int> dims(n);
@@ -155,6 +170,7 @@ struct Plan {
             const Problem &p = pb[j];
             std::memset(&hj[j], 0, sizeof(BatchJob));
             hj[j].P = p.P;
+            if (fast.count({p.d, p.fid}) && fast[{p.d, p.fid}]) fast64_fold(p.fid, hj[j].P, p.d);
             hj[j].P.probe = nullptr;
             hj[j].P.probe_mask = 0xFFFFFFFFu;
             g0[j] = grid0 + go;
@@ -196,6 +212,8 @@ struct Plan {
             c.fid = kv.first.second;
             c.shape = shape_for(tune, c.d);
             if (!shape_ok(c.shape)) return MCUBES_ERR_INVALID_ARG;
+            const auto fi = fast.find(kv.first);
+            if (fi != fast.end() && fi->second) c.shape.hist = 2;   // the fast FP64 kernel (shared histogram)
             const uint64_t per = (uint64_t)c.shape.threads * (uint64_t)c.shape.cpt;
             std::vector<BatchTile> tl;
             for (int j : kv.second) {
@@ -313,8 +331,10 @@ extern "C" int mcubes_integrate_batch(int n_jobs, const mcubes_job *jobs, int it
     if (st) return st;
     std::memset(out, 0, sizeof(mcubes_result) * n_jobs);
 
+    if (tune && tune->fp64_plain != 0 && tune->fp64_plain != 1) return MCUBES_ERR_INVALID_ARG;
+
     Plan plan;
-    if ((st = plan.init(n_jobs, jobs, itmax, iter_adjust, precision))) return st;
+    if ((st = plan.init(n_jobs, jobs, itmax, iter_adjust, precision, tune ? tune->fp64_plain : 0))) return st;
     if ((st = plan.tile(tune))) return st;
 
     cudaStream_t run = nullptr;

@@ -73,7 +73,8 @@ MCUBES_DECLARE_LAUNCHER(f32, 9)
 #undef MCUBES_DECLARE_LAUNCHER
 
 // Batched launchers: one (precision, integrand) slice, any d. hist_mode 0 = block-private
-// shared histogram, 1 = FP64 atomics straight into each job's global bin contributions.
+// shared histogram, 1 = FP64 atomics straight into each job's global bin contributions, 2 = the fast
+// FP64 kernel of the Genz families (shared histogram; every job's parameters carry its fold).
 struct BatchJob;
 struct BatchTile;
 #define MCUBES_DECLARE_BATCH_LAUNCHER(PREC, FID)                                                   \

@@ -20,6 +20,7 @@ constexpr int kIters = 512;
 constexpr int kThreads = 256;
 constexpr int kBins = 500;    // bins per axis, as the histogram
 constexpr int kAxes = 8;
+constexpr int kUnitRates = 10;
 
 __device__ __forceinline__ uint32_t lcg(uint32_t s) { return s * 1664525u + 1013904223u; }
 // a bin index in [0, kBins) from the top 16 bits of a 32-bit state
@@ -145,6 +146,59 @@ __global__ void k_atom_u32x8(float *out, uint32_t seed)
     out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// 64-bit fixed-point adds without a returned value (red.shared.add.u64) into R lane-interleaved
+// copies of the 8 x 500 histogram (copy g = lane mod R holds bin e at word e R + g)
+template <int R>
+__global__ void k_red_u64(float *out, uint32_t seed)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(sm);
+    for (int e = threadIdx.x; e < kAxes * kBins * R; e += blockDim.x) h[e] = 0ull;
+    __syncthreads();
+    const int g = threadIdx.x & (R - 1);
+    uint32_t s = seed ^ (threadIdx.x * 0x9E3779B9u) ^ (blockIdx.x * 0x85EBCA6Bu);
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(h);
+    for (int it = 0; it < kIters / 8; ++it) {
+        const unsigned long long v = ((unsigned long long)(s >> 4) << 12) | 1ull;
+#pragma unroll
+        for (int i = 0; i < kAxes; ++i) {
+            s = lcg(s);
+            const uint32_t a = base + (uint32_t)(((i * kBins + bin_of(s)) * R + g) * 8);
+            asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+        }
+    }
+    __syncthreads();
+    float acc = 0.f;
+    for (int e = threadIdx.x; e < kAxes * kBins * R; e += blockDim.x) acc += (float)h[e];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// u32 adds without a returned value (red.shared.add.u32) into 8 lane-interleaved copies: the
+// fixed-point update without its carry
+__global__ void k_red_u32x8(float *out, uint32_t seed)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint32_t *h = reinterpret_cast<uint32_t *>(sm);
+    for (int e = threadIdx.x; e < kAxes * kBins * 8; e += blockDim.x) h[e] = 0u;
+    __syncthreads();
+    const int g = threadIdx.x & 7;
+    uint32_t s = seed ^ (threadIdx.x * 0x9E3779B9u) ^ (blockIdx.x * 0x85EBCA6Bu);
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(h);
+    for (int it = 0; it < kIters / 8; ++it) {
+        const uint32_t v = (s >> 4) | 1u;
+#pragma unroll
+        for (int i = 0; i < kAxes; ++i) {
+            s = lcg(s);
+            const uint32_t a = base + (uint32_t)(((i * kBins + bin_of(s)) * 8 + g) * 4);
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+        }
+    }
+    __syncthreads();
+    float acc = 0.f;
+    for (int e = threadIdx.x; e < kAxes * kBins * 8; e += blockDim.x) acc += (float)h[e];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 struct Probe {
     int threads, blocks_per_sm;
     size_t smem;
@@ -193,13 +247,17 @@ extern "C" int mcubes_unit_rates(double *out, int n_out)
     const double clk = clk_khz * 1e3;
     const size_t tab_bytes = sizeof(float2) * kAxes * kBins, f32_bytes = sizeof(float) * kAxes * kBins;
     const size_t u32_bytes = sizeof(uint32_t) * kAxes * kBins * 9;
+    const size_t u64x1_bytes = sizeof(uint64_t) * kAxes * kBins, u64x4_bytes = 4 * u64x1_bytes;
+    const size_t r32_bytes = sizeof(uint32_t) * kAxes * kBins * 8;
     e = cudaFuncSetAttribute(k_atom_u32x8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)u32_bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_red_u64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)u64x4_bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_red_u32x8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r32_bytes);
     if (e != cudaSuccess) return cuda_status(e);
     float *buf = nullptr;
     e = mc_malloc((void **)&buf, sizeof(float) * (size_t)sms * 4 * kThreads);
     if (e != cudaSuccess) return cuda_status(e);
     int st = MCUBES_OK;
-    double r[7] = {0, 0, 0, 0, 0, 0, 0};
+    double r[kUnitRates] = {};
     const Probe alu{kThreads, 4, 0, 8.0 * kIters};
     r[0] = time_probe(alu, sms, clk, buf, [](unsigned b, int t, size_t m, float *o) { k_ffma<<<b, t, m>>>(o, 1.0000001f, 1e-7f); }, st);
     if (!st)
@@ -218,8 +276,17 @@ extern "C" int mcubes_unit_rates(double *out, int n_out)
     if (!st)
         r[6] = time_probe(Probe{4 * kThreads, 1, u32_bytes, 1.0 * kIters}, sms, clk, buf,
                           [](unsigned b, int t, size_t m, float *o) { k_atom_u32x8<<<b, t, m>>>(o, 7u); }, st);
+    if (!st)
+        r[7] = time_probe(Probe{4 * kThreads, 1, u64x1_bytes, 1.0 * kIters}, sms, clk, buf,
+                          [](unsigned b, int t, size_t m, float *o) { k_red_u64<1><<<b, t, m>>>(o, 7u); }, st);
+    if (!st)
+        r[8] = time_probe(Probe{4 * kThreads, 1, u64x4_bytes, 1.0 * kIters}, sms, clk, buf,
+                          [](unsigned b, int t, size_t m, float *o) { k_red_u64<4><<<b, t, m>>>(o, 7u); }, st);
+    if (!st)
+        r[9] = time_probe(Probe{4 * kThreads, 1, r32_bytes, 1.0 * kIters}, sms, clk, buf,
+                          [](unsigned b, int t, size_t m, float *o) { k_red_u32x8<<<b, t, m>>>(o, 7u); }, st);
     cudaFree(buf);
     if (st) return st;
-    for (int i = 0; i < n_out && i < 7; ++i) out[i] = r[i];
+    for (int i = 0; i < n_out && i < kUnitRates; ++i) out[i] = r[i];
     return MCUBES_OK;
 }

@@ -26,6 +26,8 @@
 // (vsample.cuh): finish_block, the FP64 shared histogram.
 #pragma once
 
+#include <cmath>
+
 #include "vsample.cuh"
 
 namespace mcubes {
@@ -72,6 +74,36 @@ __device__ __forceinline__ double c_plus_u(uint32_t hi, uint32_t lo)
     return N != 0ull ? __longlong_as_double((long long)bits) : 0.0;
 }
 
+// Host: the fast kernel's per-launch parameters for family fid (0..5) at dimension d, from the
+// plain FP64 parameters in Q. It serves the family when the strata fit its integer c + u (g <= 2^11)
+// and the per-axis fold factors are usable: every a_i finite and non-zero (positive for C0, whose
+// |a (x - u)| must equal a |x - u|) and the folded scale finite and non-zero. Q then carries the fold
+// factors in ip.b (a, or a / (2 pi) for the oscillatory family), the scale nd^d / prod(fold)
+// (nd^d prod a for the product peak) and the fraction bits of the fixed-point table sums (sum_i |fold_i|
+// 2^fix_shift below 2^61). Returns false, leaving Q's fold fields unspecified, otherwise.
+inline bool fast64_fold(int fid, VsampleParams &Q, int d)
+{
+    if (fid < 0 || fid > 5 || Q.g > 2048u) return false;
+    constexpr double kTwoPi = 6.283185307179586;
+    double scale = 1.0, fsum = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const double a = Q.ip.a[i];
+        if (!std::isfinite(a) || a == 0.0 || (fid == kC0 && a < 0.0)) return false;
+        const double f = fid == kOscillatory ? a / kTwoPi : a;
+        if (!std::isfinite(f) || f == 0.0) return false;
+        Q.ip.b[i] = f;
+        fsum += std::fabs(f);
+        scale *= (double)kNB;
+        scale = fid == kProductPeak ? scale * f : scale / f;
+    }
+    if (!std::isfinite(scale) || scale == 0.0 || !(fsum < 1e15)) return false;
+    Q.fscale = scale;
+    int e = 0;
+    std::frexp(fsum * 1.0000001 + 1.0, &e);   // fsum + 1 < 2^e
+    Q.fix_shift = 61 - e;
+    return true;
+}
+
 // Shared-memory bytes of one fast FP64 block: the (P, Q) table, the FP64 histogram copy when
 // adjusting, the cut thresholds, and the exp or cos table.
 template <int D, int FID, int HK>
@@ -79,6 +111,15 @@ __host__ __device__ constexpr size_t fast64_smem_bytes()
 {
     return (size_t)D * kNB * (16 + (HK == 1 ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
            (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
+}
+
+// The same at a run-time d and family (0..5), for host-side eligibility checks; 0 for other families.
+inline size_t fast64_smem_bytes_rt(int d, int fid, int hk)
+{
+    const bool cut = fid == kDiscontinuous, ex = fid == kGaussian || fid == kC0 || fid == kDiscontinuous,
+               co = fid == kOscillatory;
+    if (fid < 0 || fid > 5) return 0;
+    return (size_t)d * kNB * (16 + (hk == 1 ? 8 : 0) + (cut ? 8 : 0)) + (ex ? kExpTab * 8 : 0) + (co ? kCosTab * 16 : 0);
 }
 
 // exp(x): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(x) = 2^m 2^(j/64) e^r; e^r - 1 from
@@ -216,7 +257,8 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
 
 // Algorithm 2's loop over sub-cubes [t, t_end) for the fast FP64 kernel.
 template <int D, int FID, int HK>
-__device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, uint32_t t, const uint32_t t_end,
+__device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, const PhiloxPre &ph, uint32_t t,
+                                                    const uint32_t t_end,
                                                     const double2 *tab, double *hist,
                                                     const unsigned long long *thr, const double *ftab,
                                                     ThreadSums &acc)
@@ -244,7 +286,7 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, uint
     for (; t < t_end; ++t) {
         if (!mc_check(P.chk, t, P.m, 3)) break;
         double S1 = 0.0, S2 = 0.0;
-        const PhiloxCube cube = philox_cube(t, P.ph);
+        const PhiloxCube cube = philox_cube(t, ph);
         for (uint32_t q = 0; q < p; ++q) {
             double s = s0, prod = 1.0, J = 1.0;
             long long sq = 0;   // fixed-point sum of the Q_k (kFixedQ)
@@ -252,7 +294,7 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, uint
             int kofs[D];
 #pragma unroll
             for (int j = 0; j < kCalls; ++j) {
-                const Words4 r = philox_draw(q, j, cube, P.ph);
+                const Words4 r = philox_draw(q, j, cube, ph);
                 const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -358,9 +400,70 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(con
     const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     ThreadSums acc;
-    sample_cubes_fast64<D, FID, HK>(P, t, t_end, tab, hist, thr, ftab, acc);
+    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
     const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
     finish_block<D, false, HK>(P, acc, hist, none, adjust, 1.0f, red_scratch);
+}
+
+// ------------------------------------------------------------------------------ batches
+// The batched form (the batch kernel's tiling: block b takes the contiguous tile range
+// [b n / B, (b+1) n / B) of one (d, family) class and switches job only at job boundaries) for
+// classes whose jobs all take the fast kernel. On each switch the block flushes the finished job's
+// sums and histogram, stages the next job's folded tables and prepares its Philox launch constants
+// (for this iteration) in shared memory. The shared-memory layout is the adjusting one in every
+// iteration; frozen iterations leave the histogram untouched. Each job's parameters carry its fold
+// (fast64_fold on the host).
+template <int D, int FID>
+__global__ void __launch_bounds__(kMaxBlockThreads, 1)
+    vsample_batch_fast64_kernel(const BatchJob *__restrict__ jobs, const BatchTile *__restrict__ tiles, int n_tiles,
+                                int iteration, int parity, int adjust, uint32_t perm_mul)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *tab = reinterpret_cast<double2 *>(smem_raw);
+    unsigned char *next = smem_raw + (size_t)D * kNB * 16;
+    double *hist = reinterpret_cast<double *>(next);
+    next += (size_t)D * kNB * 8;
+    unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
+    if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
+    double *ftab = reinterpret_cast<double *>(next);
+    __shared__ double red_scratch[64];
+    __shared__ PhiloxPre ph;
+
+    const int tb = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
+    const int te = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
+    const uint32_t r = (uint32_t)(((uint64_t)threadIdx.x * perm_mul) % blockDim.x);
+    const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
+
+    int cur = -1;
+    VsampleParams P;
+    ThreadSums acc;
+    for (int ti = tb; ti < te; ++ti) {
+        const BatchTile tile = tiles[ti];
+        if ((int)tile.job != cur) {
+            if (cur >= 0) {
+                finish_block<D, false, 1>(P, acc, hist, none, adjust != 0, 1.0f, red_scratch);
+                acc = ThreadSums();
+            }
+            cur = (int)tile.job;
+            const BatchJob &J = jobs[cur];
+            P = J.P;
+            P.grid = J.grid[parity];
+            P.C = J.C;
+            P.sums = J.sums + 2 * iteration;
+            P.prev = nullptr;
+            P.ctr2_hi = (uint32_t)iteration << 16;
+            P.adjust = adjust;
+            P.probe = nullptr;
+            if (threadIdx.x == 0) philox_prepare(ph, P.key0, P.key1, P.ctr2_hi, P.job);
+            stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);   // ends with a barrier
+        }
+        if (!mc_check(P.chk, (long long)tile.c1 - 1, P.m, 5) || !mc_check(P.chk, tile.c0, (long long)tile.c1, 5)) continue;
+        const uint32_t n = tile.c1 - tile.c0;
+        const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
+        const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
+        sample_cubes_fast64<D, FID, 1>(P, ph, t, t_end, tab, hist, thr, ftab, acc);
+    }
+    if (cur >= 0) finish_block<D, false, 1>(P, acc, hist, none, adjust != 0, 1.0f, red_scratch);
 }
 
 }  // namespace mcubes

@@ -120,41 +120,6 @@ int launch_hr(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
-// The fast FP64 kernel (vsample64.cuh) serves a Genz family when the strata fit its integer
-// c + u (g <= 2^11) and its per-axis fold factors are usable: every a_i finite and non-zero
-// (positive for C0, whose |a (x - u)| must equal a |x - u|) and the folded scale finite and
-// non-zero. The launch's copy of the parameters then carries the fold factors in ip.b, the scale
-// nd^d / prod(fold) (nd^d prod a for the product peak), and the fraction bits of the fixed-point
-// table sums: sum_i |fold_i| 2^fix_shift stays below 2^61.
-template <int FID>
-bool fast64_params(VsampleParams &Q, int d)
-{
-    if constexpr (kF32 || !Fast64<FID>::kOn) {
-        (void)Q; (void)d;
-        return false;
-    } else {
-        constexpr double kTwoPi = 6.283185307179586;
-        if (Q.g > 2048u) return false;
-        double scale = 1.0, fsum = 0.0;
-        for (int i = 0; i < d; ++i) {
-            const double a = Q.ip.a[i];
-            if (!std::isfinite(a) || a == 0.0 || (FID == kC0 && a < 0.0)) return false;
-            const double f = FID == kOscillatory ? a / kTwoPi : a;
-            if (!std::isfinite(f) || f == 0.0) return false;
-            Q.ip.b[i] = f;
-            fsum += std::fabs(f);
-            scale *= (double)kNB;
-            scale = FID == kProductPeak ? scale * f : scale / f;
-        }
-        if (!std::isfinite(scale) || scale == 0.0 || !(fsum < 1e15)) return false;
-        Q.fscale = scale;
-        int e = 0;
-        std::frexp(fsum * 1.0000001 + 1.0, &e);   // fsum + 1 < 2^e
-        Q.fix_shift = 61 - e;
-        return true;
-    }
-}
-
 template <int D, int HK>
 int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, bool &launched)
 {
@@ -164,7 +129,7 @@ int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, 
         return (int)cudaSuccess;
     } else {
         VsampleParams F = P;
-        if (!fast64_params<kFid>(F, D)) return (int)cudaSuccess;
+        if (!fast64_fold(kFid, F, D)) return (int)cudaSuccess;
         static InstanceInfo info;
         auto kern = vsample_fast64_kernel<D, kFid, HK>;
         constexpr size_t smem = fast64_smem_bytes<D, kFid, HK>();
@@ -245,6 +210,52 @@ int launch_batch_d(const BatchJob *jobs, const BatchTile *tiles, int n_tiles, in
     return (int)cudaGetLastError();
 }
 
+// The batched fast FP64 kernel (vsample64.cuh) of one (d, family) class whose jobs all carry the fold.
+template <int D>
+int launch_batch_fast_d(const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration, int parity,
+                        int adjust, const LaunchReq &req, cudaStream_t s)
+{
+    if constexpr (kF32 || !Fast64<kFid>::kOn) {
+        (void)jobs; (void)tiles; (void)n_tiles; (void)iteration; (void)parity; (void)adjust; (void)req; (void)s;
+        return (int)cudaErrorInvalidValue;
+    } else {
+        static InstanceInfo info;
+        auto kern = vsample_batch_fast64_kernel<D, kFid>;
+        constexpr size_t smem = fast64_smem_bytes<D, kFid, 1>();
+        if (smem > (size_t)227 * 1024) return (int)cudaErrorInvalidValue;
+        int occ = 1;
+        const int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
+        if (e != (int)cudaSuccess) return e;
+        const int threads = req.threads;
+        int bps = req.blocks_per_sm;
+        if (bps <= 0) {
+            bps = occ;
+            if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
+        }
+        int blocks = req.num_sms * bps;
+        if (blocks > n_tiles) blocks = n_tiles;
+        if (blocks < 1) return (int)cudaSuccess;
+        const uint32_t perm_mul = ((uint32_t)((double)threads * 0.6180339887498949)) | 1u;
+        kern<<<blocks, threads, smem, s>>>(jobs, tiles, n_tiles, iteration, parity, adjust, perm_mul);
+        return (int)cudaGetLastError();
+    }
+}
+
+int launch_batch_fast(int d, const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration, int parity,
+                      int adjust, const LaunchReq &req, cudaStream_t s)
+{
+    switch (d) {
+#define MCUBES_FAST_CASE(DD) \
+    case DD: return launch_batch_fast_d<DD>(jobs, tiles, n_tiles, iteration, parity, adjust, req, s);
+    MCUBES_FAST_CASE(1) MCUBES_FAST_CASE(2) MCUBES_FAST_CASE(3) MCUBES_FAST_CASE(4)
+    MCUBES_FAST_CASE(5) MCUBES_FAST_CASE(6) MCUBES_FAST_CASE(7) MCUBES_FAST_CASE(8)
+    MCUBES_FAST_CASE(9) MCUBES_FAST_CASE(10) MCUBES_FAST_CASE(11) MCUBES_FAST_CASE(12)
+    MCUBES_FAST_CASE(13) MCUBES_FAST_CASE(14) MCUBES_FAST_CASE(15) MCUBES_FAST_CASE(16)
+#undef MCUBES_FAST_CASE
+    default: return (int)cudaErrorInvalidValue;
+    }
+}
+
 template <bool kGlobalHist>
 int launch_batch(int d, const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration, int parity,
                  int adjust, const LaunchReq &req, cudaStream_t s)
@@ -268,6 +279,7 @@ int launch_batch(int d, const BatchJob *jobs, const BatchTile *tiles, int n_tile
 int MCUBES_BATCH_LAUNCHER(int d, const BatchJob *jobs, const BatchTile *tiles, int n_tiles, int iteration,
                           int parity, int adjust, int hist_mode, const LaunchReq &req, cudaStream_t s)
 {
+    if (hist_mode == 2) return launch_batch_fast(d, jobs, tiles, n_tiles, iteration, parity, adjust, req, s);
     return hist_mode == 1 ? launch_batch<true>(d, jobs, tiles, n_tiles, iteration, parity, adjust, req, s)
                           : launch_batch<false>(d, jobs, tiles, n_tiles, iteration, parity, adjust, req, s);
 }

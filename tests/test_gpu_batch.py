@@ -43,17 +43,20 @@ def _oracle_runs(jobs, itmax, adjust, mode):
             for k, j in enumerate(jobs)]
 
 
-@pytest.mark.parametrize("hist_mode", [0, 1])
-def test_batch_fp64_matches_oracle(capi, hist_mode):
+@pytest.mark.parametrize("hist_mode,plain", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_batch_fp64_matches_oracle(capi, hist_mode, plain):
+    """plain = 0: the Genz families' classes take the fast FP64 kernel (the others hist_mode's
+    plain kernel); plain = 1: every class the plain kernel with hist_mode's histogram."""
     jobs = _mixed_jobs()
     itmax, adjust = 4, 2
     tune = None
-    if hist_mode == 1:
+    if hist_mode == 1 or plain:
         tune = capi.BatchTuning()
+        tune.fp64_plain = plain
         for d in range(1, 17):
-            tune.block_threads[d] = 128
-            tune.cubes_per_thread[d] = 2
-            tune.hist_mode[d] = 1
+            tune.block_threads[d] = 128 if hist_mode == 1 else 256
+            tune.cubes_per_thread[d] = 2 if hist_mode == 1 else 4
+            tune.hist_mode[d] = hist_mode
     got = capi.integrate_batch(jobs, itmax, adjust, precision=0, tune=tune, return_iters=True)
     ref = _oracle_runs(jobs, itmax, adjust, 0)
     for k, (g, r) in enumerate(zip(got, ref)):
@@ -64,6 +67,28 @@ def test_batch_fp64_matches_oracle(capi, hist_mode):
         if jobs[k]["fid"] != W.CONSTANT:   # a constant's variance is pure rounding noise
             assert math.isclose(g["error"], sig, rel_tol=1e-8, abs_tol=1e-300), (k, g["error"], sig)
         assert np.allclose(g["iters"][:, 0], iI, rtol=1e-9, atol=1e-10 * max(np.abs(iI).max(), 1e-300)), k
+
+
+def test_batch_fast_class_falls_back_whole(capi):
+    """A (d, family) class takes the fast FP64 kernel only when every job of it can: one job with a
+    zero a_i (oscillatory) or a negative a_i (C0) sends its whole class to the plain kernel, while
+    the other classes keep the fast one. Every job still equals the oracle's run."""
+    d = 3
+    jobs = []
+    for k, fid in enumerate([W.OSCILLATORY, W.OSCILLATORY, W.C0, W.C0, W.GAUSSIAN, W.PRODUCT_PEAK]):
+        par = W.genz_params(fid, d, seed=40 + k)
+        if k == 1:
+            par[1] = 0.0
+        if k == 3:
+            par[0] = -par[0]
+        jobs.append(dict(fid=fid, d=d, ncall=30000 + 977 * k, params=par, seed=60 + k))
+    got = capi.integrate_batch(jobs, 3, 2, precision=0, return_iters=True)
+    ref = _oracle_runs(jobs, 3, 2, 0)
+    for k, (g, r) in enumerate(zip(got, ref)):
+        est, sig, chi2, iI, iV = r
+        assert g["status"] == 0
+        assert abs(g["estimate"] - est) <= 1e-10 * max(abs(est), sig), (k, g["estimate"], est)
+        assert math.isclose(g["error"], sig, rel_tol=1e-8), (k, g["error"], sig)
 
 
 def test_batch_fp32_matches_oracle(capi):
