@@ -496,7 +496,7 @@ void mcubes_shutdown(void);
 
 /* Unit rates of the current device, measured by microbenchmarks (about 50 ms): the per-SM
  * throughput of the operations the V-Sample kernels are built from, per SM clock at the
- * device's maximum SM clock (cudaDevAttrClockRate). out[0..min(n_out, 10) - 1] receives:
+ * device's maximum SM clock (cudaDevAttrClockRate). out[0..min(n_out, 12) - 1] receives:
  *   0: FP32 fused multiply-adds (lanes); 1: FP64 fused multiply-adds (lanes);
  *   2: exp2f (lanes); 3: Philox4x32-10 calls;
  *   4: random 8-byte shared-memory gathers from an 8 x 500 table (lanes);
@@ -505,7 +505,9 @@ void mcubes_shutdown(void);
  *      8 x 500 histogram, carry into a high word (lanes; one 1024-thread block an SM);
  *   7: random u64 shared reductions (no returned value) into one 8 x 500 histogram (lanes; one
  *      1024-thread block an SM); 8: the same into 4 lane-interleaved copies;
- *   9: random u32 shared reductions (no returned value) into 8 lane-interleaved copies.
+ *   9: random u32 shared reductions (no returned value) into 8 lane-interleaved copies;
+ *   10: random 8-byte read-only global gathers from an 8 x 500 table (L1-resident; lanes);
+ *   11: the same gathers, axes 0-3 from shared memory and 4-7 through L1 (lanes).
  * Errors: INVALID_ARG (NULL out, n_out < 1), ALLOC, CUDA. Synchronous. */
 int mcubes_unit_rates(double *out, int n_out);
 

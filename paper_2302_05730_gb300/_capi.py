@@ -525,7 +525,8 @@ def checked_violations(reset: bool = True):
 
 UNIT_RATE_NAMES = ("ffma_lanes", "dfma_lanes", "exp2f_lanes", "philox_calls", "shared_gather8_lanes",
                    "shared_atomic_f32_lanes", "shared_atomic_u32x8_lanes", "shared_red_u64_lanes",
-                   "shared_red_u64x4_lanes", "shared_red_u32x8_lanes")
+                   "shared_red_u64x4_lanes", "shared_red_u32x8_lanes", "l1_gather8_lanes",
+                   "mixed_gather8_lanes")
 
 
 def unit_rates() -> dict:

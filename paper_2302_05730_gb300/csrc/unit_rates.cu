@@ -20,7 +20,7 @@ constexpr int kIters = 512;
 constexpr int kThreads = 256;
 constexpr int kBins = 500;    // bins per axis, as the histogram
 constexpr int kAxes = 8;
-constexpr int kUnitRates = 10;
+constexpr int kUnitRates = 12;
 
 __device__ __forceinline__ uint32_t lcg(uint32_t s) { return s * 1664525u + 1013904223u; }
 // a bin index in [0, kBins) from the top 16 bits of a 32-bit state
@@ -96,6 +96,36 @@ __global__ void k_gather(float *out, uint32_t seed)
         }
     }
     out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// the same gathers through the L1 data cache (read-only global loads of an 8 x 500 table), and a
+// mix: axes 0-3 from shared memory, axes 4-7 through L1
+template <bool kMix>
+__global__ void k_gather_l1(float *out, const float2 *__restrict__ gtab, uint32_t seed)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2 *tab = reinterpret_cast<float2 *>(sm);
+    if (kMix)
+        for (int e = threadIdx.x; e < kAxes * kBins; e += blockDim.x) tab[e] = make_float2(e * 1e-4f, 1.0f + e * 1e-7f);
+    __syncthreads();
+    uint32_t s = seed ^ (threadIdx.x * 0x9E3779B9u) ^ (blockIdx.x * 0x85EBCA6Bu);
+    float acc = 0.f;
+    for (int it = 0; it < kIters / 8; ++it) {
+#pragma unroll
+        for (int i = 0; i < kAxes; ++i) {
+            s = lcg(s);
+            const int e = i * kBins + bin_of(s);
+            const float2 v = (kMix && i < kAxes / 2) ? tab[e] : __ldg(&gtab[e]);
+            acc = fmaf(acc, v.y, v.x);
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+__global__ void k_fill_table(float2 *gtab)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < kAxes * kBins) gtab[e] = make_float2(e * 1e-4f, 1.0f + e * 1e-7f);
 }
 
 // random FP32 shared atomics into one d x 500 histogram
@@ -254,8 +284,10 @@ extern "C" int mcubes_unit_rates(double *out, int n_out)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_red_u32x8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r32_bytes);
     if (e != cudaSuccess) return cuda_status(e);
     float *buf = nullptr;
-    e = mc_malloc((void **)&buf, sizeof(float) * (size_t)sms * 4 * kThreads);
+    e = mc_malloc((void **)&buf, sizeof(float) * (size_t)sms * 4 * kThreads + tab_bytes);
     if (e != cudaSuccess) return cuda_status(e);
+    float2 *gtab = reinterpret_cast<float2 *>(buf + (size_t)sms * 4 * kThreads);   // 16-byte aligned
+    k_fill_table<<<(kAxes * kBins + 255) / 256, 256>>>(gtab);
     int st = MCUBES_OK;
     double r[kUnitRates] = {};
     const Probe alu{kThreads, 4, 0, 8.0 * kIters};
@@ -285,6 +317,12 @@ extern "C" int mcubes_unit_rates(double *out, int n_out)
     if (!st)
         r[9] = time_probe(Probe{4 * kThreads, 1, r32_bytes, 1.0 * kIters}, sms, clk, buf,
                           [](unsigned b, int t, size_t m, float *o) { k_red_u32x8<<<b, t, m>>>(o, 7u); }, st);
+    if (!st)
+        r[10] = time_probe(Probe{kThreads, 4, 0, 1.0 * kIters}, sms, clk, buf,
+                           [gtab](unsigned b, int t, size_t m, float *o) { k_gather_l1<false><<<b, t, m>>>(o, gtab, 7u); }, st);
+    if (!st)
+        r[11] = time_probe(Probe{kThreads, 4, tab_bytes, 1.0 * kIters}, sms, clk, buf,
+                           [gtab](unsigned b, int t, size_t m, float *o) { k_gather_l1<true><<<b, t, m>>>(o, gtab, 7u); }, st);
     cudaFree(buf);
     if (st) return st;
     for (int i = 0; i < n_out && i < kUnitRates; ++i) out[i] = r[i];
