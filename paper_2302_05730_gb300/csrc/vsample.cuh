@@ -71,30 +71,38 @@ __host__ __device__ constexpr size_t vsample_smem_bytes(int d, int hr)
 // The fixed-point histogram of the FP32 adjusting kernel (HK = 2).
 //
 // A contribution h (FP32, >= 0) becomes v = h q with q = 2^e a power of two chosen per block, so
-// the product is exact. Zero contributions add nothing. When 2^14 <= v < vmax = 2^ih_vmax_exp (at
-// most 2^44) it is rounded to a 64-bit integer (exact above 2^23, within 2^-15 relative below) and
-// added to the bin with native u32 shared atomics:
+// the product is exact. When v < vmax = 2^ih_vmax_exp (at most 2^44) it is rounded to a whole
+// number of units (exact from 2^23 units up, within half a unit below) and added to the bin with
+// native u32 shared atomics:
 //   - the low word to one of R lane-interleaved copies (copy g = lane mod R holds bin e at word
-//     e R + g, so only the 32 / R lanes of a copy can meet in a bank);
-//   - the high word, plus 1 when the low add wrapped (detected from the atomic's old value), to a
-//     single high word per bin.
-// Other contributions (below 2^14 or from vmax up, infinite or NaN) go to an FP32 side copy with
-// FP32 shared atomics. Every bin therefore keeps a relative precision of 2^-15 or better, whatever
-// the scale. The host sets vmax so that a block's samples times vmax stays below 2^63: no bin's
-// sum can overflow. The flush adds (low copies + 2^32 high) / q + side into the FP64 C.
+//     e R + g, so only the 32 / R lanes of a copy can meet in a bank). Each add returns the old
+//     word; the carry out of old + low word is shifted into a per-sample carry mask;
+//   - the high word, plus 1 for each carry, to a single high word per bin, in one branch a sample
+//     that runs only when the sample has a high word or a carry (rare: see the scale below).
+// Contributions rounding to zero units add nothing. The rest (from vmax up, infinite or NaN) go to
+// an FP32 side copy with FP32 shared atomics. The host sets vmax so that a block's samples times
+// vmax stays below 2^63: no bin's sum can overflow. The flush adds (low copies + 2^32 high) / q +
+// side into the FP64 C.
 //
 // Why: an FP32 shared atomic costs about four times a u32 one under random bins (it reads the
 // word, adds and compares-and-swaps), and the histogram's atomics bound adjusting iterations.
 //
-// The scale only decides which path a contribution takes. It comes from a pilot, each thread's
-// first sample: with P+ the pilot's fraction of positive contributions and g+ their geometric
-// mean, q = 2^28 P+ / g+ (exponent rounded), which puts the typical positive contribution near the
-// middle of the 29 octaves the integer path covers (weighting by P+ keeps the block's mean
-// contribution there for sparse integrands). A block whose pilot has no positive contribution
-// sends every contribution to the side copy.
+// The scale comes from a pilot, each thread's first sample: q puts the pilot's arithmetic mean
+// contribution at 2^20 units, or higher where needed to put the block's expected mean bin (its
+// samples times that mean over the 500 bins) at 2^30 units (exponent rounded down). The mean, not
+// a typical size, is what fixes a bin's sum, so:
+//   - at the sizes where speed matters (many samples a bin) the unit is 2^-20 of the mean: the low
+//     words wrap, and the high words are touched, about once per 2^12 adds of a mean-sized
+//     contribution, and a contribution reaches the high word (2^32 units) or vmax only at 2^12 or
+//     2^23 times the mean: by Markov's inequality a small fraction of the samples;
+//   - a contribution rounds with an error of half a unit at most, so a block's error in any bin is
+//     at most half a unit per contribution against an expected mean bin of 2^30 units or more; a
+//     contribution of the mean's size keeps 2^-21 relative precision or better.
+// A block whose pilot has no positive finite contribution sends every contribution to the side
+// copy.
 constexpr int kReplThreads = 1024;
-constexpr float kIntHistLo = 16384.0f;             // 2^14: smallest contribution (units) on the integer path
-constexpr double kIntHistCentre = 28.0;            // log2 of the scaled P+-weighted pilot mean
+constexpr double kIntHistCentre = 20.0;            // log2 of the pilot's mean contribution, in units (at least)
+constexpr double kIntHistBinSum = 30.0;            // log2 of a block's expected mean bin, in units (at least)
 template <int D>
 __host__ __device__ constexpr size_t int_hist_smem_bytes(int r)
 {
@@ -167,31 +175,65 @@ __device__ __forceinline__ uint32_t atom_add_u32(uint32_t a, uint32_t v)
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v));
     return old;
 }
-// The high-word update of a fixed-point bin: c = hi + the carry out of old + lo (add with
-// carry-out, add with carry-in), added to the high word at `a` when non-zero. One predicated
-// reduction, no branch.
-__device__ __forceinline__ void add_high(uint32_t a, uint32_t old, uint32_t lo, uint32_t hi)
+__device__ __forceinline__ void red_add_u32(uint32_t a, uint32_t v)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .u32 s, c;\n\t"
-        "add.cc.u32 s, %1, %2;\n\t"
-        "addc.u32 c, %3, 0;\n\t"
-        "setp.ne.u32 p, c, 0;\n\t"
-        "@p red.shared.add.u32 [%0], c;\n\t}" ::"r"(a), "r"(old), "r"(lo), "r"(hi)
-        : "memory");
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
 }
-// round(v) for a float 2^14 <= v < 2^44, from its bits with integer operations (a 64-bit float
-// conversion would run on the FP64 pipe): v = M 2^s with the 24-bit significand M and
-// s = exponent - 23 in [-9, 20]; halves round up.
-__device__ __forceinline__ unsigned long long round_to_u64(float v)
+// mask * 2 + the carry out of old + lo (add with carry-out, then add the mask to itself with the
+// carry in): collects a sample's low-word carries, one bit an axis.
+__device__ __forceinline__ uint32_t carry_in(uint32_t mask, uint32_t old, uint32_t lo)
+{
+    uint32_t m;
+    asm("{\n\t.reg .u32 s;\n\tadd.cc.u32 s, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}" : "=r"(m) : "r"(old), "r"(lo), "r"(mask));
+    return m;
+}
+// round(v) for a float 0 <= v < 2^44 as a 64-bit integer (lo, hi), with integer operations (a
+// 64-bit float conversion would run on the FP64 pipe). Below 2^23, v + 2^23 rounds v to an integer
+// (to nearest, ties to even) and its bit pattern is 0x4B000000 + round(v). From 2^23 up, v is the
+// integer M 2^s with its 24-bit significand M and s = exponent - 23 in [0, 20].
+__device__ __forceinline__ void round_units(float v, uint32_t &lo, uint32_t &hi)
 {
     const uint32_t b = __float_as_uint(v);
     const uint32_t M = (b & 0x7FFFFFu) | 0x800000u;
-    const int s = (int)(b >> 23) - 150;
-    return s >= 0 ? (unsigned long long)M << s : (unsigned long long)((M + (1u << (-s - 1))) >> -s);
+    const uint32_t s = (b >> 23) - 150u;
+    const uint32_t small = __float_as_uint(__fadd_rn(v, 8388608.0f)) - 0x4B000000u;
+    const bool big = v >= 8388608.0f;
+    lo = big ? M << (s & 31u) : small;
+    hi = big ? __funnelshift_l(M, 0u, s) : 0u;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// One sample's contribution h to the fixed-point histogram (HK = 2) on its d bins; kbb[i] is the bit
+// pattern 0x4B000000 + k_i of axis i's floored coordinate, the adj values the shared-window offsets
+// that turn it into this lane's low word, the bin's high word and its side word.
+template <int D>
+__device__ __forceinline__ void fixed_hist_add(const float h, const uint32_t (&kbb)[D], const IntHist &ih,
+                                               const uint32_t lo_adj, const uint32_t hi_adj, const uint32_t side_adj)
+{
+    constexpr int kR = int_hist_copies<D>();
+    const float vf = h * ih.q;   // exact: q is a power of two
+    if (vf < ih.vmax) {
+        uint32_t vlo, vhi;
+        round_units(vf, vlo, vhi);
+        if ((vlo | vhi) != 0u) {
+            uint32_t carries = 0u;   // axis i's carry in bit D - 1 - i
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                const uint32_t old = atom_add_u32(kbb[i] * (4u * kR) + (lo_adj + (uint32_t)(i * kNB * 4 * kR)), vlo);
+                carries = carry_in(carries, old, vlo);
+            }
+            if ((carries | vhi) != 0u) {
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    red_add_u32(kbb[i] * 4u + (hi_adj + (uint32_t)(i * kNB * 4)), vhi + ((carries >> (D - 1 - i)) & 1u));
+            }
+        }
+    } else if (h != 0.0f) {   // from vmax up, infinite or NaN
+#pragma unroll
+        for (int i = 0; i < D; ++i) red_add_f32(kbb[i] * 4u + (side_adj + (uint32_t)(i * kNB * 4)), h);
+    }
+}
 
 // Resident blocks per SM the FP32-eval kernels are compiled for (register budget 65536 /
 // (256 x blocks)): for the frozen and batched kernels, as many 256-thread blocks as the shared
@@ -471,19 +513,7 @@ __device__ __forceinline__ float sample_cubes(const VsampleParams &P, uint32_t t
                         for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], h);
                     }
                 } else if constexpr (HK == 2) {
-                    const float vf = h * ih.q;   // exact: q is a power of two
-                    if (vf >= kIntHistLo && vf < ih.vmax) {
-                        const unsigned long long v = round_to_u64(vf);
-                        const uint32_t vlo = (uint32_t)v, vhi = (uint32_t)(v >> 32);
-#pragma unroll
-                        for (int i = 0; i < D; ++i) {
-                            const uint32_t old = atom_add_u32(kbb[i] * (4u * kR) + (lo_adj + (uint32_t)(i * kNB * 4 * kR)), vlo);
-                            add_high(kbb[i] * 4u + (hi_adj + (uint32_t)(i * kNB * 4)), old, vlo, vhi);
-                        }
-                    } else if (h != 0.0f) {   // outside the range, infinite or NaN
-#pragma unroll
-                        for (int i = 0; i < D; ++i) red_add_f32(kbb[i] * 4u + (side_adj + (uint32_t)(i * kNB * 4)), h);
-                    }
+                    fixed_hist_add<D>(h, kbb, ih, lo_adj, hi_adj, side_adj);
                 }
             }
         }
@@ -643,25 +673,28 @@ __global__ void __launch_bounds__((HK == 2 ? kReplThreads : kMaxBlockThreads), (
         ih.side = ih.hi + 4u * (uint32_t)(D * kNB);
         ih.vmax = ldexpf(1.0f, P.ih_vmax_exp);
         if (adjust) {
-            // pilot: the threads' first contributions (their count, the positive ones' count and
-            // the positive ones' mean log2)
-            double lg = 0.0, npos = 0.0, nall = t < t_end ? 1.0 : 0.0;
+            // pilot: the threads' first contributions (the sum of the finite ones and their count),
+            // and the block's sample count
+            double hsum = 0.0, nfin = 0.0;
             if (t < t_end) {
                 const float hp = sample_cubes<D, FID, F32, false, HK, true, true>(P, t, t + 1, tab, hist, ih, hsig, acc);
-                if (hp > 0.0f && hp <= 3.0e38f) {
-                    lg = (double)log2f(fmaxf(hp, 1.17549435e-38f));
-                    npos = 1.0;
+                if (hp <= 3.0e38f) {   // finite (NaN compares false)
+                    hsum = (double)hp;
+                    nfin = 1.0;
                 }
             }
-            block_sum2(lg, npos, red_scratch);
-            double nall_sum = nall, unused = 0.0;
+            block_sum2(hsum, nfin, red_scratch);
+            double nsamp = (double)(t_end - t) * (double)P.p, unused = 0.0;
             __syncthreads();   // red_scratch is reused
-            block_sum2(nall_sum, unused, red_scratch);
+            block_sum2(nsamp, unused, red_scratch);
             if (threadIdx.x == 0) {
                 float q = 1.0f, vmax = 0.0f;   // no positive pilot contribution: all to the side copy
-                if (npos > 0.0 && nall_sum > 0.0) {
-                    const double e = kIntHistCentre + log2(npos / nall_sum) - lg / npos;
-                    q = ldexpf(1.0f, (int)rint(fmin(fmax(e, -120.0), 120.0)));
+                if (hsum > 0.0 && nfin > 0.0 && nsamp > 0.0) {
+                    // the pilot's mean at 2^kIntHistCentre units or more, and the block's expected
+                    // mean bin (samples x pilot mean / kNB) at 2^kIntHistBinSum units or more
+                    const double lg = fmax(kIntHistCentre, kIntHistBinSum + log2((double)kNB / nsamp));
+                    const double e = floor(lg - log2(hsum / nfin));
+                    q = ldexpf(1.0f, (int)fmin(fmax(e, -120.0), 120.0));
                     vmax = ih.vmax;
                 }
                 pilot_q = q;
