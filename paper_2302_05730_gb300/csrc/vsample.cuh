@@ -175,6 +175,11 @@ __device__ __forceinline__ uint32_t atom_add_u32(uint32_t a, uint32_t v)
     asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v));
     return old;
 }
+// FP64 add into global memory with no returned value (performed by the L2).
+__device__ __forceinline__ void red_add_f64_global(double *a, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(a), "d"(v) : "memory");
+}
 __device__ __forceinline__ void red_add_u32(uint32_t a, uint32_t v)
 {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));

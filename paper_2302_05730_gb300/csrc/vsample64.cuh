@@ -22,8 +22,9 @@
 //     their reduced arguments' Taylor series to 2^-54 (no library constants or steps);
 //   - the discontinuous family's cut x_i < u_i is decided exactly as defined, by one integer
 //     comparison of the offset's bits with a per-bin threshold the block finds by bisection.
-// The per-cube statistics, the reduction and the bin contributions are the FP64 kernel's own
-// (vsample.cuh): finish_block, the FP64 shared histogram.
+// The per-cube statistics and the reduction are the FP64 kernel's own (vsample.cuh: finish_block).
+// Bin contributions: native FP64 reductions into the global C (single-job kernel), or the FP64
+// shared histogram (batched kernel).
 #pragma once
 
 #include <cmath>
@@ -111,6 +112,14 @@ __host__ __device__ constexpr size_t fast64_smem_bytes()
 {
     return (size_t)D * kNB * (16 + (HK == 1 ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
            (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
+}
+
+// Shared-memory bytes of one single-job fast FP64 block (either kind: adjusting launches reduce
+// into the global C and hold no histogram copy).
+template <int D, int FID>
+__host__ __device__ constexpr size_t fast64_single_smem_bytes()
+{
+    return fast64_smem_bytes<D, FID, 0>();
 }
 
 // The same at a run-time d and family (0..5), for host-side eligibility checks; 0 for other families.
@@ -256,7 +265,7 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
 }
 
 // Algorithm 2's loop over sub-cubes [t, t_end) for the fast FP64 kernel.
-template <int D, int FID, int HK>
+template <int D, int FID, int HK, bool kGlobalC = false>
 __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, const PhiloxPre &ph, uint32_t t,
                                                     const uint32_t t_end,
                                                     const double2 *tab, double *hist,
@@ -346,8 +355,13 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
             if (adjust) {
                 const double wf = w * P.fscale;
                 const double hv = wf * wf;
+                if constexpr (kGlobalC) {
 #pragma unroll
-                for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], hv);
+                    for (int i = 0; i < D; ++i) red_add_f64_global(&P.C[kofs[i]], hv);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], hv);
+                }
             }
         }
         const bool probe_this = P.probe != nullptr && (t & P.probe_mask) == 0 &&
@@ -376,22 +390,23 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
     }
 }
 
-// One job, persistent grid; HK = 0 frozen, HK = 1 adjusting (FP64 shared histogram).
+// One job, persistent grid; HK = 0 frozen, HK = 1 adjusting. Adjusting launches add each sample's
+// contribution on its d bins straight into the job's FP64 C with native FP64 reductions, which the
+// L2 performs: the adds leave the SM's FP64 pipe (the kernel's bound), and no block holds or flushes
+// a shared copy. (A shared FP64 atomic is a compare-and-swap loop around an FP64 add on the SM.)
 template <int D, int FID, int HK>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(const VsampleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
-    double *hist = reinterpret_cast<double *>(next);
-    if constexpr (HK == 1) next += (size_t)D * kNB * 8;
+    double *hist = nullptr;
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
     __shared__ double red_scratch[64];
 
-    const bool adjust = HK == 1 && P.adjust != 0;
-    stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);
+    stage_fast64<D, FID>(P, tab, hist, 0, thr, ftab);
 
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -400,9 +415,9 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(con
     const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     ThreadSums acc;
-    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
+    sample_cubes_fast64<D, FID, HK, true>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
     const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
-    finish_block<D, false, HK>(P, acc, hist, none, adjust, 1.0f, red_scratch);
+    finish_block<D, false, HK>(P, acc, hist, none, false, 1.0f, red_scratch);
 }
 
 // ------------------------------------------------------------------------------ batches
