@@ -23,8 +23,8 @@
 //   - the discontinuous family's cut x_i < u_i is decided exactly as defined, by one integer
 //     comparison of the offset's bits with a per-bin threshold the block finds by bisection.
 // The per-cube statistics and the reduction are the FP64 kernel's own (vsample.cuh: finish_block).
-// Bin contributions: native FP64 reductions into the global C (single-job kernel), or the FP64
-// shared histogram (batched kernel).
+// Bin contributions: native FP64 reductions straight into the global C (both kernels below), the
+// subnormal ones through a shared FP64 copy.
 #pragma once
 
 #include <cmath>
@@ -105,21 +105,13 @@ inline bool fast64_fold(int fid, VsampleParams &Q, int d)
     return true;
 }
 
-// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the FP64 histogram copy when
-// adjusting, the cut thresholds, and the exp or cos table.
+// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the FP64 copy of the bin
+// contributions that holds the subnormal ones (HK = 1), the cut thresholds, and the exp or cos table.
 template <int D, int FID, int HK>
 __host__ __device__ constexpr size_t fast64_smem_bytes()
 {
     return (size_t)D * kNB * (16 + (HK == 1 ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
            (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
-}
-
-// Shared-memory bytes of one single-job fast FP64 block (either kind: adjusting launches reduce
-// into the global C and hold no histogram copy).
-template <int D, int FID>
-__host__ __device__ constexpr size_t fast64_single_smem_bytes()
-{
-    return fast64_smem_bytes<D, FID, 0>();
 }
 
 // The same at a run-time d and family (0..5), for host-side eligibility checks; 0 for other families.
@@ -196,7 +188,8 @@ __device__ __forceinline__ int split_bin(unsigned long long yb, unsigned long lo
 }
 
 // Stage the fast kernel's tables: per axis and bin (P, Q) (see the header), the discontinuous
-// family's cut thresholds, and the exp or cos table; clear the histogram copy. Block-wide.
+// family's cut thresholds, and the exp or cos table; clear n_hist words of the histogram copy.
+// Block-wide.
 template <int D, int FID>
 __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *tab, double *hist, int n_hist,
                                              unsigned long long *thr, double *ftab)
@@ -265,7 +258,7 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
 }
 
 // Algorithm 2's loop over sub-cubes [t, t_end) for the fast FP64 kernel.
-template <int D, int FID, int HK, bool kGlobalC = false>
+template <int D, int FID, int HK>
 __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, const PhiloxPre &ph, uint32_t t,
                                                     const uint32_t t_end,
                                                     const double2 *tab, double *hist,
@@ -355,10 +348,14 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
             if (adjust) {
                 const double wf = w * P.fscale;
                 const double hv = wf * wf;
-                if constexpr (kGlobalC) {
+                // Normal (and non-finite) contributions: native FP64 reductions into the global C, which
+                // the L2 performs. Subnormal ones (below 2^-1022; a peaked integrand's early iterations
+                // underflow often): the block's shared copy, whose adds run on the SM (the L2 takes a slow
+                // path on subnormal operands). Zeros add nothing.
+                if (!(hv < 0x1p-1022)) {
 #pragma unroll
                     for (int i = 0; i < D; ++i) red_add_f64_global(&P.C[kofs[i]], hv);
-                } else {
+                } else if (hv != 0.0) {
 #pragma unroll
                     for (int i = 0; i < D; ++i) atomicAdd(&hist[kofs[i]], hv);
                 }
@@ -392,21 +389,24 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
 
 // One job, persistent grid; HK = 0 frozen, HK = 1 adjusting. Adjusting launches add each sample's
 // contribution on its d bins straight into the job's FP64 C with native FP64 reductions, which the
-// L2 performs: the adds leave the SM's FP64 pipe (the kernel's bound), and no block holds or flushes
-// a shared copy. (A shared FP64 atomic is a compare-and-swap loop around an FP64 add on the SM.)
+// L2 performs, so the adds leave the SM's FP64 pipe (the kernel's bound); a shared FP64 atomic is a
+// compare-and-swap loop around an FP64 add on the SM. Only subnormal contributions go to the block's
+// shared copy, flushed into C at the end.
 template <int D, int FID, int HK>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(const VsampleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
-    double *hist = nullptr;
+    double *hist = reinterpret_cast<double *>(next);
+    if constexpr (HK == 1) next += (size_t)D * kNB * 8;
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
     __shared__ double red_scratch[64];
 
-    stage_fast64<D, FID>(P, tab, hist, 0, thr, ftab);
+    const bool adjust = HK == 1 && P.adjust != 0;
+    stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);
 
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -415,19 +415,19 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(con
     const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     ThreadSums acc;
-    sample_cubes_fast64<D, FID, HK, true>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
+    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
     const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
-    finish_block<D, false, HK>(P, acc, hist, none, false, 1.0f, red_scratch);
+    finish_block<D, false, HK>(P, acc, hist, none, adjust, 1.0f, red_scratch);
 }
 
 // ------------------------------------------------------------------------------ batches
 // The batched form (the batch kernel's tiling: block b takes the contiguous tile range
 // [b n / B, (b+1) n / B) of one (d, family) class and switches job only at job boundaries) for
 // classes whose jobs all take the fast kernel. On each switch the block flushes the finished job's
-// sums and histogram, stages the next job's folded tables and prepares its Philox launch constants
-// (for this iteration) in shared memory. The shared-memory layout is the adjusting one in every
-// iteration; frozen iterations leave the histogram untouched. Each job's parameters carry its fold
-// (fast64_fold on the host).
+// sums and shared copy, stages the next job's folded tables and prepares its Philox launch constants
+// (for this iteration) in shared memory. Adjusting iterations add the bin contributions straight into
+// each job's global C with native FP64 reductions, as the single-job kernel does. Each job's
+// parameters carry its fold (fast64_fold on the host).
 template <int D, int FID>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1)
     vsample_batch_fast64_kernel(const BatchJob *__restrict__ jobs, const BatchTile *__restrict__ tiles, int n_tiles,

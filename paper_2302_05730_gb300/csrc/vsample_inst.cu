@@ -132,7 +132,7 @@ int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, 
         if (!fast64_fold(kFid, F, D)) return (int)cudaSuccess;
         static InstanceInfo info;
         auto kern = vsample_fast64_kernel<D, kFid, HK>;
-        constexpr size_t smem = fast64_single_smem_bytes<D, kFid>();
+        constexpr size_t smem = fast64_smem_bytes<D, kFid, HK>();
         if (smem > (size_t)227 * 1024) return (int)cudaSuccess;
         int occ = 1;
         int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
