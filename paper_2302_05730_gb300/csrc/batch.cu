@@ -156,7 +156,7 @@ struct Plan {
                 const std::pair<int, int> key{pb[j].d, pb[j].fid};
                 VsampleParams Q = pb[j].P;
                 const bool ok = fast64_fold(pb[j].fid, Q, pb[j].d) &&
-                                fast64_smem_bytes_rt(pb[j].d, pb[j].fid) <= (size_t)227 * 1024;
+                                fast64_smem_bytes_rt(pb[j].d, pb[j].fid, 1) <= (size_t)227 * 1024;
                 auto it = fast.find(key);
                 fast[key] = (it == fast.end() ? true : it->second) && ok;
             }

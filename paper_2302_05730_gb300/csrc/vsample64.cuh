@@ -23,7 +23,8 @@
 //   - the discontinuous family's cut x_i < u_i is decided exactly as defined, by one integer
 //     comparison of the offset's bits with a per-bin threshold the block finds by bisection.
 // The per-cube statistics and the reduction are the FP64 kernel's own (vsample.cuh: finish_block).
-// Bin contributions: native FP64 reductions straight into the global C (both kernels below).
+// Bin contributions (both kernels below): each sample's first (d + 1) / 2 axes go straight to the
+// global C with native FP64 reductions, the rest to the block's shared FP64 copy, flushed into C.
 #pragma once
 
 #include <cmath>
@@ -104,22 +105,22 @@ inline bool fast64_fold(int fid, VsampleParams &Q, int d)
     return true;
 }
 
-// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the cut thresholds, and the exp or
-// cos table (bin contributions go straight to the global C).
-template <int D, int FID>
+// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the FP64 copy of the bin
+// contributions (HK = 1), the cut thresholds, and the exp or cos table.
+template <int D, int FID, int HK>
 __host__ __device__ constexpr size_t fast64_smem_bytes()
 {
-    return (size_t)D * kNB * (16 + (Fast64<FID>::kCut ? 8 : 0)) + (Fast64<FID>::kExp ? kExpTab * 8 : 0) +
-           (Fast64<FID>::kCos ? kCosTab * 16 : 0);
+    return (size_t)D * kNB * (16 + (HK == 1 ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
+           (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
 }
 
 // The same at a run-time d and family (0..5), for host-side eligibility checks; 0 for other families.
-inline size_t fast64_smem_bytes_rt(int d, int fid)
+inline size_t fast64_smem_bytes_rt(int d, int fid, int hk)
 {
     const bool cut = fid == kDiscontinuous, ex = fid == kGaussian || fid == kC0 || fid == kDiscontinuous,
                co = fid == kOscillatory;
     if (fid < 0 || fid > 5) return 0;
-    return (size_t)d * kNB * (16 + (cut ? 8 : 0)) + (ex ? kExpTab * 8 : 0) + (co ? kCosTab * 16 : 0);
+    return (size_t)d * kNB * (16 + (hk == 1 ? 8 : 0) + (cut ? 8 : 0)) + (ex ? kExpTab * 8 : 0) + (co ? kCosTab * 16 : 0);
 }
 
 // exp(x): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(x) = 2^m 2^(j/64) e^r; e^r - 1 from
@@ -187,10 +188,11 @@ __device__ __forceinline__ int split_bin(unsigned long long yb, unsigned long lo
 }
 
 // Stage the fast kernel's tables: per axis and bin (P, Q) (see the header), the discontinuous
-// family's cut thresholds, and the exp or cos table. Block-wide.
+// family's cut thresholds, and the exp or cos table; clear n_hist words of the histogram copy.
+// Block-wide.
 template <int D, int FID>
-__device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *tab, unsigned long long *thr,
-                                             double *ftab)
+__device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *tab, double *hist, int n_hist,
+                                             unsigned long long *thr, double *ftab)
 {
     const IntegrandParams &ip = P.ip;
     for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
@@ -251,6 +253,7 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
             cs[j] = make_double2(c, s);
         }
     }
+    for (int e = threadIdx.x; e < n_hist; e += blockDim.x) hist[e] = 0.0;
     __syncthreads();
 }
 
@@ -258,7 +261,7 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
 template <int D, int FID, int HK>
 __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, const PhiloxPre &ph, uint32_t t,
                                                     const uint32_t t_end,
-                                                    const double2 *tab,
+                                                    const double2 *tab, double *hist,
                                                     const unsigned long long *thr, const double *ftab,
                                                     ThreadSums &acc)
 {
@@ -345,10 +348,16 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
             if (adjust) {
                 const double wf = w * P.fscale;
                 const double hv = wf * wf;
-                // native FP64 reductions into the global C, which the L2 performs; a zero adds nothing
+                // The first kL2 axes: native FP64 reductions into the global C, which the L2 performs, off
+                // the FP64 pipe. The rest: the block's shared copy, whose atomics are compare-and-swap loops
+                // around an FP64 add on the SM. Half and half keeps the launch time the same wherever C lies
+                // (the L2's reduction rate into C depends on its physical placement). A zero adds nothing.
                 if (hv != 0.0) {
+                    constexpr int kL2 = (D + 1) / 2;
 #pragma unroll
-                    for (int i = 0; i < D; ++i) red_add_f64_global(&P.C[kofs[i]], hv);
+                    for (int i = 0; i < kL2; ++i) red_add_f64_global(&P.C[kofs[i]], hv);
+#pragma unroll
+                    for (int i = kL2; i < D; ++i) atomicAdd(&hist[kofs[i]], hv);
                 }
             }
         }
@@ -379,21 +388,24 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
 }
 
 // One job, persistent grid; HK = 0 frozen, HK = 1 adjusting. Adjusting launches add each sample's
-// contribution on its d bins straight into the job's FP64 C with native FP64 reductions, which the
-// L2 performs, so the adds leave the SM's FP64 pipe (the kernel's bound); a shared FP64 atomic is a
-// compare-and-swap loop around an FP64 add on the SM. No block holds a copy of C.
+// contribution on half its axes straight into the job's FP64 C with native FP64 reductions, which the
+// L2 performs (off the FP64 pipe, the kernel's bound), and on the other half into the block's shared
+// FP64 copy, flushed into C at the end.
 template <int D, int FID, int HK>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(const VsampleParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
+    double *hist = reinterpret_cast<double *>(next);
+    if constexpr (HK == 1) next += (size_t)D * kNB * 8;
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
     __shared__ double red_scratch[64];
 
-    stage_fast64<D, FID>(P, tab, thr, ftab);
+    const bool adjust = HK == 1 && P.adjust != 0;
+    stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);
 
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -402,19 +414,19 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(con
     const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     ThreadSums acc;
-    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, thr, ftab, acc);
+    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
     const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
-    finish_block<D, false, HK>(P, acc, nullptr, none, false, 1.0f, red_scratch);
+    finish_block<D, false, HK>(P, acc, hist, none, adjust, 1.0f, red_scratch);
 }
 
 // ------------------------------------------------------------------------------ batches
 // The batched form (the batch kernel's tiling: block b takes the contiguous tile range
 // [b n / B, (b+1) n / B) of one (d, family) class and switches job only at job boundaries) for
-// classes whose jobs all take the fast kernel. On each switch the block adds the finished job's
-// sums, stages the next job's folded tables and prepares its Philox launch constants
-// (for this iteration) in shared memory. Adjusting iterations add the bin contributions straight into
-// each job's global C with native FP64 reductions, as the single-job kernel does. Each job's
-// parameters carry its fold (fast64_fold on the host).
+// classes whose jobs all take the fast kernel. On each switch the block flushes the finished job's
+// sums and shared copy, stages the next job's folded tables and prepares its Philox launch constants
+// (for this iteration) in shared memory. Adjusting iterations route the bin contributions as the
+// single-job kernel does: half the axes to each job's global C with native FP64 reductions, half to
+// the shared copy. Each job's parameters carry its fold (fast64_fold on the host).
 template <int D, int FID>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1)
     vsample_batch_fast64_kernel(const BatchJob *__restrict__ jobs, const BatchTile *__restrict__ tiles, int n_tiles,
@@ -423,6 +435,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
+    double *hist = reinterpret_cast<double *>(next);
+    next += (size_t)D * kNB * 8;
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
@@ -441,7 +455,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
         const BatchTile tile = tiles[ti];
         if ((int)tile.job != cur) {
             if (cur >= 0) {
-                finish_block<D, false, 1>(P, acc, nullptr, none, false, 1.0f, red_scratch);
+                finish_block<D, false, 1>(P, acc, hist, none, adjust != 0, 1.0f, red_scratch);
                 acc = ThreadSums();
             }
             cur = (int)tile.job;
@@ -455,15 +469,15 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
             P.adjust = adjust;
             P.probe = nullptr;
             if (threadIdx.x == 0) philox_prepare(ph, P.key0, P.key1, P.ctr2_hi, P.job);
-            stage_fast64<D, FID>(P, tab, thr, ftab);   // ends with a barrier
+            stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);   // ends with a barrier
         }
         if (!mc_check(P.chk, (long long)tile.c1 - 1, P.m, 5) || !mc_check(P.chk, tile.c0, (long long)tile.c1, 5)) continue;
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
-        sample_cubes_fast64<D, FID, 1>(P, ph, t, t_end, tab, thr, ftab, acc);
+        sample_cubes_fast64<D, FID, 1>(P, ph, t, t_end, tab, hist, thr, ftab, acc);
     }
-    if (cur >= 0) finish_block<D, false, 1>(P, acc, nullptr, none, false, 1.0f, red_scratch);
+    if (cur >= 0) finish_block<D, false, 1>(P, acc, hist, none, adjust != 0, 1.0f, red_scratch);
 }
 
 }  // namespace mcubes

@@ -132,7 +132,7 @@ int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, 
         if (!fast64_fold(kFid, F, D)) return (int)cudaSuccess;
         static InstanceInfo info;
         auto kern = vsample_fast64_kernel<D, kFid, HK>;
-        constexpr size_t smem = fast64_smem_bytes<D, kFid>();
+        constexpr size_t smem = fast64_smem_bytes<D, kFid, HK>();
         if (smem > (size_t)227 * 1024) return (int)cudaSuccess;
         int occ = 1;
         int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
@@ -221,7 +221,7 @@ int launch_batch_fast_d(const BatchJob *jobs, const BatchTile *tiles, int n_tile
     } else {
         static InstanceInfo info;
         auto kern = vsample_batch_fast64_kernel<D, kFid>;
-        constexpr size_t smem = fast64_smem_bytes<D, kFid>();
+        constexpr size_t smem = fast64_smem_bytes<D, kFid, 1>();
         if (smem > (size_t)227 * 1024) return (int)cudaErrorInvalidValue;
         int occ = 1;
         const int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
