@@ -106,7 +106,9 @@ typedef struct mcubes_tuning {
     int32_t blocks_per_sm;    /* resident blocks per SM to launch (persistent grid); default: occupancy */
     int32_t fp64_plain;       /* FP64 precision, single-job V-Sample: 0 (default) takes the FP64 kernel with
                                  integer bin extraction and per-bin folded integrand tables for the six Genz
-                                 families (the same quantities to FP64 rounding, bins bit-identical);
+                                 families (the same quantities to FP64 rounding, bins bit-identical; adjusting
+                                 launches add half of each sample's bin contributions to C with FP64
+                                 reductions, so C's summation order varies from run to run);
                                  1 forces the plain FP64 kernel, which evaluates the definition step by step */
     int32_t reserved[5];
 } mcubes_tuning;
@@ -280,7 +282,8 @@ typedef struct mcubes_job {
  * hist_mode 0: block-private shared-memory histogram, flushed once per job and block.
  * hist_mode 1: FP64 atomics straight into the job's global bin contributions.
  * In FP64, the jobs of one (d, Genz family) class take the fast FP64 V-Sample kernel (the one
- * mcubes_tuning.fp64_plain describes; block-private shared histogram, hist_mode not consulted)
+ * mcubes_tuning.fp64_plain describes; half of each sample's bin adds as FP64 reductions into the
+ * job's C, half into a block-private shared copy; hist_mode not consulted)
  * when every job of the class meets its conditions and its shared memory fits; fp64_plain = 1
  * sends every class to the plain kernels. mcubes_tune_batch leaves it 0. */
 typedef struct mcubes_batch_tuning {
