@@ -61,7 +61,7 @@ METRIC = "m-Cubes samples/s; time to 1e-3 rel err, plain vs learned/FP32 (1 GB30
 # iteration: the mean over one timed step's 30 adjusting and 30 frozen launches (six families), from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands; None
 # where the kernel changed after the capture.
-VSAMPLE64_DRAM_BYTES_BY_KIND = {"adjusting": 365807, "frozen": 223369}
+VSAMPLE64_DRAM_BYTES_BY_KIND = {"adjusting": None, "frozen": None}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts: 152 SMs; 4 SM sub-partitions x 32 lanes issue one instruction per clock;
@@ -75,22 +75,27 @@ FALLBACK_SM_MHZ = 2070.0
 # ------------------------------------------------------------------------------ operation counts
 # FP64 operations per sample of the FP64 V-Sample's formulation for the six Genz families (the
 # kernel with integer c + u and bin extraction and folded per-bin tables): per axis the product
-# (c + u) R, the Jacobian's product and the family's terms -- one fma of the folded table entries
-# and its accumulation for the Gaussian and C0 (an fma, an add), three for the product peak (fma,
-# fma, product), one fma into the sum for the families that only need sum a x (their constant parts
-# summed as fixed-point integers, converted and added once a sample: 2); per sample the family's
-# closing function at the FP64 operations of its table-driven evaluation (exp 10, cos 13, a
-# reciprocal 5, the corner peak's 1 + s and ninth power 5 + a reciprocal), w = f J and the two
-# sub-cube sums; per sub-cube the mean, the variance (fma, clamp) and the two thread sums; on
-# adjusting iterations the contribution (w F)^2 (2). The d bin additions of an adjusting sample are
-# FP64 reductions the L2 performs, off the FP64 pipe this roofline measures, so they are not
-# counted. Counted from the formulation, not from compiled code.
+# (c + u) R, the Jacobian's product (not for the families closed by exp: Gaussian, C0 and
+# discontinuous, whose Jacobian joins the exponent through integer sums of the bins' exponents and
+# fixed-point ln m_k) and the family's terms -- one fma of the folded table entries and its
+# accumulation for the Gaussian and C0 (an fma, an add), three for the product peak (fma, fma,
+# product), one fma into the sum for the families that only need sum a x (their constant parts
+# summed as fixed-point integers, converted and added once a sample: 2; the Gaussian and C0 convert
+# and add their ln m_k sum the same way); per sample the family's closing function at the FP64
+# operations of its table-driven evaluation (exp 7, cos 11, a reciprocal 5, the corner peak's 1 + s
+# and ninth power 5 + a reciprocal), w = f J where J is a product, and the two sub-cube sums; per
+# sub-cube the mean, the variance (fma, clamp) and the two thread sums; on adjusting iterations the
+# contribution (w F)^2 (2). The d bin additions of an adjusting sample are FP64 reductions the L2
+# performs and compare-and-swap loops on the block's shared copy, not counted. Counted from the
+# formulation, not from compiled code.
 FP64_AXIS_TERMS = {0: 1, 1: 3, 2: 1, 3: 2, 4: 2, 5: 1}
-FP64_FINISH = {0: 15, 1: 5, 2: 12, 3: 10, 4: 10, 5: 12}
+FP64_FINISH = {0: 13, 1: 5, 2: 12, 3: 9, 4: 9, 5: 9}
+FP64_JACOBIAN_IN_EXP = {0: False, 1: False, 2: False, 3: True, 4: True, 5: True}
 
 
 def fp64_ops_per_sample(fid: int, d: int, adjust: bool, p: int = 2) -> float:
-    return d * (2 + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 3 + 5.0 / p + (2 if adjust else 0)
+    jac = 0 if FP64_JACOBIAN_IN_EXP[fid] else 1
+    return d * (1 + jac + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 2 + jac + 5.0 / p + (2 if adjust else 0)
 
 
 def algorithmic_ops_per_sample(fid: int, d: int, adjust: bool, f32: bool) -> float:

@@ -18,8 +18,14 @@
 //     one FP64 fma into the sum;
 //   - the Jacobian prod_i nd Delta_k is taken as prod_i P_k, its constant factor nd^d / prod a
 //     (times prod a^2 for the product peak) folded into the launch's scale fscale;
-//   - exp and cos are table-driven (2^(j/64), cos and sin of 2 pi j / 256, filled per block), with
-//     their reduced arguments' Taylor series to 2^-54 (no library constants or steps);
+//   - for the families closed by exp (Gaussian, C0, discontinuous) the Jacobian joins the exponent:
+//     |P_k| = 2^E_k m_k, so prod |P_k| = 2^(sum E_k) exp(sum ln m_k); E_k is read from the bits of
+//     P_k and summed as an integer, ln m_k (tabulated per bin, below ln 2) is summed exactly in
+//     64-bit fixed point, and the product costs no FP64 operation (the sign of prod a goes to
+//     fscale);
+//   - exp and cos are table-driven (2^(j/256), cos and sin of 2 pi j / 256, filled per block), with
+//     their reduced arguments' Taylor series to 2^-54 (no library constants or steps); the integer
+//     k of the reduction is found in FP32 (within one of the nearest), off the FP64 pipe;
 //   - the discontinuous family's cut x_i < u_i is decided exactly as defined, by one integer
 //     comparison of the offset's bits with a per-bin threshold the block finds by bisection.
 // The per-cube statistics and the reduction are the FP64 kernel's own (vsample.cuh: finish_block).
@@ -33,15 +39,18 @@
 
 namespace mcubes {
 
-constexpr int kExpTab = 64;      // 2^(j / 64), j = 0..63
+constexpr int kExpTab = 256;     // 2^(j / 256), j = 0..255
 constexpr int kCosTab = 256;     // cos and sin of 2 pi j / 256
 
-// ln 2 / 64 in two parts: the high part has 36 significant bits, so k * hi is exact for |k| < 2^17.
-constexpr double kLn2by64Hi = 0x1.62e42fefa0000p-7;
-constexpr double kLn2by64Lo = 0x1.cf79abc9e3b3ap-46;
-constexpr double k64byLn2 = 0x1.71547652b82fep+6;
+// ln 2 / 256 in two parts: the high part has 34 significant bits, so k * hi is exact for |k| < 2^19.
+constexpr double kLn2by256Hi = 0x1.62e42fef80000p-9;
+constexpr double kLn2by256Lo = 0x1.1cf79abc9e3b4p-44;
+constexpr float k256byLn2f = 369.32993f;
 constexpr double kTwoPi64 = 0x1.921fb54442d18p+2;
 constexpr double kRoundMagic = 0x1.8p52;   // 1.5 2^52: adding it rounds to an integer in the low word
+constexpr float kRoundMagicF = 12582912.0f;   // 1.5 2^23, the same in FP32
+// ln m_k of a zero-width bin (P_k = 0): the weight's factor e^-64 2^-1023 underflows with the rest
+constexpr double kLogZero = -64.0;
 
 // Families the fast FP64 kernel serves, and which per-sample closing function each takes.
 template <int FID>
@@ -50,10 +59,14 @@ struct Fast64 {
     static constexpr bool kExp = FID == kGaussian || FID == kC0 || FID == kDiscontinuous;
     static constexpr bool kCos = FID == kOscillatory;
     static constexpr bool kCut = FID == kDiscontinuous;
+    // the Jacobian joins the exponent (exp families): ln m_k per bin, in its own table (centred
+    // families) or added to the fixed-point Q_k (the discontinuous family)
+    static constexpr bool kJLog = kExp;
     // Q_k = a (B_k - u) - P_k for these, a B_k - P_k otherwise
     static constexpr bool kCentred = FID == kGaussian || FID == kC0 || FID == kProductPeak;
     // Q_k as a 64-bit fixed-point integer (2^fix_shift units), summed with integer additions
     static constexpr bool kFixedQ = !kCentred;
+    static constexpr bool kLTab = kJLog && kCentred;
 };
 
 // fl(c + u) for integers 0 <= c < 2^11 and u = bits 2^-52 (bits < 2^52), rounded to nearest even as
@@ -80,12 +93,15 @@ __device__ __forceinline__ double c_plus_u(uint32_t hi, uint32_t lo)
 // and the per-axis fold factors are usable: every a_i finite and non-zero (positive for C0, whose
 // |a (x - u)| must equal a |x - u|) and the folded scale finite and non-zero. Q then carries the fold
 // factors in ip.b (a, or a / (2 pi) for the oscillatory family), the scale nd^d / prod(fold)
-// (nd^d prod a for the product peak) and the fraction bits of the fixed-point table sums (sum_i |fold_i|
-// 2^fix_shift below 2^61). Returns false, leaving Q's fold fields unspecified, otherwise.
+// (nd^d prod a for the product peak; nd^d / prod |a| for the exp families, whose Jacobian is taken
+// as prod |P_k|) and the fraction bits of the fixed-point table sums (sum_i (|fold_i| + 64) 2^fix_shift
+// below 2^61 for the discontinuous family, whose sums also carry ln m_k >= kLogZero; sum_i |fold_i|
+// 2^fix_shift otherwise). Returns false, leaving Q's fold fields unspecified, otherwise.
 inline bool fast64_fold(int fid, VsampleParams &Q, int d)
 {
     if (fid < 0 || fid > 5 || Q.g > 2048u) return false;
     constexpr double kTwoPi = 6.283185307179586;
+    const bool jlog = fid == kGaussian || fid == kC0 || fid == kDiscontinuous;
     double scale = 1.0, fsum = 0.0;
     for (int i = 0; i < d; ++i) {
         const double a = Q.ip.a[i];
@@ -93,9 +109,9 @@ inline bool fast64_fold(int fid, VsampleParams &Q, int d)
         const double f = fid == kOscillatory ? a / kTwoPi : a;
         if (!std::isfinite(f) || f == 0.0) return false;
         Q.ip.b[i] = f;
-        fsum += std::fabs(f);
+        fsum += std::fabs(f) + (fid == kDiscontinuous ? -kLogZero : 0.0);
         scale *= (double)kNB;
-        scale = fid == kProductPeak ? scale * f : scale / f;
+        scale = fid == kProductPeak ? scale * f : scale / (jlog ? std::fabs(f) : f);
     }
     if (!std::isfinite(scale) || scale == 0.0 || !(fsum < 1e15)) return false;
     Q.fscale = scale;
@@ -105,12 +121,17 @@ inline bool fast64_fold(int fid, VsampleParams &Q, int d)
     return true;
 }
 
-// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the FP64 copy of the bin
-// contributions (HK = 1), the cut thresholds, and the exp or cos table.
+// Axes whose bin contributions go straight to the global C (the rest use the block's shared copy).
+__host__ __device__ constexpr int fast64_l2_axes(int d) { return (d + 1) / 2; }
+
+// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the ln m_k table (centred exp
+// families), the FP64 copy of the bin contributions of the axes the L2 does not take (HK = 1), the
+// cut thresholds, and the exp or cos table.
 template <int D, int FID, int HK>
 __host__ __device__ constexpr size_t fast64_smem_bytes()
 {
-    return (size_t)D * kNB * (16 + (HK == 1 ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
+    return (size_t)D * kNB * (16 + (Fast64<FID>::kLTab ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
+           (HK == 1 ? (size_t)(D - fast64_l2_axes(D)) * kNB * 8 : 0) +
            (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
 }
 
@@ -118,42 +139,82 @@ __host__ __device__ constexpr size_t fast64_smem_bytes()
 inline size_t fast64_smem_bytes_rt(int d, int fid, int hk)
 {
     const bool cut = fid == kDiscontinuous, ex = fid == kGaussian || fid == kC0 || fid == kDiscontinuous,
-               co = fid == kOscillatory;
+               co = fid == kOscillatory, ltab = fid == kGaussian || fid == kC0;
     if (fid < 0 || fid > 5) return 0;
-    return (size_t)d * kNB * (16 + (hk == 1 ? 8 : 0) + (cut ? 8 : 0)) + (ex ? kExpTab * 8 : 0) + (co ? kCosTab * 16 : 0);
+    return (size_t)d * kNB * (16 + (ltab ? 8 : 0) + (cut ? 8 : 0)) +
+           (hk == 1 ? (size_t)(d - fast64_l2_axes(d)) * kNB * 8 : 0) + (ex ? kExpTab * 8 : 0) +
+           (co ? kCosTab * 16 : 0);
 }
 
-// exp(x): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so exp(x) = 2^m 2^(j/64) e^r; e^r - 1 from
-// its Taylor series through r^5 (remainder below 4e-17), 2^(j/64) from the block's table, 2^m added
-// to the exponent field. 10 FP64 operations. Outside |x| < 708 (results near or beyond the
-// subnormal range, infinities, NaN) it returns the library's exp.
-__device__ __forceinline__ double exp_tab(double x, const double *T)
+// x cut to 24 significant bits, as an FP32 value (0 below 2^-126); |x| < 2^128.
+__device__ __forceinline__ float f32_cut(double x)
 {
-    if ((__double2hiint(x) & 0x7FFFFFFF) >= 0x40862000) return exp(x);   // |x| >= 708
-    const double kd = __fma_rn(x, k64byLn2, kRoundMagic);
-    const int k = __double2loint(kd);
-    const double kf = kd - kRoundMagic;
-    double r = __fma_rn(kf, -kLn2by64Hi, x);
-    r = __fma_rn(kf, -kLn2by64Lo, r);
-    double q = __fma_rn(r, 1.0 / 120.0, 1.0 / 24.0);
-    q = __fma_rn(q, r, 1.0 / 6.0);
+    const int hx = __double2hiint(x);
+    const int ex = (hx >> 20) & 0x7FF;
+    const int bits = (hx & (int)0x80000000) | ((ex - 896) << 23) | ((hx & 0xFFFFF) << 3) |
+                     (int)((unsigned)__double2loint(x) >> 29);
+    return ex > 896 ? __int_as_float(bits) : 0.0f;
+}
+
+// The nearest integer to v (|v| < 2^22) in FP32: adding 1.5 2^23 rounds it into the low bits.
+__device__ __forceinline__ int f32_round_int(float v)
+{
+    return __float_as_int(__fadd_rn(v, kRoundMagicF)) - 0x4B400000;
+}
+
+// k as an FP64 value (|k| <= 2^20) from its bits with integer operations: the sign, the exponent
+// of the leading one and the bits below it as the top fraction bits.
+__device__ __forceinline__ double small_int_to_double(int k)
+{
+    const unsigned a = (unsigned)(k < 0 ? -k : k);
+    const int e = a != 0u ? 31 - __clz((int)a) : 0;   // a in [2^e, 2^(e+1)), e <= 20
+    const int hi = (k < 0 ? (int)0x80000000 : 0) | ((1023 + e) << 20) | (int)((a ^ (1u << e)) << (20 - e));
+    return a != 0u ? __hiloint2double(hi, 0) : 0.0;
+}
+
+// 2^E exp(x): x = (256 m + j) ln2/256 + r with |r| <= 0.56 ln2/256 (k = 256 m + j within one of the
+// nearest integer to x 256/ln2), so 2^E exp(x) = 2^(m + E) 2^(j/256) e^r; e^r - 1 from its Taylor
+// series through r^4 (remainder below 7e-17), 2^(j/256) from the block's table, m + E added to the
+// exponent field. 7 FP64 operations. Outside |x| < 708, or where the result leaves the normal
+// range, the library's exp and ldexp.
+__device__ __forceinline__ double exp_tab(double x, int E, const double *T)
+{
+    if ((__double2hiint(x) & 0x7FFFFFFF) >= 0x40862000) return ldexp(exp(x), E);   // |x| >= 708
+    const int k = f32_round_int(__fmul_rn(f32_cut(x), k256byLn2f));
+    const double kf = small_int_to_double(k);
+    double r = __fma_rn(kf, -kLn2by256Hi, x);
+    r = __fma_rn(kf, -kLn2by256Lo, r);
+    double q = __fma_rn(r, 1.0 / 24.0, 1.0 / 6.0);
     q = __fma_rn(q, r, 0.5);
     q = __fma_rn(q, r, 1.0);
     q = q * r;                                   // e^r - 1
     const double tj = T[k & (kExpTab - 1)];
-    const double y = __fma_rn(tj, q, tj);        // 2^(j/64) e^r, in [0.99, 2)
-    return __hiloint2double(__double2hiint(y) + ((k >> 6) << 20), __double2loint(y));
+    const double y = __fma_rn(tj, q, tj);        // 2^(j/256) e^r, in [0.99, 2.01)
+    const int m = (k >> 8) + E;
+    const int hy = __double2hiint(y);
+    const int ey = ((hy >> 20) & 0x7FF) + m;
+    if (ey <= 0 || ey >= 0x7FF) return ldexp(y, m);
+    return __hiloint2double(hy + (m << 20), __double2loint(y));
 }
 
-// cos(2 pi t) for |t| < 2^40 turns: t = j/256 + r with |r| <= 1/512 exactly, theta = 2 pi r, and
-// cos(2 pi t) = C_j cos(theta) - S_j sin(theta); cos(theta) - 1 through theta^6 and sin(theta)
-// through theta^5 (remainders below 1e-17). 13 FP64 operations. CS holds (C_j, S_j) pairs.
+// cos(2 pi t) for |t| < 2^40 turns: t = k/256 + r, |r| <= 0.63/256 (k within one of the nearest
+// integer to 256 t: found in FP32 for |t| < 2^12, else rounded in FP64), r exact; theta = 2 pi r and
+// cos(2 pi t) = C_j cos(theta) - S_j sin(theta), j = k mod 256; cos(theta) - 1 through theta^6 and
+// sin(theta) through theta^5 (remainders below 5e-17). 11 FP64 operations below 2^12 turns.
+// CS holds (C_j, S_j) pairs.
 __device__ __forceinline__ double cos_turns(double t, const double2 *CS)
 {
-    const double kd = __fma_rn(t, 256.0, kRoundMagic);
-    const int k = __double2loint(kd);
-    const double kf = kd - kRoundMagic;
-    const double r = __fma_rn(kf, -1.0 / 256.0, t);   // exact
+    int k;
+    double kf;
+    if ((__double2hiint(t) & 0x7FFFFFFF) < 0x40B00000) {   // |t| < 2^12
+        k = f32_round_int(__fmul_rn(f32_cut(t), 256.0f));
+        kf = small_int_to_double(k);
+    } else {
+        const double kd = __fma_rn(t, 256.0, kRoundMagic);
+        k = __double2loint(kd);
+        kf = kd - kRoundMagic;
+    }
+    const double r = __fma_rn(kf, -1.0 / 256.0, t);
     const double th = r * kTwoPi64;
     const double z = th * th;
     double c = __fma_rn(z, -1.0 / 720.0, 1.0 / 24.0);
@@ -187,12 +248,13 @@ __device__ __forceinline__ int split_bin(unsigned long long yb, unsigned long lo
     return k;
 }
 
-// Stage the fast kernel's tables: per axis and bin (P, Q) (see the header), the discontinuous
-// family's cut thresholds, and the exp or cos table; clear n_hist words of the histogram copy.
-// Block-wide.
+// Stage the fast kernel's tables: per axis and bin (P, Q) (see the header), ln m_k (the exp
+// families: in ltab for the centred ones, added to the fixed-point Q_k for the discontinuous one), the
+// discontinuous family's cut thresholds, and the exp or cos table; clear n_hist words of the
+// histogram copy. Block-wide.
 template <int D, int FID>
-__device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *tab, double *hist, int n_hist,
-                                             unsigned long long *thr, double *ftab)
+__device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *tab, long long *ltab, double *hist,
+                                             int n_hist, unsigned long long *thr, double *ftab)
 {
     const IntegrandParams &ip = P.ip;
     for (int e = threadIdx.x; e < D * kNB; e += blockDim.x) {
@@ -204,13 +266,24 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
         const double a = ip.b[i];   // the fold factor (a, or a / (2 pi) for the oscillatory family)
         const double pk = a * w;
         const double base = Fast64<FID>::kCentred ? a * (b0 - ip.u[i]) : a * b0;
+        // ln m_k, where |P_k| = 2^E_k m_k and E_k = (exponent field of P_k) - 1023: m_k in [1, 2), or in
+        // (0, 2) for a subnormal P_k (ln m_k >= -37); kLogZero for a zero-width bin
+        double lm = 0.0;
+        if constexpr (Fast64<FID>::kJLog) {
+            const double ap = fabs(pk);
+            const int E = ((__double2hiint(ap) >> 20) & 0x7FF) - 1023;
+            lm = ap > 0.0 ? log(ldexp(ap, -E)) : kLogZero;
+        }
         if constexpr (Fast64<FID>::kFixedQ) {
-            // |base - pk| <= |a|, and the launch's fix_shift keeps d |a|max 2^fix_shift below 2^62
-            const long long qf = __double2ll_rn(ldexp(base - pk, P.fix_shift));
+            // |base - pk| <= |a| and |ln m_k| <= 64; the launch's fix_shift keeps the sum over the axes
+            // of these bounds, times 2^fix_shift, below 2^61
+            long long qf = __double2ll_rn(ldexp(base - pk, P.fix_shift));
+            if constexpr (Fast64<FID>::kJLog) qf += __double2ll_rn(ldexp(lm, P.fix_shift));
             tab[e] = make_double2(pk, __longlong_as_double(qf));
         } else {
             tab[e] = make_double2(pk, base - pk);
         }
+        if constexpr (Fast64<FID>::kLTab) ltab[e] = __double2ll_rn(ldexp(lm, 52));   // 2^-52 units
         if constexpr (Fast64<FID>::kCut) {
             // inside iff fma(w, delta, b0) < u; the decision is monotone in the offset, so it is a
             // threshold on the offset's bit pattern: yn's bits in bin 0, G's bits in the others,
@@ -261,7 +334,7 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
 template <int D, int FID, int HK>
 __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, const PhiloxPre &ph, uint32_t t,
                                                     const uint32_t t_end,
-                                                    const double2 *tab, double *hist,
+                                                    const double2 *tab, const long long *ltab, double *hist,
                                                     const unsigned long long *thr, const double *ftab,
                                                     ThreadSums &acc)
 {
@@ -291,7 +364,9 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
         const PhiloxCube cube = philox_cube(t, ph);
         for (uint32_t q = 0; q < p; ++q) {
             double s = s0, prod = 1.0, J = 1.0;
-            long long sq = 0;   // fixed-point sum of the Q_k (kFixedQ)
+            long long sq = 0;   // fixed-point sum of the Q_k (kFixedQ; with the ln m_k for kJLog)
+            long long sl = 0;   // sum of the ln m_k, 2^-52 units (kLTab)
+            int sE = 0;         // sum of the exponent fields of the P_k (kJLog)
             bool inside = true;
             int kofs[D];
 #pragma unroll
@@ -311,6 +386,8 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
                         kofs[i] = i * kNB + k;
                         const double2 pq = tab[kofs[i]];
                         const double G = __longlong_as_double((long long)gb);
+                        if constexpr (Fast64<FID>::kJLog) sE += (__double2hiint(pq.x) >> 20) & 0x7FF;
+                        if constexpr (Fast64<FID>::kLTab) sl += ltab[kofs[i]];
                         if constexpr (Fast64<FID>::kFixedQ) {
                             s = __fma_rn(pq.x, G, s);
                             sq += __double_as_longlong(pq.y);
@@ -325,16 +402,18 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
                             }
                         }
                         if constexpr (Fast64<FID>::kCut) inside = inside && ((k == 0 ? yb : gb) < thr[kofs[i]]);
-                        J *= pq.x;
+                        if constexpr (!Fast64<FID>::kJLog) J *= pq.x;
                     }
                 }
             }
             if constexpr (Fast64<FID>::kFixedQ) s = __fma_rn(__ll2double_rn(sq), inv_fix, s);
+            // the exp families' weight f prod |P_k| = 2^(sum E_k) exp(+-s + sum ln m_k)
+            const int E = sE - D * 1023;
             double fv;
             if constexpr (FID == kGaussian || FID == kC0) {
-                fv = exp_tab(-s, ftab);
+                fv = exp_tab(__fma_rn(__ll2double_rn(sl), 0x1p-52, -s), E, ftab);
             } else if constexpr (FID == kDiscontinuous) {
-                fv = inside ? exp_tab(s, ftab) : 0.0;
+                fv = inside ? exp_tab(s, E, ftab) : 0.0;
             } else if constexpr (FID == kOscillatory) {
                 fv = cos_turns(s, reinterpret_cast<const double2 *>(ftab));
             } else if constexpr (FID == kProductPeak) {
@@ -342,7 +421,7 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
             } else {   // corner peak
                 fv = inv_pow<D + 1>(1.0 + s);
             }
-            const double w = fv * J;   // the weight without the launch's scale fscale
+            const double w = Fast64<FID>::kJLog ? fv : fv * J;   // the weight without the launch's scale fscale
             S1 += w;
             S2 = __fma_rn(w, w, S2);
             if (adjust) {
@@ -353,11 +432,11 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
                 // around an FP64 add on the SM. Half and half keeps the launch time the same wherever C lies
                 // (the L2's reduction rate into C depends on its physical placement). A zero adds nothing.
                 if (hv != 0.0) {
-                    constexpr int kL2 = (D + 1) / 2;
+                    constexpr int kL2 = fast64_l2_axes(D);
 #pragma unroll
                     for (int i = 0; i < kL2; ++i) red_add_f64_global(&P.C[kofs[i]], hv);
 #pragma unroll
-                    for (int i = kL2; i < D; ++i) atomicAdd(&hist[kofs[i]], hv);
+                    for (int i = kL2; i < D; ++i) atomicAdd(&hist[kofs[i] - kL2 * kNB], hv);
                 }
             }
         }
@@ -387,6 +466,19 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
     }
 }
 
+// Add the block's shared copy (the bins of axes fast64_l2_axes(D)..D-1) into C; block-wide, ends
+// with a barrier so that the copy can be cleared again.
+template <int D>
+__device__ __forceinline__ void flush_fast64_hist(double *C, const double *hist)
+{
+    constexpr int kL2 = fast64_l2_axes(D);
+    for (int e = threadIdx.x; e < (D - kL2) * kNB; e += blockDim.x) {
+        const double v = hist[e];
+        if (v != 0.0) atomicAdd(&C[kL2 * kNB + e], v);
+    }
+    __syncthreads();
+}
+
 // One job, persistent grid; HK = 0 frozen, HK = 1 adjusting. Adjusting launches add each sample's
 // contribution on half its axes straight into the job's FP64 C with native FP64 reductions, which the
 // L2 performs (off the FP64 pipe, the kernel's bound), and on the other half into the block's shared
@@ -394,18 +486,21 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
 template <int D, int FID, int HK>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(const VsampleParams P)
 {
+    constexpr int kL2 = fast64_l2_axes(D);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
+    long long *ltab = reinterpret_cast<long long *>(next);
+    if constexpr (Fast64<FID>::kLTab) next += (size_t)D * kNB * 8;
     double *hist = reinterpret_cast<double *>(next);
-    if constexpr (HK == 1) next += (size_t)D * kNB * 8;
+    if constexpr (HK == 1) next += (size_t)(D - kL2) * kNB * 8;
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
     __shared__ double red_scratch[64];
 
     const bool adjust = HK == 1 && P.adjust != 0;
-    stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);
+    stage_fast64<D, FID>(P, tab, ltab, hist, adjust ? (D - kL2) * kNB : 0, thr, ftab);
 
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,9 +509,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(con
     const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     ThreadSums acc;
-    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, hist, thr, ftab, acc);
+    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, ltab, hist, thr, ftab, acc);
     const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
-    finish_block<D, false, HK>(P, acc, hist, none, adjust, 1.0f, red_scratch);
+    finish_block<D, false, HK>(P, acc, hist, none, false, 1.0f, red_scratch);
+    if (adjust) flush_fast64_hist<D>(P.C, hist);
 }
 
 // ------------------------------------------------------------------------------ batches
@@ -432,11 +528,14 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
     vsample_batch_fast64_kernel(const BatchJob *__restrict__ jobs, const BatchTile *__restrict__ tiles, int n_tiles,
                                 int iteration, int parity, int adjust, uint32_t perm_mul)
 {
+    constexpr int kL2 = fast64_l2_axes(D);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
+    long long *ltab = reinterpret_cast<long long *>(next);
+    if constexpr (Fast64<FID>::kLTab) next += (size_t)D * kNB * 8;
     double *hist = reinterpret_cast<double *>(next);
-    next += (size_t)D * kNB * 8;
+    next += (size_t)(D - kL2) * kNB * 8;
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
@@ -455,7 +554,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
         const BatchTile tile = tiles[ti];
         if ((int)tile.job != cur) {
             if (cur >= 0) {
-                finish_block<D, false, 1>(P, acc, hist, none, adjust != 0, 1.0f, red_scratch);
+                finish_block<D, false, 1>(P, acc, hist, none, false, 1.0f, red_scratch);
+                if (adjust) flush_fast64_hist<D>(P.C, hist);
                 acc = ThreadSums();
             }
             cur = (int)tile.job;
@@ -469,15 +569,18 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
             P.adjust = adjust;
             P.probe = nullptr;
             if (threadIdx.x == 0) philox_prepare(ph, P.key0, P.key1, P.ctr2_hi, P.job);
-            stage_fast64<D, FID>(P, tab, hist, adjust ? D * kNB : 0, thr, ftab);   // ends with a barrier
+            stage_fast64<D, FID>(P, tab, ltab, hist, adjust ? (D - kL2) * kNB : 0, thr, ftab);   // ends with a barrier
         }
         if (!mc_check(P.chk, (long long)tile.c1 - 1, P.m, 5) || !mc_check(P.chk, tile.c0, (long long)tile.c1, 5)) continue;
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
-        sample_cubes_fast64<D, FID, 1>(P, ph, t, t_end, tab, hist, thr, ftab, acc);
+        sample_cubes_fast64<D, FID, 1>(P, ph, t, t_end, tab, ltab, hist, thr, ftab, acc);
     }
-    if (cur >= 0) finish_block<D, false, 1>(P, acc, hist, none, adjust != 0, 1.0f, red_scratch);
+    if (cur >= 0) {
+        finish_block<D, false, 1>(P, acc, hist, none, false, 1.0f, red_scratch);
+        if (adjust) flush_fast64_hist<D>(P.C, hist);
+    }
 }
 
 }  // namespace mcubes
