@@ -61,7 +61,7 @@ METRIC = "m-Cubes samples/s; time to 1e-3 rel err, plain vs learned/FP32 (1 GB30
 # iteration: the mean over one timed step's 30 adjusting and 30 frozen launches (six families), from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel as it stands; None
 # where the kernel changed after the capture.
-VSAMPLE64_DRAM_BYTES_BY_KIND = {"adjusting": None, "frozen": None}
+VSAMPLE64_DRAM_BYTES_BY_KIND = {"adjusting": 341547, "frozen": 215808}
 NB = 500
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts: 152 SMs; 4 SM sub-partitions x 32 lanes issue one instruction per clock;
@@ -74,11 +74,11 @@ FALLBACK_SM_MHZ = 2070.0
 
 # ------------------------------------------------------------------------------ operation counts
 # FP64 operations per sample of the FP64 V-Sample's formulation for the six Genz families (the
-# kernel with integer c + u and bin extraction and folded per-bin tables): per axis the product
-# (c + u) R, the Jacobian's product (not for the families closed by exp: Gaussian, C0 and
-# discontinuous, whose Jacobian joins the exponent through integer sums of the bins' exponents and
-# fixed-point ln m_k) and the family's terms -- one fma of the folded table entries and its
-# accumulation for the Gaussian and C0 (an fma, an add), three for the product peak (fma, fma,
+# kernel with integer c + u, an integer (c + u) R rounded as FP64 rounds it, integer bin extraction
+# and folded per-bin tables): per axis the Jacobian's product (not for the families closed by exp:
+# Gaussian, C0 and discontinuous, whose Jacobian joins the exponent through integer sums of the bins'
+# exponents and fixed-point ln m_k) and the family's terms -- one fma of the folded table entries and
+# its accumulation for the Gaussian and C0 (an fma, an add), three for the product peak (fma, fma,
 # product), one fma into the sum for the families that only need sum a x (their constant parts
 # summed as fixed-point integers, converted and added once a sample: 2; the Gaussian and C0 convert
 # and add their ln m_k sum the same way); per sample the family's closing function at the FP64
@@ -95,7 +95,7 @@ FP64_JACOBIAN_IN_EXP = {0: False, 1: False, 2: False, 3: True, 4: True, 5: True}
 
 def fp64_ops_per_sample(fid: int, d: int, adjust: bool, p: int = 2) -> float:
     jac = 0 if FP64_JACOBIAN_IN_EXP[fid] else 1
-    return d * (1 + jac + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 2 + jac + 5.0 / p + (2 if adjust else 0)
+    return d * (jac + FP64_AXIS_TERMS[fid]) + FP64_FINISH[fid] + 2 + jac + 5.0 / p + (2 if adjust else 0)
 
 
 def algorithmic_ops_per_sample(fid: int, d: int, adjust: bool, f32: bool) -> float:

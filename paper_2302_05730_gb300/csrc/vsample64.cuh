@@ -3,8 +3,9 @@
 // the definition does not need is moved off that pipe, while every step keeps FP64 accuracy and
 // the bin index stays bit-identical to the definition's:
 //   - c + u rounded to FP64 (nearest even, as an FP64 addition rounds) is built from the integers
-//     c 2^52 + bits with integer operations, and yn = (c + u) R is one FP64 product, exactly as
-//     defined (the bin depends on its rounding);
+//     c 2^52 + bits, and yn = (c + u) R from the 106-bit integer product of the two significands,
+//     rounded to nearest even as the FP64 multiply rounds it: both with integer operations, and yn
+//     bit-identical to the definition's (the bin depends on its rounding);
 //   - the bin k = floor(yn) and the offset in the bin come from the bits of yn with integer
 //     operations: for yn >= 1, G = 1 + (yn - k) is exact and is built by shifting the fraction
 //     bits of yn under the exponent of 1; for yn < 1 (bin 0) G is 1 + yn cut to 52 fraction bits
@@ -69,23 +70,37 @@ struct Fast64 {
     static constexpr bool kLTab = kJLog && kCentred;
 };
 
-// fl(c + u) for integers 0 <= c < 2^11 and u = bits 2^-52 (bits < 2^52), rounded to nearest even as
-// an FP64 addition rounds, from hi = c 2^20 + (bits >> 32) and lo = the low 32 bits: with N = c 2^52
-// + bits of bit length L, the significand is N shifted to 53 bits (rounded when L > 53) and the
-// exponent is L - 53.
-__device__ __forceinline__ double c_plus_u(uint32_t hi, uint32_t lo)
+// The bits of yn = fl(fl(c + u) R) (both FP64 roundings, to nearest even) for integers 0 <= c < 2^11 and
+// u = bits 2^-52 (bits < 2^52), from hi = c 2^20 + (bits >> 32) and lo = the low 32 bits, with integer
+// operations only. N = c 2^52 + bits has bit length L; fl(c + u) = q 2^(L - 105), q = N cut to 53 bits
+// and rounded to nearest even (exact when L <= 53); R = Rm 2^(eR - 52) (Rm with its leading bit); yn's
+// significand is the 105- or 106-bit product q Rm cut to 53 bits and rounded to nearest even. 0 for
+// c + u = 0.
+__device__ __forceinline__ unsigned long long cu_times_r_bits(uint32_t hi, uint32_t lo, unsigned long long Rm, int eR)
 {
     const unsigned long long N = ((unsigned long long)hi << 32) | lo;
-    const int L = 64 - __clzll((long long)N);
+    int L = 64 - __clzll((long long)N);
     unsigned long long q;
     if (L > 53) {
         const int s = L - 53;
         q = (N + (1ull << (s - 1)) - 1ull + ((N >> s) & 1ull)) >> s;
+        if (q >> 53) {   // rounded up to 2^53
+            q >>= 1;
+            ++L;
+        }
     } else {
         q = N << (53 - L);
     }
-    const unsigned long long bits = ((unsigned long long)(969 + L) << 52) + q;
-    return N != 0ull ? __longlong_as_double((long long)bits) : 0.0;
+    const unsigned long long plo = q * Rm;
+    const unsigned long long phi = __umul64hi(q, Rm);   // q Rm < 2^106: phi < 2^42
+    const int sh = 52 + (int)(phi >> 41);               // bits below the 53-bit significand
+    unsigned long long sig = (phi << (64 - sh)) | (plo >> sh);
+    const unsigned long long rem = plo & ((1ull << sh) - 1ull);
+    const unsigned long long half = 1ull << (sh - 1);
+    sig += (rem > half || (rem == half && (sig & 1ull))) ? 1ull : 0ull;
+    // yn = sig 2^(E - 52) with E = L - 105 + eR + sh; sig = 2^53 carries into the exponent field
+    const int E = L - 105 + eR + sh;
+    return N != 0ull ? ((unsigned long long)(E + 1022) << 52) + sig : 0ull;
 }
 
 // Host: the fast kernel's per-launch parameters for family fid (0..5) at dimension d, from the
@@ -120,6 +135,12 @@ inline bool fast64_fold(int fid, VsampleParams &Q, int d)
     Q.fix_shift = 61 - e;
     return true;
 }
+
+// Block size of the single-job fast kernel: one 512-thread block an SM (16 warps, as two blocks of 256)
+// holds one copy of the tables, which leaves the SM more of its L1 (frozen launches of the exp families
+// ran 7-10% faster than with two 256-thread blocks). Above d = 12 the 128 registers of a 512-thread
+// block would spill: 256 threads there.
+__host__ __device__ constexpr int fast64_threads(int d) { return d <= 12 ? 512 : 256; }
 
 // Axes whose bin contributions go straight to the global C (the rest use the block's shared copy).
 __host__ __device__ constexpr int fast64_l2_axes(int d) { return (d + 1) / 2; }
@@ -352,7 +373,9 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
     }
     const uint32_t gsh = P.g << 20;
     const double inv_fix = ldexp(1.0, -P.fix_shift);
-    const double R = P.R;
+    const unsigned long long Rb = (unsigned long long)__double_as_longlong(P.R);
+    const unsigned long long Rm = (Rb & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int eR = (int)(Rb >> 52) - 1023;   // R = nd / g >= 500 / 2048: normal
     const unsigned long long ycap_bits = (unsigned long long)__double_as_longlong(P.ycap);
     const uint32_t p = P.p;
     const double s0 = FID == kOscillatory ? P.ip.u[0] : 0.0;   // the phase offset u_1, in turns
@@ -377,8 +400,7 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
                 for (int h = 0; h < 2; ++h) {
                     const int i = 2 * j + h;
                     if (i < D) {
-                        const double yn = __dmul_rn(c_plus_u(dsh[i] | (wv[2 * h] & 0xFFFFFu), wv[2 * h + 1]), R);
-                        unsigned long long yb = (unsigned long long)__double_as_longlong(yn);
+                        unsigned long long yb = cu_times_r_bits(dsh[i] | (wv[2 * h] & 0xFFFFFu), wv[2 * h + 1], Rm, eR);
                         yb = yb < ycap_bits ? yb : ycap_bits;   // min(yn, largest double below nd)
                         unsigned long long gb;
                         int k = split_bin(yb, gb);
@@ -484,7 +506,7 @@ __device__ __forceinline__ void flush_fast64_hist(double *C, const double *hist)
 // L2 performs (off the FP64 pipe, the kernel's bound), and on the other half into the block's shared
 // FP64 copy, flushed into C at the end.
 template <int D, int FID, int HK>
-__global__ void __launch_bounds__(kMaxBlockThreads, 1) vsample_fast64_kernel(const VsampleParams P)
+__global__ void __launch_bounds__(fast64_threads(D), 1) vsample_fast64_kernel(const VsampleParams P)
 {
     constexpr int kL2 = fast64_l2_axes(D);
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -135,13 +135,14 @@ int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, 
         constexpr size_t smem = fast64_smem_bytes<D, kFid, HK>();
         if (smem > (size_t)227 * 1024) return (int)cudaSuccess;
         int occ = 1;
-        int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
+        constexpr int kThreads = fast64_threads(D);
+        int e = instance_occupancy(info, kern, kThreads, smem, occ);
         if (e != (int)cudaSuccess) return e;
-        const int threads = req.user_threads ? req.threads : kMaxBlockThreads;
+        const int threads = req.user_threads ? req.threads : kThreads;
         int bps = req.blocks_per_sm;
         if (bps <= 0) {
             bps = occ;
-            if (threads < kMaxBlockThreads) bps = bps * (kMaxBlockThreads / threads);
+            if (threads < kThreads) bps = bps * (kThreads / threads);
         }
         VsampleParams Q;
         const uint64_t blocks = single_launch_shape(Q, F, req, threads, bps);
