@@ -145,18 +145,51 @@ __host__ __device__ constexpr int fast64_threads(int d) { return d <= 12 ? 512 :
 // Axes whose bin contributions go straight to the global C (the rest use the block's shared copy).
 __host__ __device__ constexpr int fast64_l2_axes(int d) { return (d + 1) / 2; }
 
-// Shared-memory bytes of one fast FP64 block: the (P, Q) table, the ln m_k table (centred exp
-// families), the FP64 copy of the bin contributions of the axes the L2 does not take (HK = 1), the
-// cut thresholds, and the exp or cos table.
-template <int D, int FID, int HK>
-__host__ __device__ constexpr size_t fast64_smem_bytes()
+// Shared-memory bytes of one fast FP64 block's tables: the (P, Q) table, the ln m_k table (centred
+// exp families), the cut thresholds, and the exp or cos table.
+template <int D, int FID>
+__host__ __device__ constexpr size_t fast64_table_bytes()
 {
     return (size_t)D * kNB * (16 + (Fast64<FID>::kLTab ? 8 : 0) + (Fast64<FID>::kCut ? 8 : 0)) +
-           (HK == 1 ? (size_t)(D - fast64_l2_axes(D)) * kNB * 8 : 0) +
            (Fast64<FID>::kExp ? kExpTab * 8 : 0) + (Fast64<FID>::kCos ? kCosTab * 16 : 0);
 }
 
-// The same at a run-time d and family (0..5), for host-side eligibility checks; 0 for other families.
+// Bytes of R copies of the FP64 bin contributions of the axes the L2 does not take.
+__host__ __device__ constexpr size_t fast64_hist_bytes(int d, int r)
+{
+    return (size_t)r * (size_t)(d - fast64_l2_axes(d)) * kNB * 8;
+}
+
+// Copies of the shared FP64 bins in the single-job kernel, lane-interleaved: lane l adds into copy
+// l mod R (word R e + l mod R of bin e), so only the lanes that share a copy can collide in one
+// compare-and-swap round. A warp repeats the round while any of its lanes collided: with one copy and
+// 500 random bins, 63% of warp-level updates; 20% with four. The most copies, up to 4, that keep the
+// block within kFast64HistSmemCap bytes, so that the SM keeps a large L1 beside it.
+constexpr size_t kFast64HistSmemCap = 164 * 1024;
+template <int D, int FID>
+__host__ __device__ constexpr int fast64_hist_copies()
+{
+    int r = 4;
+    while (r > 1 && fast64_table_bytes<D, FID>() + fast64_hist_bytes(D, r) > kFast64HistSmemCap) r /= 2;
+    return r;
+}
+
+// Shared-memory bytes of one single-job fast FP64 block (HK = 1: with the copies of the bins).
+template <int D, int FID, int HK>
+__host__ __device__ constexpr size_t fast64_smem_bytes()
+{
+    return fast64_table_bytes<D, FID>() + (HK == 1 ? fast64_hist_bytes(D, fast64_hist_copies<D, FID>()) : 0);
+}
+
+// Shared-memory bytes of one batched fast FP64 block (one copy of the bins).
+template <int D, int FID>
+__host__ __device__ constexpr size_t fast64_batch_smem_bytes()
+{
+    return fast64_table_bytes<D, FID>() + fast64_hist_bytes(D, 1);
+}
+
+// fast64_batch_smem_bytes (hk = 1) or the tables alone (hk = 0) at a run-time d and family (0..5), for
+// host-side eligibility checks of batched classes; 0 for other families.
 inline size_t fast64_smem_bytes_rt(int d, int fid, int hk)
 {
     const bool cut = fid == kDiscontinuous, ex = fid == kGaussian || fid == kC0 || fid == kDiscontinuous,
@@ -352,7 +385,7 @@ __device__ __forceinline__ void stage_fast64(const VsampleParams &P, double2 *ta
 }
 
 // Algorithm 2's loop over sub-cubes [t, t_end) for the fast FP64 kernel.
-template <int D, int FID, int HK>
+template <int D, int FID, int HK, int kR>
 __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, const PhiloxPre &ph, uint32_t t,
                                                     const uint32_t t_end,
                                                     const double2 *tab, const long long *ltab, double *hist,
@@ -360,7 +393,9 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
                                                     ThreadSums &acc)
 {
     static_assert(Fast64<FID>::kOn, "the fast FP64 kernel serves the six Genz families");
+    static_assert(kR >= 1 && (kR & (kR - 1)) == 0, "a power of two of copies");
     const bool adjust = HK == 1 && P.adjust != 0;
+    const int copy = (int)(threadIdx.x & (unsigned)(kR - 1));   // this lane's copy of the shared bins
     // strata digits c_i, held as c_i 2^20 (the high word of c_i 2^52; g <= 2^11)
     uint32_t dsh[D];
     {
@@ -458,7 +493,7 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
 #pragma unroll
                     for (int i = 0; i < kL2; ++i) red_add_f64_global(&P.C[kofs[i]], hv);
 #pragma unroll
-                    for (int i = kL2; i < D; ++i) atomicAdd(&hist[kofs[i] - kL2 * kNB], hv);
+                    for (int i = kL2; i < D; ++i) atomicAdd(&hist[(kofs[i] - kL2 * kNB) * kR + copy], hv);
                 }
             }
         }
@@ -488,14 +523,17 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
     }
 }
 
-// Add the block's shared copy (the bins of axes fast64_l2_axes(D)..D-1) into C; block-wide, ends
-// with a barrier so that the copy can be cleared again.
-template <int D>
+// Add the block's kR lane-interleaved copies of the shared bins (axes fast64_l2_axes(D)..D-1) into C,
+// the copies of a bin summed in order; block-wide, ends with a barrier so that the copies can be
+// cleared again.
+template <int D, int kR>
 __device__ __forceinline__ void flush_fast64_hist(double *C, const double *hist)
 {
     constexpr int kL2 = fast64_l2_axes(D);
     for (int e = threadIdx.x; e < (D - kL2) * kNB; e += blockDim.x) {
-        const double v = hist[e];
+        double v = hist[(size_t)e * kR];
+#pragma unroll
+        for (int c = 1; c < kR; ++c) v += hist[(size_t)e * kR + c];
         if (v != 0.0) atomicAdd(&C[kL2 * kNB + e], v);
     }
     __syncthreads();
@@ -503,26 +541,27 @@ __device__ __forceinline__ void flush_fast64_hist(double *C, const double *hist)
 
 // One job, persistent grid; HK = 0 frozen, HK = 1 adjusting. Adjusting launches add each sample's
 // contribution on half its axes straight into the job's FP64 C with native FP64 reductions, which the
-// L2 performs (off the FP64 pipe, the kernel's bound), and on the other half into the block's shared
-// FP64 copy, flushed into C at the end.
+// L2 performs (off the FP64 pipe, the kernel's bound), and on the other half into the block's
+// lane-interleaved shared FP64 copies (fast64_hist_copies), flushed into C at the end.
 template <int D, int FID, int HK>
 __global__ void __launch_bounds__(fast64_threads(D), 1) vsample_fast64_kernel(const VsampleParams P)
 {
     constexpr int kL2 = fast64_l2_axes(D);
+    constexpr int kR = fast64_hist_copies<D, FID>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *tab = reinterpret_cast<double2 *>(smem_raw);
     unsigned char *next = smem_raw + (size_t)D * kNB * 16;
     long long *ltab = reinterpret_cast<long long *>(next);
     if constexpr (Fast64<FID>::kLTab) next += (size_t)D * kNB * 8;
     double *hist = reinterpret_cast<double *>(next);
-    if constexpr (HK == 1) next += (size_t)(D - kL2) * kNB * 8;
+    if constexpr (HK == 1) next += fast64_hist_bytes(D, kR);
     unsigned long long *thr = reinterpret_cast<unsigned long long *>(next);
     if constexpr (Fast64<FID>::kCut) next += (size_t)D * kNB * 8;
     double *ftab = reinterpret_cast<double *>(next);
     __shared__ double red_scratch[64];
 
     const bool adjust = HK == 1 && P.adjust != 0;
-    stage_fast64<D, FID>(P, tab, ltab, hist, adjust ? (D - kL2) * kNB : 0, thr, ftab);
+    stage_fast64<D, FID>(P, tab, ltab, hist, adjust ? (D - kL2) * kNB * kR : 0, thr, ftab);
 
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -531,10 +570,10 @@ __global__ void __launch_bounds__(fast64_threads(D), 1) vsample_fast64_kernel(co
     const uint32_t t_end = (uint32_t)(((rng + 1) * P.m) / nthreads);
 
     ThreadSums acc;
-    sample_cubes_fast64<D, FID, HK>(P, P.ph, t, t_end, tab, ltab, hist, thr, ftab, acc);
+    sample_cubes_fast64<D, FID, HK, kR>(P, P.ph, t, t_end, tab, ltab, hist, thr, ftab, acc);
     const IntHist none{0u, 0u, 0u, 0.0f, 0.0f};
     finish_block<D, false, HK>(P, acc, hist, none, false, 1.0f, red_scratch);
-    if (adjust) flush_fast64_hist<D>(P.C, hist);
+    if (adjust) flush_fast64_hist<D, kR>(P.C, hist);
 }
 
 // ------------------------------------------------------------------------------ batches
@@ -577,7 +616,7 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
         if ((int)tile.job != cur) {
             if (cur >= 0) {
                 finish_block<D, false, 1>(P, acc, hist, none, false, 1.0f, red_scratch);
-                if (adjust) flush_fast64_hist<D>(P.C, hist);
+                if (adjust) flush_fast64_hist<D, 1>(P.C, hist);
                 acc = ThreadSums();
             }
             cur = (int)tile.job;
@@ -597,11 +636,11 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1)
         const uint32_t n = tile.c1 - tile.c0;
         const uint32_t t = tile.c0 + (uint32_t)(((uint64_t)r * n) / blockDim.x);
         const uint32_t t_end = tile.c0 + (uint32_t)(((uint64_t)(r + 1) * n) / blockDim.x);
-        sample_cubes_fast64<D, FID, 1>(P, ph, t, t_end, tab, ltab, hist, thr, ftab, acc);
+        sample_cubes_fast64<D, FID, 1, 1>(P, ph, t, t_end, tab, ltab, hist, thr, ftab, acc);
     }
     if (cur >= 0) {
         finish_block<D, false, 1>(P, acc, hist, none, false, 1.0f, red_scratch);
-        if (adjust) flush_fast64_hist<D>(P.C, hist);
+        if (adjust) flush_fast64_hist<D, 1>(P.C, hist);
     }
 }
 

@@ -222,7 +222,7 @@ int launch_batch_fast_d(const BatchJob *jobs, const BatchTile *tiles, int n_tile
     } else {
         static InstanceInfo info;
         auto kern = vsample_batch_fast64_kernel<D, kFid>;
-        constexpr size_t smem = fast64_smem_bytes<D, kFid, 1>();
+        constexpr size_t smem = fast64_batch_smem_bytes<D, kFid>();
         if (smem > (size_t)227 * 1024) return (int)cudaErrorInvalidValue;
         int occ = 1;
         const int e = instance_occupancy(info, kern, kMaxBlockThreads, smem, occ);
