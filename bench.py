@@ -883,10 +883,10 @@ def main():
     def fp32_obj():
         if not run32:
             return None
-        return {"value": value32, "unit": "samples/s", "steps": steps32, "ms_per_step": total32 / steps32,
-                "dtype": "f32 point/integrand, f64 sums/Rebin",
+        return {"value": round(value32, 1), "unit": "samples/s", "steps": steps32,
+                "ms_per_step": round(total32 / steps32, 4), "dtype": "f32 point/integrand, f64 sums/Rebin",
                 "roofline": {"bound": "alu", "pipe": "fp32 issue", "unit": "T lane-ops/s", "peak": peak32 / 1e12,
-                             "achieved": roof32["achieved"], "frac": roof32["frac"],
+                             "achieved": round(roof32["achieved"], 5), "frac": round(roof32["frac"], 4),
                              "by_kind": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4), "frac": round(v["frac"], 4)}
                                          for k, v in roof32["by_kind"].items()}}}
 
@@ -894,8 +894,8 @@ def main():
         v = value64 if run64 else value32
         tot = total64 if run64 else total32
         st = args.steps if run64 else steps32
-        line = {"metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": world, "steps": st,
-                "warmup": args.warmup, "ms_per_step": tot / st, "higher_is_better": True, "scaling": "weak",
+        line = {"metric": METRIC, "value": round(v, 1), "unit": "samples/s", "n_gpus": world, "steps": st,
+                "warmup": args.warmup, "ms_per_step": round(tot / st, 4), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if run64 else "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD if run64 else "genz6-d8-n1e8-fp32eval", "d": D, "ncall": ncall,
                            "m": m, "p": p, "iters": ITMAX, "iter_adjust": ADJ, "families": n_fam,
@@ -905,14 +905,14 @@ def main():
         if run64:
             line["roofline"] = {
                 "bound": "alu", "pipe": "fp64", "unit": "T fp64-ops/s", "peak": peak64 / 1e12,
-                "achieved": roof64["achieved"], "frac": roof64["frac"],
+                "achieved": round(roof64["achieved"], 5), "frac": round(roof64["frac"], 4),
                 "traffic": None if ncall != NCALL or None in VSAMPLE64_DRAM_BYTES_BY_KIND.values() else
                 float(np.mean(list(VSAMPLE64_DRAM_BYTES_BY_KIND.values()))),
                 "kernel": "vsample_fast64_kernel<8,fid,HK>",
                 "avg_launch_ms": round(roof64["avg_launch_ms"], 4),
                 "by_kind": {k: {"avg_launch_ms": round(v["avg_launch_ms"], 4), "frac": round(v["frac"], 4),
                                 "traffic": v["traffic"]} for k, v in roof64["by_kind"].items()},
-                "peak_basis": f"152 SMs x 2 FP64 lanes x {sm_mhz:.0f} MHz ({peak_src}; 1.25 TFLOP/s nominal)"}
+                "peak_basis": f"152 SMs x 2 FP64 lanes x {sm_mhz:.0f} MHz ({peak_src})"}
         line.update(extra)
         line["fp32_eval"] = fp32_obj()
         line["clocks"] = clk
@@ -959,7 +959,7 @@ def main():
         for fid in fams:
             capi.integrate(fid, pars[fid], D, ncall, ITMAX, ADJ, 1 + k, precision=prec_e2e, return_iters=True)
     e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
-    e2e = {"value": samples * n_fam * ITMAX * e2e_steps * world / e2e_s, "unit": "samples/s",
+    e2e = {"value": round(samples * n_fam * ITMAX * e2e_steps * world / e2e_s, 1), "unit": "samples/s",
            "h2d_bytes_per_step": n_fam * 16, "d2h_bytes_per_step": n_fam * 2 * (ITMAX + 1) * 8,
            "call": "mcubes_integrate_ex per family, host results"}
 
@@ -1033,9 +1033,9 @@ def main():
         t0 = time.perf_counter()
         nn = oracle_vsample_ranges(fams, pars, grids, ncall, starts, cn, threads, mode=0)
         el = time.perf_counter() - t0
-        cpu = {"value": nn / el, "unit": "samples/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": round(nn / el, 1), "unit": "samples/s", "cores": threads, "kind": "oracle",
                "sample": f"first {cn} sub-cubes of each of 6 families, FP64, adjusting, {threads} threads ({el:.1f} s)",
-               "single_thread": n1 / el1}
+               "single_thread": round(n1 / el1, 1)}
 
     if rank == 0:
         line = headline({"e2e": e2e, "cpu_baseline": cpu})
