@@ -100,9 +100,10 @@ typedef struct mcubes_result {
 
 /* Launch tuning. Zero fields take the defaults. */
 typedef struct mcubes_tuning {
-    int32_t block_threads;    /* threads per V-Sample block (64..256, multiple of 32). Default: 256, and
+    int32_t block_threads;    /* threads per V-Sample block (64..256, multiple of 32). Default: 256;
                                  1024 for FP32 adjusting iterations, whose one block per SM holds the
-                                 fixed-point histogram */
+                                 fixed-point histogram; 512 for the FP64 kernel of the Genz families up to
+                                 d = 12 (one block per SM, one copy of its tables) */
     int32_t blocks_per_sm;    /* resident blocks per SM to launch (persistent grid); default: occupancy */
     int32_t fp64_plain;       /* FP64 precision, single-job V-Sample: 0 (default) takes the FP64 kernel with
                                  integer bin extraction and per-bin folded integrand tables for the six Genz
