@@ -65,6 +65,21 @@ int main()
             int E;
             if (std::scanf("%llu %d", &v, &E) != 2) return 1;
             std::printf("%llu\n", b(exp_tab(d(v), E, T)));
+        } else if (op[0] == 'J') {     // d, s bits, then d bin factors P_k: the exp families' folded weight
+            int dd;
+            if (std::scanf("%d %llu", &dd, &v) != 2) return 1;
+            const double s = d(v);
+            int sE = 0;                 // the exponent fields of the P_k
+            long long sl = 0;           // ln m_k, |P_k| = 2^E_k m_k, in 2^-52 units (the block's table)
+            for (int i = 0; i < dd; ++i) {
+                if (std::scanf("%llu", &w) != 1) return 1;
+                const double pk = d(w), ap = std::fabs(pk);
+                const int field = (bits::hi(pk) >> 20) & 0x7FF;
+                const double lm = ap > 0.0 ? std::log(std::ldexp(ap, -(field - 1023))) : -64.0;
+                sE += field;
+                sl += std::llrint(std::ldexp(lm, 52));
+            }
+            std::printf("%llu\n", b(exp_tab(bits::fma_rn((double)sl, 0x1p-52, -s), sE - dd * 1023, T)));
         } else if (op[0] == 'C') {     // t bits: cos(2 pi t)
             if (std::scanf("%llu", &v) != 1) return 1;
             std::printf("%llu\n", b(cos_turns(d(v), CS)));
@@ -205,6 +220,44 @@ def test_exp_tab_against_high_precision(bits_exe, tables, mp):
             else:                                   # subnormal or zero: within two subnormal units
                 assert abs(mp.mpf(got) - want) <= 2 * mp.mpf(2) ** -1074 + 3 * U53 * want, (x, E, got, float(want))
     assert worst > 0.0
+
+
+def test_jacobian_in_exponent(bits_exe, tables, mp):
+    """The Gaussian's and C0's weight exp(-s) prod |P_k| as the kernel forms it: the bins' exponent
+    fields summed as integers, ln m_k summed in 2^-52 fixed point, one exp_tab call. Its error is that of
+    exp at the argument x = sum ln m_k - s (|x| units of 2^-53) plus the d table entries' roundings."""
+    rng = np.random.default_rng(9)
+    lines, cases = [], []
+    for _ in range(3000):
+        d = int(rng.integers(1, 17))
+        P = rng.choice([-1.0, 1.0], d) * 10.0 ** rng.uniform(-6, 1.5, d)
+        s = float(rng.uniform(0.0, 40.0))
+        lines.append(f"J {d} {_bits(s)} " + " ".join(str(_bits(float(p))) for p in P))
+        cases.append((s, P))
+    # subnormal and zero-width factors: the weight is prod |P_k| exp(-s), or zero
+    for P in ([1e-310, 0.3, 2.0], [0.0, 0.5, 0.7], [5e-324, 1e300, 1e10]):
+        lines.append(f"J 3 {_bits(0.5)} " + " ".join(str(_bits(p)) for p in P))
+        cases.append((0.5, np.array(P)))
+    out = _run(bits_exe, tables, lines)
+    worst = 0.0
+    with mp.workprec(400):
+        for (s, P), line in zip(cases, out):
+            got = _from_bits(int(line))
+            want = mp.exp(-mp.mpf(s)) * mp.fprod([abs(mp.mpf(float(p))) for p in P])
+            if want == 0:
+                assert got == 0.0
+                continue
+            if want < 2.0 ** -1022:
+                assert abs(mp.mpf(got) - want) <= 2 * mp.mpf(2) ** -1074 + 1e-12 * want, (s, P, got)
+                continue
+            # the argument exp_tab receives: ln m_k with E_k = (exponent field) - 1023, as the kernel takes it
+            # (a subnormal factor's m_k lies below 1)
+            x = abs(float(sum(mp.log(abs(mp.mpf(float(p))) / mp.mpf(2) ** (((_bits(float(p)) >> 52) & 0x7FF) - 1023))
+                              for p in P)) - s)
+            err = float(abs(mp.mpf(got) - want) / want) / U53
+            worst = max(worst, err)
+            assert err <= x + len(P) + 4, (s, list(P), got, float(want), err)
+    assert worst > 1.0
 
 
 def test_cos_turns_against_high_precision(bits_exe, tables, mp):
