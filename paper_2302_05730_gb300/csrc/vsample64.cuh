@@ -21,17 +21,20 @@
 //     (times prod a^2 for the product peak) folded into the launch's scale fscale;
 //   - for the families closed by exp (Gaussian, C0, discontinuous) the Jacobian joins the exponent:
 //     |P_k| = 2^E_k m_k, so prod |P_k| = 2^(sum E_k) exp(sum ln m_k); E_k is read from the bits of
-//     P_k and summed as an integer, ln m_k (tabulated per bin, below ln 2) is summed exactly in
-//     64-bit fixed point, and the product costs no FP64 operation (the sign of prod a goes to
-//     fscale);
+//     P_k and summed as an integer, ln m_k (tabulated per bin: below ln 2, and above -37 for a
+//     subnormal P_k) is summed exactly in 64-bit fixed point, and the product costs no FP64
+//     operation (the sign of prod a goes to fscale);
 //   - exp and cos are table-driven (2^(j/256), cos and sin of 2 pi j / 256, filled per block), with
 //     their reduced arguments' Taylor series to 2^-54 (no library constants or steps); the integer
 //     k of the reduction is found in FP32 (within one of the nearest), off the FP64 pipe;
 //   - the discontinuous family's cut x_i < u_i is decided exactly as defined, by one integer
 //     comparison of the offset's bits with a per-bin threshold the block finds by bisection.
-// The per-cube statistics and the reduction are the FP64 kernel's own (vsample.cuh: finish_block).
-// Bin contributions (both kernels below): each sample's first (d + 1) / 2 axes go straight to the
-// global C with native FP64 reductions, the rest to the block's shared FP64 copy, flushed into C.
+// The bit-level steps (c + u and yn, the bin split, exp and cos) are in fp64_bits.cuh, which also
+// compiles for the host. The per-cube statistics and the reduction are the FP64 kernel's own
+// (vsample.cuh: finish_block). Bin contributions (both kernels below): each sample's first (d + 1) / 2
+// axes go straight to the global C with native FP64 reductions, the rest to the block's shared FP64
+// copies (four lane-interleaved ones in the single-job kernel, one in the batched kernel), flushed
+// into C.
 #pragma once
 
 #include <cmath>
