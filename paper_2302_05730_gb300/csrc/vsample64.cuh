@@ -103,7 +103,7 @@ inline bool fast64_fold(int fid, VsampleParams &Q, int d)
 // block would spill: 256 threads there.
 __host__ __device__ constexpr int fast64_threads(int d) { return d <= 12 ? 512 : 256; }
 
-// Axes whose bin contributions go straight to the global C (the rest use the block's shared copy).
+// Axes whose bin contributions go straight to the global C (the rest use the block's shared copies).
 __host__ __device__ constexpr int fast64_l2_axes(int d) { return (d + 1) / 2; }
 
 // Shared-memory bytes of one fast FP64 block's tables: the (P, Q) table, the ln m_k table (centred
@@ -344,9 +344,10 @@ __device__ __forceinline__ void sample_cubes_fast64(const VsampleParams &P, cons
                 const double wf = w * P.fscale;
                 const double hv = wf * wf;
                 // The first kL2 axes: native FP64 reductions into the global C, which the L2 performs, off
-                // the FP64 pipe. The rest: the block's shared copy, whose atomics are compare-and-swap loops
-                // around an FP64 add on the SM. Half and half keeps the launch time the same wherever C lies
-                // (the L2's reduction rate into C depends on its physical placement). A zero adds nothing.
+                // the FP64 pipe. The rest: this lane's copy of the block's shared bins, whose atomics are
+                // compare-and-swap loops around an FP64 add on the SM. Half and half keeps the launch time the
+                // same wherever C lies (the L2's reduction rate into C depends on its physical placement). A
+                // zero adds nothing.
                 if (hv != 0.0) {
                     constexpr int kL2 = fast64_l2_axes(D);
 #pragma unroll

@@ -153,7 +153,8 @@ int launch_fast64(const VsampleParams &P, const LaunchReq &req, cudaStream_t s, 
 }
 
 // Frozen iterations take the histogram-free instance; adjusting ones the FP32 kernel with the
-// fixed-point histogram, or the FP64 kernel with one shared copy.
+// fixed-point histogram, or an FP64 kernel: the fast one for the Genz families (half the axes on the
+// L2, half in lane-interleaved shared copies), else the plain one with one shared copy.
 template <int D>
 int launch_d(const VsampleParams &P, const LaunchReq &req, cudaStream_t s)
 {
